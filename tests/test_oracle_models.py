@@ -1,0 +1,282 @@
+"""Pins of the oracle's cell models and time stepping (Eq. (Euler), Eq. (RL),
+Eq. (RLcoeff), Eq. (FHN), Barkley, ZFK, Beeler-Reuter) and of the unsplit
+whole-grid step.  Closed forms and fixed points come from the model
+definitions (polynomial roots), not from the oracle."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1605_06015_gb300 import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def test_fhn_rest_point_is_root_of_the_cubic():
+    # Reading of Eq. (FHN): u - u^3/3.  Rest: v = (u+beta)/gamma and
+    # u - u^3/3 - v = 0, i.e. -u^3/3 + (1 - 1/gamma) u - beta/gamma = 0.
+    eps, beta, gamma = 0.3, 0.71, 0.5
+    roots = np.roots([-1 / 3, 0, 1 - 1 / gamma, -beta / gamma])
+    real = roots[np.abs(roots.imag) < 1e-12].real
+    assert real.size == 1  # unique rest state
+    y = oracle.rest_state(oracle.FHN)
+    assert abs(y[0] - real[0]) < 1e-12
+    assert abs(y[1] - (real[0] + beta) / gamma) < 1e-12
+    # the rest state is a fixed point of the Euler step
+    yn = oracle.cell_update(oracle.FHN, y, dt=0.01)
+    assert np.allclose(yn, y, rtol=0, atol=1e-14)
+    # With the printed u^2/3 the same parameters have no real rest state.
+    roots2 = np.roots([-1 / 3, 1 - 1 / gamma, -beta / gamma])
+    assert np.all(np.abs(roots2.imag) > 1e-3)
+
+
+def test_barkley_fixed_points_and_threshold():
+    a, b, eps = 0.75, 0.02, 0.02
+    for u in (0.0, 1.0, b / (a - 1)):
+        y = np.array([u, u])
+        yn = oracle.cell_update(oracle.BARKLEY, y, dt=0.005, par=[a, b, eps])
+        assert np.allclose(yn, y, rtol=0, atol=1e-15)
+    # excitable: below the threshold b/a a small u decays, above it grows
+    th = b / a
+    lo = oracle.cell_update(oracle.BARKLEY, [0.5 * th, 0.0], dt=1e-3, par=[a, b, eps])
+    hi = oracle.cell_update(oracle.BARKLEY, [2.0 * th, 0.0], dt=1e-3, par=[a, b, eps])
+    assert lo[0] < 0.5 * th and hi[0] > 2.0 * th
+
+
+def test_zfk_fixed_points():
+    for u in (0.0, 0.13, 1.0):
+        assert oracle.cell_update(oracle.ZFK, [u], dt=0.1)[0] == pytest.approx(u, abs=1e-16)
+
+
+def test_euler_is_first_order():
+    # Forward Euler (Eq. Euler) converges at first order: halving dt halves
+    # the error against a much finer run of the same scheme extrapolated.
+    y0 = np.array([1.7, 0.7])
+    T = 2.0
+
+    def run(dt):
+        y = y0.copy()
+        for _ in range(int(round(T / dt))):
+            y = oracle.cell_update(oracle.FHN, y, dt=dt)
+        return y
+
+    a, b, c = run(0.02), run(0.01), run(0.005)
+    r = np.linalg.norm(a - b) / np.linalg.norm(b - c)
+    assert 1.8 < r < 2.2
+
+
+def test_rush_larsen_is_exact_for_clamped_voltage():
+    # Eq. (RL) read as y_{n+1} = A y_n + B: with V held fixed, n steps of
+    # size k equal the closed-form gate solution at t = n k for any k, and
+    # y_inf = alpha/(alpha+beta) is a fixed point.
+    V = -30.0
+    al, be = oracle.br_rates(V)
+    rest = oracle.rest_state(oracle.BR)
+    for k, n in ((0.02, 50), (0.5, 2), (3.0, 1)):
+        y = rest.copy(); y[0] = V
+        for _ in range(n):
+            yn = oracle.cell_update(oracle.BR, y, dt=k)
+            y[2:] = yn[2:]  # gates advance; V and Ca stay clamped
+        yinf = al / (al + be)
+        g0 = rest[2:]
+        exact = yinf + (g0 - yinf) * np.exp(-(al + be) * n * k)
+        assert np.allclose(y[2:], exact, rtol=1e-12, atol=1e-15)
+    y = rest.copy(); y[0] = V; y[2:] = al / (al + be)
+    yn = oracle.cell_update(oracle.BR, y, dt=0.7)
+    assert np.allclose(yn[2:], y[2:], rtol=1e-13, atol=1e-16)
+
+
+def test_br_removable_singularities_are_continuous():
+    for Vs in (-47.0, -23.0):
+        a0, _ = oracle.br_rates(Vs)
+        a1, _ = oracle.br_rates(Vs + 1e-7)
+        assert np.allclose(a0, a1, rtol=1e-5)
+        y = oracle.rest_state(oracle.BR)
+        y0 = y.copy(); y0[0] = Vs
+        y1 = y.copy(); y1[0] = Vs + 1e-7
+        c0, c1 = oracle.br_currents(y0), oracle.br_currents(y1)
+        assert np.all(np.isfinite(c0)) and abs(c0[0] - c1[0]) < 1e-4
+
+
+def test_br_action_potential_qualitative():
+    """PARITY UNPINNED (the paper does not print the BR constants): only the
+    textbook shape of the BR action potential is checked."""
+    y = oracle.rest_state(oracle.BR)
+    assert -86.0 < y[0] < -83.0  # BR resting potential about -84.6 mV
+    res = oracle.cell_update(oracle.BR, y, dt=0.01)
+    assert abs(res[0] - y[0]) < 1e-9
+    y[0] = 20.0  # +20 mV initial depolarisation, as the apex stimulus
+    Vmax, t, dt, t_rep = -100.0, 0.0, 0.01, None
+    while t < 600:
+        y = oracle.cell_update(oracle.BR, y, dt=dt)
+        t += dt
+        Vmax = max(Vmax, y[0])
+        if t > 20 and t_rep is None and y[0] < -60:
+            t_rep = t
+    assert Vmax > 20.0
+    assert t_rep is not None and 150 < t_rep < 450  # plateau, then repolarisation
+    assert -87.0 < y[0] < -80.0
+
+
+def _disc_run(h, off, T=0.2):
+    """Section "Monodomain diffusion...": J0 disc problem, no-flux boundary,
+    forward Euler with dt = h^2/80; returns (Linf, L2) errors over [0, T]."""
+    from scipy.special import j0, jn_zeros
+    gam = jn_zeros(1, 1)[0]  # first positive root of J0' = -J1
+    n = int(np.ceil(2.0 / h)) + 5
+    c0 = (n // 2 + off[0]) * h, (n // 2 + off[1]) * h
+    y, x = np.meshgrid(np.arange(n) * h, np.arange(n) * h, indexing="ij")
+    r = np.sqrt((x - c0[0]) ** 2 + (y - c0[1]) ** 2)
+    inside = r <= 1.0
+    g = oracle.Grid(n, n, 1, h, inside.astype(np.uint8)[None], None, 1.0)
+    dt = h * h / 80
+    nsteps = int(round(T / dt))
+    sim = oracle.Sim(g, oracle.DIFFUSION, state=np.where(inside, j0(gam * r), 0.0)[None, None])
+    chunks = 40
+    per = nsteps // chunks
+    linf, l2s, ts = 0.0, [], []
+    for ci in range(chunks + 1):
+        t = ci * per * dt
+        ex = j0(gam * r) * np.exp(-gam * gam * t)
+        e = np.where(inside, sim.state[0, 0] - ex, 0.0)
+        linf = max(linf, np.abs(e).max())
+        l2s.append((e ** 2).sum() / inside.sum()); ts.append(t)
+        if ci == chunks:
+            break
+        sim.step(dt, per)
+    l2 = np.sqrt(np.trapezoid(l2s, ts) / ts[-1])
+    return linf, l2
+
+
+@pytest.mark.slow
+def test_disc_convergence_slopes_like_the_paper():
+    """Fig. discerror: errors converge faster than h^1, slower than h^2; the
+    paper's fitted slopes are 1.564 (Linf) and 1.719 (L2)."""
+    gd = _golden("disc_convergence.json")
+    hs = [1 / 6, 1 / 8, 1 / 11, 1 / 16]
+    offs = [(0, 0), (0.2, 0.2), (0.2, 0.6), (0.6, 0.6)]
+    H, EI, E2 = [], [], []
+    for h in hs:
+        for off in offs:
+            li, l2 = _disc_run(h, off)
+            H.append(h); EI.append(li); E2.append(l2)
+    si = np.polyfit(np.log(H), np.log(EI), 1)[0]
+    s2 = np.polyfit(np.log(H), np.log(E2), 1)[0]
+    assert 1.0 < si < 2.0 and 1.0 < s2 < 2.2, (si, s2)
+    assert abs(si - gd["slope_Linf"]) < 0.35 and abs(s2 - gd["slope_L2"]) < 0.35, (si, s2)
+
+
+def _zfk_run(h, L=10.0, T=10.0, alpha=0.13, Dpar=2.0, Dperp=0.2, fib_deg=30.0, wave_deg=0.0,
+             s=-2.0):
+    """Monodomain reduction of the ZFK test (Eq. ZFKbidomV with one domain):
+    plane front V = 1/(1+exp((n.r - s - c t)/sqrt(2 D*))), D* = n^T D n,
+    c = sqrt(2 D*)(1/2 - alpha); Dirichlet values from the exact solution on
+    the outer ring of nodes, as in the paper's set-up; dt = 3h^2/(16 Dpar)."""
+    n = int(round(L / h)) + 1
+    y, x = np.meshgrid(np.arange(n) * h, np.arange(n) * h, indexing="ij")
+    fa = np.deg2rad(fib_deg)
+    f = np.array([np.cos(fa), np.sin(fa), 0.0])
+    fib = np.zeros((1, n, n, 3), np.float32); fib[...] = f.astype(np.float32)
+    f64 = fib[0, 0, 0].astype(np.float64); f64 /= np.linalg.norm(f64)
+    D = Dperp * np.eye(3) + (Dpar - Dperp) * np.outer(f64, f64)
+    wa = np.deg2rad(wave_deg)
+    nv = np.array([np.cos(wa), np.sin(wa), 0.0])
+    Ds = nv @ D @ nv
+    c = np.sqrt(2 * Ds) * (0.5 - alpha)
+
+    def exact(t):
+        return 1.0 / (1.0 + np.exp((x * nv[0] + y * nv[1] - s - c * t) / np.sqrt(2 * Ds)))
+
+    g = oracle.Grid(n, n, 1, h, None, fib, Dpar, Dperp)
+    sim = oracle.Sim(g, oracle.ZFK, par=[alpha], state=exact(0.0)[None, None])
+    dt = 3 * h * h / (16 * Dpar)
+    nsteps = int(round(T / dt))
+    ring = np.zeros((n, n), bool); ring[0, :] = ring[-1, :] = ring[:, 0] = ring[:, -1] = True
+    err = 0.0
+    for k in range(nsteps):
+        sim.step(dt, 1)
+        ex = exact((k + 1) * dt)
+        sim.state[0, 0][ring] = ex[ring]
+        err = max(err, np.abs(sim.state[0, 0] - ex).max())
+    return err
+
+
+@pytest.mark.slow
+def test_zfk_front_converges_at_second_order_oblique_fibres():
+    e1, e2 = _zfk_run(0.5), _zfk_run(0.25)
+    slope = np.log2(e1 / e2)
+    assert e2 < 2e-2 and 1.6 < slope < 2.5, (e1, e2, slope)
+
+
+def test_homogeneous_grid_reproduces_the_single_cell_ode_bitwise():
+    # L(const) = 0 exactly, so a homogeneous tissue follows the cell ODE with
+    # the same arithmetic: bit-identical trajectories.
+    mask, fib = wl.random_geometry(6, 5, 4, seed=21)
+    g = oracle.Grid(6, 5, 4, 0.3, mask, fib, 1.0, 0.25)
+    y0 = np.array([0.9, 0.1])
+    st = np.empty((2, 4, 5, 6)); st[0] = y0[0]; st[1] = y0[1]
+    sim = oracle.Sim(g, oracle.BARKLEY, state=st)
+    sim.step(0.005, 200)
+    y = y0.copy()
+    for _ in range(200):
+        y = oracle.cell_update(oracle.BARKLEY, y, dt=0.005)
+    tis = mask != 0
+    assert np.all(sim.state[0][tis] == y[0]) and np.all(sim.state[1][tis] == y[1])
+
+
+def test_void_nodes_never_change_and_activation_is_first_upward_crossing():
+    nx = 40
+    mask = np.ones((1, 3, nx), np.uint8); mask[0, 1, 5] = 0
+    g = oracle.Grid(nx, 3, 1, 0.3, mask, None, 1.0)
+    st = np.zeros((2, 1, 3, nx)); st[0, :, :, :3] = 1.0; st[0, 0, 1, 5] = 7.0
+    sim = oracle.Sim(g, oracle.BARKLEY, state=st)
+    for _ in range(100):
+        sim.step(0.005, 40)
+    assert sim.state[0, 0, 1, 5] == 7.0 and sim.state[1, 0, 1, 5] == 0.0
+    a = sim.act[0, 0]
+    assert np.all(a[3:] < oracle.INT32_MAX)      # the front reached the far end
+    assert np.all(np.diff(a[3:].astype(np.int64)) >= 0)  # monotone in x
+    assert np.all(sim.act[0, 1, :3] == oracle.INT32_MAX)  # started above theta
+
+
+def test_stimulus_window_is_half_open_and_depolarising():
+    g = oracle.Grid(3, 1, 1, 0.3, None, None, 1.0)
+    sim = oracle.Sim(g, oracle.ZFK, state=np.zeros((1, 1, 1, 3)))
+    reg = np.array([[[0, 1, 0]]], np.uint8)
+    sim.set_stimulus(reg, amp=2.0, t_on=0.0, t_off=0.03)
+    sim.step(0.01, 3)  # t = 0, 0.01, 0.02: on
+    v3 = sim.state[0, 0, 0, 1]
+    assert v3 > 0 and sim.state[0, 0, 0, 0] > 0  # diffused to the neighbour
+    st = sim.state.copy()
+    sim.step(0.01, 1)  # t = 0.03: off
+    tmp = oracle.Sim(g, oracle.ZFK, state=st)
+    tmp.step(0.01, 1)
+    assert np.array_equal(sim.state, tmp.state)
+
+
+def test_active_bricks_bruteforce_matches_numpy_reshape():
+    rng = np.random.default_rng(5)
+    for (nx, ny, nz, tx, ty, tz) in ((37, 21, 9, 16, 4, 4), (64, 64, 16, 64, 8, 8), (5, 3, 2, 16, 4, 4)):
+        mask = (rng.random((nz, ny, nx)) < 0.02).astype(np.uint8)
+        g = oracle.Grid(nx, ny, nz, 1.0, mask)
+        got = g.active_bricks(tx, ty, tz)
+        nbx, nby, nbz = -(-nx // tx), -(-ny // ty), -(-nz // tz)
+        pad = np.zeros((nbz * tz, nby * ty, nbx * tx), np.uint8)
+        pad[:nz, :ny, :nx] = mask
+        anyb = pad.reshape(nbz, tz, nby, ty, nbx, tx).any(axis=(1, 3, 5))
+        ref = np.nonzero(anyb.reshape(-1))[0].astype(np.int32)
+        assert np.array_equal(got, ref)
+
+
+def test_total_is_tissue_sum():
+    mask, _ = wl.random_geometry(9, 7, 3, seed=2)
+    g = oracle.Grid(9, 7, 3, 1.0, mask)
+    u = np.random.default_rng(1).normal(size=(3, 7, 9))
+    assert g.total(u) == pytest.approx(float(np.sum(u[mask != 0])), rel=1e-14)
