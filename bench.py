@@ -1,0 +1,323 @@
+"""Benchmark of the fused monodomain step on GB300.
+
+Workload: the 3D Barkley slab, 256 x 256 x 64 nodes, fibre angle rotating
+linearly by 120 degrees through z, D_par = 1, D_perp = 0.25, h = 0.3,
+dt = 0.005, 19-point anisotropic stencil, FP32 state, 8 seeded point stimuli.
+One benchmark step is one explicit time step of the whole grid: stencil +
+reaction + activation map + tissue total of V, all in one kernel launch.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl bbx|reference]
+
+value:  cell-updates/s with the state resident in HBM, device-timed with CUDA
+        events around each step's launch; L2 is flushed (256 MiB write)
+        between timed steps, outside the events.
+e2e:    the same metric through the C ABI with host buffers: every step
+        writes u and v from pinned host memory, steps, and reads u and v back.
+Under torchrun each rank steps its own slab (independent replicas, no
+collective on the data path): weak scaling, value summed over ranks.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD_DESC = ("3D Barkley slab 256x256x64, fibre angle rotating 120 deg through z, D_par=1 D_perp=0.25, "
+                 "h=0.3, dt=0.005, a=0.75 b=0.02 eps=0.02, 19-point stencil, 8 seeded point stimuli")
+METRIC = "cell-updates/s"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1605_06015_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def load_traffic(workload):
+    """DRAM bytes per launch of the step kernel from a committed ncu summary,
+    valid only while the kernel sources are unchanged."""
+    p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("kernel_source_hash") == kernel_source_hash() and d.get("workload") == workload:
+            return float(d["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rate(w, steps, nz_sample=None):
+    """Oracle (FP64 CPU, single thread) cell-updates/s on a bounded sample:
+    `steps` steps in one call on the first nz_sample planes of the slab."""
+    import numpy as np
+    import oracle
+    from paper_1605_06015_gb300 import workloads as wl
+    if nz_sample is not None and nz_sample < w.nz:
+        w = wl.barkley_slab(w.nx, w.ny, nz_sample)
+    og = oracle.Grid(w.nx, w.ny, w.nz, w.h, w.mask, w.fibres, w.D_par, w.D_perp)
+    st = w.initial_state(oracle.rest_state(w.model, w.params))
+    sim = oracle.Sim(og, w.model, par=w.params, state=st)
+    t0 = time.perf_counter()
+    sim.step(w.dt, steps)
+    dt = time.perf_counter() - t0
+    return w.n_active() * steps / dt, dt, w
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws == 1:
+        return 0, 1, 0, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, ws, local, dist
+
+
+def run_reference(args):
+    rank, ws, local, dist = dist_setup()
+    if rank != 0:
+        return 0
+    from paper_1605_06015_gb300 import workloads as wl
+    w = wl.barkley_slab()
+    times = []
+    for i in range(args.warmup + args.steps):
+        rate, dt, ws_ = oracle_rate(w, 1, nz_sample=8)
+        if i >= args.warmup:
+            times.append(dt)
+    cells = 256 * 256 * 8
+    T = sum(times)
+    value = cells * args.steps / T
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)",
+            "config": {"workload": WORKLOAD_DESC, "sample": "first 8 z-planes (256x256x8) per step"},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": "one oracle call of 1 step on the 256x256x8 sub-slab per benchmark step"},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_bbx(args):
+    import numpy as np
+    import torch
+    rank, ws, local, dist = dist_setup()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    import oracle
+    from paper_1605_06015_gb300 import bbx
+    from paper_1605_06015_gb300 import workloads as wl
+
+    w = wl.barkley_slab()
+    rest = oracle.rest_state(w.model, w.params)  # only to build the IC host-side
+    st0 = w.initial_state(rest).astype(np.float32)
+    stream = torch.cuda.current_stream()
+    G = bbx.Grid(w.nx, w.ny, w.nz, w.h, w.mask, stream=stream)
+    G.set_fibres(w.fibres, w.D_par, w.D_perp)
+    G.set_ionic_model(w.model, w.params)
+    G.set_threshold(w.theta)
+    G.write_all(st0)
+    tune_ms = G.autotune(w.dt)
+    info = G.get_info()
+    n_tissue = info["n_tissue"]
+    S = info["nvars"]
+    B_alg = 2 * S * 4 + (12 if info["anisotropic"] else 0) + (1 if info["masked"] else 0)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        G.step(w.dt, 1)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        G.step(w.dt, 1)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    total_v = G.step_total()
+    if dist:
+        t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms = float(t.item())
+    ms_step = dev_ms / args.steps
+    value = n_tissue * args.steps * ws / (dev_ms * 1e-3)
+
+    # end to end through the C ABI with host buffers
+    pin_in = [torch.from_numpy(st0[v].copy()).pin_memory() for v in range(S)]
+    pin_out = [torch.empty(st0[v].shape, dtype=torch.float32).pin_memory() for v in range(S)]
+    e2e_steps = max(3, min(args.steps, 20))
+    for _ in range(2):
+        for v in range(S):
+            G.write_state(v, pin_in[v])
+        G.step(w.dt, 1)
+        for v in range(S):
+            G.read_state(v, out=pin_out[v])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for v in range(S):
+            G.write_state(v, pin_in[v])
+        G.step(w.dt, 1)
+        for v in range(S):
+            G.read_state(v, out=pin_out[v])
+    torch.cuda.synchronize()
+    e_wall = time.perf_counter() - e0
+    if dist:
+        t = torch.tensor([e_wall], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_wall = float(t.item())
+    e2e_value = n_tissue * e2e_steps * ws / e_wall
+    bytes_io = S * w.n_cells * 4
+
+    peak, peak_kind = load_peaks()
+    achieved = B_alg * n_tissue / (ms_step * 1e-3) / 1e9
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, secs, _ = oracle_rate(w, args.cpu_steps)
+        cpu = {"value": rate, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+               "sample": "%d steps of the full 256x256x64 slab in one oracle call (%.1f s, weights built once "
+                         "per call)" % (args.cpu_steps, secs)}
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+        "config": {"workload": WORKLOAD_DESC, "active_cells": n_tissue, "l2": "flushed between timed steps "
+                   "(256 MiB write, outside the events)", "tile": [info["tile_x"], info["tile_y"], info["tile_z"]],
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": load_traffic("barkley_slab_256x256x64"), "peak_kind": peak_kind,
+                     "bytes_per_cell": B_alg},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": bytes_io,
+                "d2h_bytes_per_step": bytes_io, "steps": e2e_steps},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "tissue_total_V": total_v,
+        "autotune_ms_per_step": tune_ms,
+        "wall_s_timed": wall,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    G.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="bbx", choices=["bbx", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_bbx(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

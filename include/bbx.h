@@ -1,0 +1,212 @@
+/*
+ * bbx.h - C ABI of the GB300 (sm_103a) monodomain reaction-diffusion step.
+ *
+ * The library (libbbx.so) advances the monodomain model of arXiv:1605.06015,
+ * Eq. (monodomain), on a regular finite-difference grid:
+ *
+ *   dV/dt = -I_ion(V, g)/Cm + (L V) + I_stim/Cm,     dg/dt = f(g, V)
+ *
+ * with the anisotropic diffusion operator L of Eq. (Lu) discretised by the
+ * weights W = Wbar + Wtilde of the section "Monodomain diffusion and boundary
+ * conditions" (19 points in 3D, corner weights 0; 9 points in 2D, 5 when
+ * isotropic), no-flux boundaries through the grid indicator psi, the
+ * transversely isotropic tensor of Eq. (sigma), and the unsplit scheme of the
+ * section "Computation of intermediate expressions": forward Euler, Eq.
+ * (Euler), for V and the other non-gate variables, Rush-Larsen, Eq. (RL), for
+ * gates.  One call of bbx_step with n_steps = 1 is one turn of the paper's
+ * diff + euler/rushlarsen ring.
+ *
+ * Conventions for every call:
+ *   - Return value: BBX_OK (0) or a negative BBX_ERR_* code.  No call throws,
+ *     exits the process or traps on the GPU.  bbx_status_string() names codes.
+ *   - Host arrays use the dense layout, x fastest: index x + nx*(y + ny*z),
+ *     n = nx*ny*nz elements.  The caller owns every host buffer; the library
+ *     copies what it needs before returning (except where stated).
+ *   - Device memory owned by the library is pitched: each x-row holds
+ *     px = round_up(nx, 32) elements (bbx_get_info).
+ *   - Work is enqueued on the CUDA stream given at bbx_create_grid.  Calls
+ *     that return data to the host synchronise that stream first, and report
+ *     sticky device errors (BBX_ERR_NAN, BBX_ERR_TIMEOUT) raised by earlier
+ *     asynchronous steps.
+ *   - A grid handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef BBX_H
+#define BBX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define BBX_OK 0
+#define BBX_ERR_ARG (-1)        /* invalid argument (null pointer, size, range) */
+#define BBX_ERR_CUDA (-2)       /* a CUDA runtime or driver call failed */
+#define BBX_ERR_FIBRE (-3)      /* zero fibre vector at a tissue node */
+#define BBX_ERR_UNSTABLE (-4)   /* dt above the explicit diffusion stability bound */
+#define BBX_ERR_NAN (-5)        /* a step produced a non-finite V (sticky) */
+#define BBX_ERR_TIMEOUT (-6)    /* a bounded in-kernel wait gave up (sticky) */
+#define BBX_ERR_STATE (-7)      /* call out of order (e.g. step before a model) */
+#define BBX_ERR_NOMEM (-8)      /* device allocation failed */
+#define BBX_ERR_UNSUPPORTED (-9) /* no compiled kernel for this configuration */
+
+/* ---- cell models (section "Cell models") ------------------------------- */
+/* Parameters in order; a shorter params array keeps the remaining defaults.
+ *  BBX_FHN       2 vars (u, v).  eps=0.3 beta=0.71 gamma=0.5.  Eq. (FHN), read
+ *                with the cubic u - u^3/3 (fhncub).  threshold 0.
+ *  BBX_BARKLEY   2 vars (u, v).  a=0.75 b=0.02 eps=0.02.  Barkley (1991):
+ *                du = u(1-u)(u-(v+b)/a)/eps, dv = u - v.  threshold 0.5.
+ *  BBX_BR        8 vars (V, Ca, x1, m, h, j, d, f).  gNa=4 gNaC=0.003 ENa=50
+ *                gs=0.09.  Beeler-Reuter (1977) ionic model: V and Ca by
+ *                Euler, the 6 gates by Rush-Larsen.  Cm = 1 uF/cm^2, V in mV,
+ *                t in ms, Ca in mol/L.  threshold -40 mV.
+ *  BBX_ZFK       1 var.  alpha=0.13.  dV = V(V-alpha)(1-V), Eq. (ZFKbidomV).
+ *                threshold 0.5.
+ *  BBX_DIFFUSION 1 var, no reaction (the diffusion equation alone).
+ *                threshold 0.5. */
+#define BBX_FHN 1
+#define BBX_BARKLEY 2
+#define BBX_BR 3
+#define BBX_ZFK 4
+#define BBX_DIFFUSION 5
+
+#define BBX_ACT_NONE 2147483647 /* activation map value of a node never activated */
+
+typedef struct bbx_grid bbx_grid;
+
+typedef struct {
+    int nx, ny, nz;          /* grid dimensions (nz = 1: 2D) */
+    int px;                  /* device row pitch in elements */
+    int nvars;               /* state variables of the current model (0: none) */
+    int model;               /* BBX_* model id (0: none) */
+    int masked;              /* 1 if a tissue mask was given */
+    int anisotropic;         /* 1 if fibres were given */
+    int tile_x, tile_y, tile_z; /* brick shape of the step kernel */
+    long long n_bricks;      /* bricks with at least one tissue node */
+    long long n_tissue;      /* tissue nodes (active cells per step) */
+    long long step;          /* steps taken since the model was set */
+    double t;                /* model time */
+} bbx_info;
+
+/* Create a grid of nx*ny*nz nodes with spacing h (the paper's hx).
+ * mask_host: NULL (every node is tissue) or n bytes, nonzero = tissue (the
+ * .bbg status flag, section "Format of BeatBox geometry files"); nodes outside
+ * the array are void.  cuda_stream: a cudaStream_t (NULL = legacy default).
+ * Idle bricks (no tissue) are elided (section "Domain partitioning").
+ * Allocates device memory for the mask and the brick list; the caller keeps
+ * its buffer.  Errors: BBX_ERR_ARG (null out, nonpositive size or h,
+ * nx*ny*nz >= 2^31), BBX_ERR_NOMEM, BBX_ERR_CUDA. */
+int bbx_create_grid(bbx_grid** out, int nx, int ny, int nz, double h, const uint8_t* mask_host,
+                    void* cuda_stream);
+
+/* Fibres and diffusivities, Eq. (sigma): D = D_perp I + (D_par - D_perp) f f^T.
+ * f_xyz_host: NULL (isotropic, D = D_par I) or 3*n floats, interleaved
+ * (fx, fy, fz) per node as in a .bbg line.  Vectors are normalised; values at
+ * void nodes are ignored.  Errors: BBX_ERR_FIBRE (zero vector at a tissue
+ * node; the grid keeps its previous fibres), BBX_ERR_ARG (negative D). */
+int bbx_set_fibres(bbx_grid* g, const float* f_xyz_host, double D_par, double D_perp);
+
+/* Select the cell model and its parameters (copied).  Allocates the two
+ * ping-pong state buffers (unless bound by bbx_bind_state), sets every node to
+ * the model's rest state, clears the activation map, and resets t and the
+ * step counter to 0.  Errors: BBX_ERR_ARG (unknown model, n_params < 0 or
+ * params NULL with n_params > 0), BBX_ERR_NOMEM. */
+int bbx_set_ionic_model(bbx_grid* g, int model, const double* params, int n_params);
+
+/* Copy one state variable from the host (n = nx*ny*nz floats) into both
+ * ping-pong buffers.  Synchronous.  Errors: BBX_ERR_STATE (no model),
+ * BBX_ERR_ARG (var out of range, n wrong, null). */
+int bbx_write_state(bbx_grid* g, int var, const float* host, size_t n);
+
+/* Let the caller (e.g. PyTorch) own the state: dev_a and dev_b each hold
+ * bytes >= nvars*nz*ny*px*4 bytes laid out [var][z][y][x] with row pitch px,
+ * 16-byte aligned.  The library never frees them.  Must follow
+ * bbx_set_ionic_model; the rest state is written into both.  Errors:
+ * BBX_ERR_STATE, BBX_ERR_ARG (null, misaligned, too small). */
+int bbx_bind_state(bbx_grid* g, void* dev_a, void* dev_b, size_t bytes);
+
+/* Stimulus current (section "Explicit solvers", I_eff of Eq. (ODE)): amp is
+ * added to dV/dt (divided by Cm) at the nodes where region_host is nonzero,
+ * on steps whose start time t_n satisfies t_on <= t_n < t_off.  region_host
+ * NULL removes the stimulus.  The region is copied. */
+int bbx_set_stimulus(bbx_grid* g, const uint8_t* region_host, double amp, double t_on, double t_off);
+
+/* Activation threshold theta (k_poincare device): a node's activation step is
+ * the first n+1 with V^n < theta <= V^{n+1}.  Default: the model's threshold. */
+int bbx_set_threshold(bbx_grid* g, double theta);
+
+/* Advance n_steps explicit steps of size dt (asynchronous on the grid's
+ * stream).  Each step also writes the double-precision sum of the new V over
+ * tissue nodes (read with bbx_step_total).  Errors: BBX_ERR_STATE (no
+ * model), BBX_ERR_ARG (dt <= 0, n_steps < 0), BBX_ERR_CUDA (launch),
+ * BBX_ERR_UNSTABLE when dt (4 tr D + 2 |D_par - D_perp|) > 2 h^2, tr D =
+ * D_par + 2 D_perp (3 D_par when isotropic): a Gershgorin bound on the
+ * spectrum of the discrete diffusion operator, above which forward Euler
+ * can amplify round-off. */
+int bbx_step(bbx_grid* g, double dt, int n_steps);
+
+/* Copy one state variable to the host (n = nx*ny*nz floats).  Synchronises. */
+int bbx_read_state(bbx_grid* g, int var, float* host_out, size_t n);
+
+/* Activation steps (BBX_ACT_NONE where not activated), n int32.  Synchronises. */
+int bbx_read_activation(bbx_grid* g, int32_t* host_out, size_t n);
+
+/* Restore an activation map (checkpoint/resume).  Synchronous. */
+int bbx_write_activation(bbx_grid* g, const int32_t* host, size_t n);
+
+/* Sum of one state variable over tissue nodes (reduce device), accumulated in
+ * double precision.  Synchronises. */
+int bbx_total(bbx_grid* g, int var, double* out);
+
+/* The tissue sum of V after the most recent step, computed inside that step.
+ * Synchronises.  BBX_ERR_STATE if no step was taken. */
+int bbx_step_total(bbx_grid* g, double* out);
+
+/* Model time and step counter (checkpoint/resume). */
+int bbx_get_time(bbx_grid* g, double* t, long long* step);
+int bbx_set_time(bbx_grid* g, double t, long long step);
+
+/* Geometry, model and brick-shape information. */
+int bbx_get_info(bbx_grid* g, bbx_info* out);
+
+/* Brick ids (bx + nbx*(by + nby*bz)) of the bricks holding tissue, in
+ * increasing order, for the current brick shape.  cap: capacity of out;
+ * *count receives the number of bricks.  Synchronises. */
+int bbx_read_active_bricks(bbx_grid* g, int32_t* out, size_t cap, long long* count);
+
+/* Choose the brick shape of the step kernel: tile_y in {4, 8, 16} rows of 64
+ * nodes, and tile_z >= 1 planes per brick.  Rebuilds the brick list. */
+int bbx_set_tiling(bbx_grid* g, int tile_y, int tile_z);
+
+/* Time candidate brick shapes with CUDA events on the grid's stream (a few
+ * steps each, state restored afterwards) and keep the fastest.  best_ms (may
+ * be NULL) receives its time per step. */
+int bbx_autotune(bbx_grid* g, double dt, double* best_ms);
+
+/* Device pointer of the current buffer of one state variable (pitched
+ * layout), for callers that keep data on the GPU. */
+int bbx_state_device_ptr(bbx_grid* g, int var, void** dev_ptr);
+
+/* Fault injection for failure-detection tests: when on, the first plane load
+ * of CTA 0 in each step waits for bytes no copy delivers, so that CTA's
+ * bounded wait (about 1 ms in this mode) runs out; the step then records
+ * BBX_ERR_TIMEOUT, which the next synchronising call returns.  No fault, trap
+ * or hang reaches the GPU. */
+int bbx_debug_poison_first_load(bbx_grid* g, int on);
+
+/* Clear the sticky device error bits (after a reported BBX_ERR_NAN or
+ * BBX_ERR_TIMEOUT).  Synchronous. */
+int bbx_clear_device_error(bbx_grid* g);
+
+/* Release every resource of the grid (NULL is ignored). */
+void bbx_destroy_grid(bbx_grid* g);
+
+/* Static text for a status code. */
+const char* bbx_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BBX_H */

@@ -1,0 +1,311 @@
+"""Thin ctypes binding of the C ABI in include/bbx.h (libbbx.so).
+
+Every function keeps the C name and only marshals arguments: NumPy arrays (or
+PyTorch CPU tensors, e.g. pinned buffers) become host pointers, status codes
+become ``BbxError``.  All computation happens in the CUDA library; there is no
+fallback.  Importing this module fails loudly if libbbx.so has not been built
+(``__graft_entry__.build()`` or ``python paper_1605_06015_gb300/build.py``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libbbx.so")
+
+BBX_OK = 0
+BBX_ERR_ARG = -1
+BBX_ERR_CUDA = -2
+BBX_ERR_FIBRE = -3
+BBX_ERR_UNSTABLE = -4
+BBX_ERR_NAN = -5
+BBX_ERR_TIMEOUT = -6
+BBX_ERR_STATE = -7
+BBX_ERR_NOMEM = -8
+BBX_ERR_UNSUPPORTED = -9
+
+BBX_FHN, BBX_BARKLEY, BBX_BR, BBX_ZFK, BBX_DIFFUSION = 1, 2, 3, 4, 5
+NVARS = {BBX_FHN: 2, BBX_BARKLEY: 2, BBX_BR: 8, BBX_ZFK: 1, BBX_DIFFUSION: 1}
+BBX_ACT_NONE = 2147483647
+
+
+class BbxError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (where, bbx_status_string(code), code))
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("px", ctypes.c_int),
+                ("nvars", ctypes.c_int), ("model", ctypes.c_int), ("masked", ctypes.c_int),
+                ("anisotropic", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
+                ("tile_z", ctypes.c_int), ("n_bricks", ctypes.c_longlong), ("n_tissue", ctypes.c_longlong),
+                ("step", ctypes.c_longlong), ("t", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libbbx.so is not built (%s): run __graft_entry__.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, D, Z, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_longlong
+    sig = {
+        "bbx_create_grid": [ctypes.POINTER(P), I, I, I, D, P, P],
+        "bbx_set_fibres": [P, P, D, D],
+        "bbx_set_ionic_model": [P, I, P, I],
+        "bbx_write_state": [P, I, P, Z],
+        "bbx_bind_state": [P, P, P, Z],
+        "bbx_set_stimulus": [P, P, D, D, D],
+        "bbx_set_threshold": [P, D],
+        "bbx_step": [P, D, I],
+        "bbx_read_state": [P, I, P, Z],
+        "bbx_read_activation": [P, P, Z],
+        "bbx_write_activation": [P, P, Z],
+        "bbx_total": [P, I, ctypes.POINTER(D)],
+        "bbx_step_total": [P, ctypes.POINTER(D)],
+        "bbx_get_time": [P, ctypes.POINTER(D), ctypes.POINTER(LL)],
+        "bbx_set_time": [P, D, LL],
+        "bbx_get_info": [P, ctypes.POINTER(Info)],
+        "bbx_read_active_bricks": [P, P, Z, ctypes.POINTER(LL)],
+        "bbx_set_tiling": [P, I, I],
+        "bbx_autotune": [P, D, ctypes.POINTER(D)],
+        "bbx_state_device_ptr": [P, I, ctypes.POINTER(P)],
+        "bbx_debug_poison_first_load": [P, I],
+        "bbx_clear_device_error": [P],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = I
+    L.bbx_destroy_grid.argtypes = [P]
+    L.bbx_destroy_grid.restype = None
+    L.bbx_status_string.argtypes = [I]
+    L.bbx_status_string.restype = ctypes.c_char_p
+    return L
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(rc, where):
+    if rc != BBX_OK:
+        raise BbxError(rc, where)
+
+
+def _hostptr(a, dtype, n):
+    """Host pointer of a contiguous NumPy array or CPU torch tensor of n
+    elements of dtype; returns (pointer, keep-alive object)."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        if a.is_cuda or not a.is_contiguous() or a.numel() != n:
+            raise ValueError("expected a contiguous CPU tensor of %d elements" % n)
+        if a.element_size() != np.dtype(dtype).itemsize:
+            raise ValueError("dtype mismatch")
+        return a.data_ptr(), a
+    arr = np.ascontiguousarray(a, dtype=dtype).reshape(-1)
+    if arr.size != n:
+        raise ValueError("expected %d elements, got %d" % (n, arr.size))
+    return arr.ctypes.data, arr
+
+
+def _stream_handle(stream):
+    if stream is not None:
+        return getattr(stream, "cuda_stream", stream)
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+def bbx_status_string(code):
+    return _lib.bbx_status_string(int(code)).decode()
+
+
+def bbx_create_grid(nx, ny, nz, h, mask=None, stream=None):
+    g = ctypes.c_void_p()
+    n = nx * ny * nz
+    mp, keep = _hostptr(None if mask is None else (np.asarray(mask) != 0), np.uint8, n)
+    _check(_lib.bbx_create_grid(ctypes.byref(g), int(nx), int(ny), int(nz), float(h), mp,
+                                _stream_handle(stream)), "bbx_create_grid")
+    return g
+
+
+def bbx_destroy_grid(g):
+    _lib.bbx_destroy_grid(g)
+
+
+def bbx_get_info(g):
+    inf = Info()
+    _check(_lib.bbx_get_info(g, ctypes.byref(inf)), "bbx_get_info")
+    return {f: getattr(inf, f) for f, _ in Info._fields_}
+
+
+def _ncell(g):
+    i = bbx_get_info(g)
+    return i["nx"] * i["ny"] * i["nz"], (i["nz"], i["ny"], i["nx"])
+
+
+def bbx_set_fibres(g, fibres, D_par, D_perp):
+    n, _ = _ncell(g)
+    fp, keep = _hostptr(fibres, np.float32, 3 * n)
+    _check(_lib.bbx_set_fibres(g, fp, float(D_par), float(D_perp)), "bbx_set_fibres")
+
+
+def bbx_set_ionic_model(g, model, params=None):
+    p = np.zeros(0) if params is None else np.ascontiguousarray(params, dtype=np.float64)
+    _check(_lib.bbx_set_ionic_model(g, int(model), p.ctypes.data if p.size else None, p.size),
+           "bbx_set_ionic_model")
+
+
+def bbx_write_state(g, var, values):
+    n, _ = _ncell(g)
+    vp, keep = _hostptr(values, np.float32, n)
+    _check(_lib.bbx_write_state(g, int(var), vp, n), "bbx_write_state")
+
+
+def bbx_bind_state(g, dev_a, dev_b, nbytes=None):
+    """dev_a, dev_b: CUDA torch tensors (or raw device pointers with nbytes)."""
+    if hasattr(dev_a, "data_ptr"):
+        nbytes = min(dev_a.numel() * dev_a.element_size(), dev_b.numel() * dev_b.element_size())
+        dev_a, dev_b = dev_a.data_ptr(), dev_b.data_ptr()
+    _check(_lib.bbx_bind_state(g, dev_a, dev_b, int(nbytes)), "bbx_bind_state")
+
+
+def bbx_set_stimulus(g, region, amp, t_on, t_off):
+    n, _ = _ncell(g)
+    rp, keep = _hostptr(None if region is None else (np.asarray(region) != 0), np.uint8, n)
+    _check(_lib.bbx_set_stimulus(g, rp, float(amp), float(t_on), float(t_off)), "bbx_set_stimulus")
+
+
+def bbx_set_threshold(g, theta):
+    _check(_lib.bbx_set_threshold(g, float(theta)), "bbx_set_threshold")
+
+
+def bbx_step(g, dt, n_steps=1):
+    _check(_lib.bbx_step(g, float(dt), int(n_steps)), "bbx_step")
+
+
+def bbx_read_state(g, var, out=None):
+    n, shape = _ncell(g)
+    if out is None:
+        out = np.empty(shape, dtype=np.float32)
+    op, keep = _hostptr(out, np.float32, n)
+    if isinstance(keep, np.ndarray) and keep is not out and not np.shares_memory(keep, out):
+        raise ValueError("out must be a contiguous float32 array")
+    _check(_lib.bbx_read_state(g, int(var), op, n), "bbx_read_state")
+    return out
+
+
+def bbx_read_activation(g, out=None):
+    n, shape = _ncell(g)
+    if out is None:
+        out = np.empty(shape, dtype=np.int32)
+    _check(_lib.bbx_read_activation(g, out.ctypes.data, n), "bbx_read_activation")
+    return out
+
+
+def bbx_write_activation(g, act):
+    n, _ = _ncell(g)
+    ap, keep = _hostptr(act, np.int32, n)
+    _check(_lib.bbx_write_activation(g, ap, n), "bbx_write_activation")
+
+
+def bbx_total(g, var=0):
+    out = ctypes.c_double()
+    _check(_lib.bbx_total(g, int(var), ctypes.byref(out)), "bbx_total")
+    return out.value
+
+
+def bbx_step_total(g):
+    out = ctypes.c_double()
+    _check(_lib.bbx_step_total(g, ctypes.byref(out)), "bbx_step_total")
+    return out.value
+
+
+def bbx_get_time(g):
+    t, n = ctypes.c_double(), ctypes.c_longlong()
+    _check(_lib.bbx_get_time(g, ctypes.byref(t), ctypes.byref(n)), "bbx_get_time")
+    return t.value, n.value
+
+
+def bbx_set_time(g, t, step):
+    _check(_lib.bbx_set_time(g, float(t), int(step)), "bbx_set_time")
+
+
+def bbx_read_active_bricks(g):
+    cnt = ctypes.c_longlong()
+    rc = _lib.bbx_read_active_bricks(g, None, 0, ctypes.byref(cnt))
+    if rc not in (BBX_OK, BBX_ERR_ARG):
+        _check(rc, "bbx_read_active_bricks")
+    out = np.zeros(max(cnt.value, 1), dtype=np.int32)
+    _check(_lib.bbx_read_active_bricks(g, out.ctypes.data, out.size, ctypes.byref(cnt)),
+           "bbx_read_active_bricks")
+    return out[:cnt.value].copy()
+
+
+def bbx_set_tiling(g, tile_y, tile_z):
+    _check(_lib.bbx_set_tiling(g, int(tile_y), int(tile_z)), "bbx_set_tiling")
+
+
+def bbx_autotune(g, dt):
+    ms = ctypes.c_double()
+    _check(_lib.bbx_autotune(g, float(dt), ctypes.byref(ms)), "bbx_autotune")
+    return ms.value
+
+
+def bbx_state_device_ptr(g, var):
+    p = ctypes.c_void_p()
+    _check(_lib.bbx_state_device_ptr(g, int(var), ctypes.byref(p)), "bbx_state_device_ptr")
+    return p.value
+
+
+def bbx_debug_poison_first_load(g, on):
+    _check(_lib.bbx_debug_poison_first_load(g, int(bool(on))), "bbx_debug_poison_first_load")
+
+
+def bbx_clear_device_error(g):
+    _check(_lib.bbx_clear_device_error(g), "bbx_clear_device_error")
+
+
+class Grid:
+    """Convenience owner of a grid handle (destroyed with the object)."""
+
+    def __init__(self, nx, ny, nz, h, mask=None, stream=None):
+        self.shape = (nz, ny, nx)
+        self.h = h
+        self.g = bbx_create_grid(nx, ny, nz, h, mask, stream)
+
+    def close(self):
+        if self.g:
+            bbx_destroy_grid(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __getattr__(self, name):
+        fn = globals().get("bbx_" + name)
+        if fn is None or not callable(fn):
+            raise AttributeError(name)
+        return lambda *a, **k: fn(self.g, *a, **k)
+
+    def read_all(self):
+        S = bbx_get_info(self.g)["nvars"]
+        return np.stack([bbx_read_state(self.g, v) for v in range(S)])
+
+    def write_all(self, state):
+        for v in range(state.shape[0]):
+            bbx_write_state(self.g, v, np.asarray(state[v], dtype=np.float32))

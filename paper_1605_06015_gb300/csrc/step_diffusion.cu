@@ -1,0 +1,23 @@
+// Explicit instantiations of the fused step kernel for the diffusion model.
+#include "bbx_device.cuh"
+
+namespace bbx {
+
+template <bool MA, bool AN, int TY>
+static StepKernel make_diffusion() {
+    using P = Plan<BBX_DIFFUSION, MA, AN, TY>;
+    return StepKernel{reinterpret_cast<const void*>(&step_kernel<BBX_DIFFUSION, MA, AN, TY>), P::SMEM, P::THREADS, TY};
+}
+
+StepKernel step_kernel_diffusion(bool masked, bool aniso, int ty) {
+#define BBX_CASE(MA, AN, T) \
+    if (masked == MA && aniso == AN && ty == T) return make_diffusion<MA, AN, T>();
+    BBX_CASE(false, false, 4) BBX_CASE(false, false, 8) BBX_CASE(false, false, 16)
+    BBX_CASE(false, true, 4) BBX_CASE(false, true, 8) BBX_CASE(false, true, 16)
+    BBX_CASE(true, false, 4) BBX_CASE(true, false, 8) BBX_CASE(true, false, 16)
+    BBX_CASE(true, true, 4) BBX_CASE(true, true, 8) BBX_CASE(true, true, 16)
+#undef BBX_CASE
+    return StepKernel{nullptr, 0, 0, 0};
+}
+
+}  // namespace bbx

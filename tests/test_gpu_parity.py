@@ -1,0 +1,330 @@
+"""GPU parity: the CUDA step (through the C ABI) against the FP64 oracle on the
+same seeded inputs.  Bars: relative L-infinity of V <= 1e-4 after 100 steps,
+activation steps within 1 step over a full run, integer outputs bit-exact."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1605_06015_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+V_TOL = 1e-4      # relative L-infinity on V after 100 steps
+OTHER_TOL = 1e-3  # other state variables (reported, looser)
+
+
+@pytest.fixture(scope="module")
+def bbx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1605_06015_gb300 import bbx as b
+    return b
+
+
+def _rel_linf(got, ref, sel):
+    scale = max(np.abs(ref[sel]).max(), 1e-30)
+    return np.abs(got[sel] - ref[sel]).max() / scale
+
+
+def _gpu_grid(bbx, w, ty=None, tz=None):
+    G = bbx.Grid(w.nx, w.ny, w.nz, w.h, w.mask)
+    if w.fibres is not None:
+        G.set_fibres(w.fibres, w.D_par, w.D_perp)
+    else:
+        G.set_fibres(None, w.D_par, w.D_par)
+    if ty is not None:
+        G.set_tiling(ty, tz)
+    G.set_ionic_model(w.model, w.params)
+    G.set_threshold(w.theta)
+    return G
+
+
+def _pair(bbx, w, n_steps, ty=None, tz=None, stim=None):
+    """Run n_steps on both sides from the same float32-rounded initial state."""
+    rest = oracle.rest_state(w.model, w.params)
+    st0 = w.initial_state(rest).astype(np.float32)
+    og = oracle.Grid(w.nx, w.ny, w.nz, w.h, w.mask, w.fibres, w.D_par, w.D_perp)
+    osim = oracle.Sim(og, w.model, par=w.params, theta=w.theta, state=st0.astype(np.float64))
+    G = _gpu_grid(bbx, w, ty, tz)
+    G.write_all(st0)
+    if stim is not None:
+        osim.set_stimulus(*stim)
+        G.set_stimulus(*stim)
+    osim.step(w.dt, n_steps)
+    G.step(w.dt, n_steps)
+    return osim, G
+
+
+def _check_state(osim, G, w):
+    tis = osim.grid.psi
+    got = G.read_all()
+    e = [_rel_linf(got[v], osim.state[v], tis) for v in range(osim.S)]
+    assert e[0] <= V_TOL, e
+    for v in range(1, osim.S):
+        assert e[v] <= OTHER_TOL, (v, e)
+    # void nodes are never touched
+    if w.mask is not None:
+        void = ~tis
+        assert np.array_equal(got[:, void], osim.state[:, void].astype(np.float32))
+    return e
+
+
+def _check_activation(osim, G, n_steps):
+    ag = G.read_activation().astype(np.int64)
+    ao = osim.act.astype(np.int64)
+    big = n_steps + 1
+    ag[ag == oracle.INT32_MAX] = big
+    ao[ao == oracle.INT32_MAX] = big
+    tis = osim.grid.psi
+    d = np.abs(ag - ao)[tis]
+    assert d.max() <= 1, (d.max(), np.count_nonzero(d > 1))
+    return int(np.count_nonzero(ao[tis] < big))
+
+
+def test_fhn2d_config1_100_steps(bbx):
+    w = wl.fhn_sheet()
+    osim, G = _pair(bbx, w, 100)
+    _check_state(osim, G, w)
+
+
+def test_fhn2d_config1_activation_full_run(bbx):
+    w = wl.fhn_sheet()
+    osim, G = _pair(bbx, w, w.n_steps)
+    n_act = _check_activation(osim, G, w.n_steps)
+    assert n_act > 1000  # the cross-field IC makes a wave that activates tissue
+
+
+@pytest.mark.parametrize("shape,ty,tz", [((96, 40, 24), 8, 16), ((67, 45, 13), 4, 5), ((130, 33, 9), 16, 4),
+                                         ((64, 16, 40), 8, 40)])
+def test_barkley3d_rotating_fibres_100_steps(bbx, shape, ty, tz):
+    nx, ny, nz = shape
+    w = wl.barkley_slab(nx, ny, nz)
+    osim, G = _pair(bbx, w, 100, ty, tz)
+    _check_state(osim, G, w)
+    _check_activation(osim, G, 100)
+
+
+def test_br_slab_100_steps(bbx):
+    w = wl.br_slab(72, 20, 10)
+    osim, G = _pair(bbx, w, 100, 8, 5)
+    _check_state(osim, G, w)
+
+
+def test_br_shell_masked_100_steps_and_bricks(bbx):
+    w = wl.br_shell(64)
+    osim, G = _pair(bbx, w, 100, 8, 8)
+    _check_state(osim, G, w)
+    _check_activation(osim, G, 100)
+    og = osim.grid
+    for ty, tz in ((8, 8), (4, 3), (16, 64)):
+        G.set_tiling(ty, tz)
+        assert np.array_equal(G.read_active_bricks(), og.active_bricks(64, ty, min(tz, w.nz)))
+
+
+@pytest.mark.parametrize("seed,shape,aniso", [(1, (37, 29, 11), True), (2, (70, 9, 6), True), (3, (23, 41, 1), True),
+                                              (4, (65, 17, 7), False)])
+def test_random_masks_and_fibres_zfk(bbx, seed, shape, aniso):
+    nx, ny, nz = shape
+    mask, fib = wl.random_geometry(nx, ny, nz, seed, tissue_frac=0.6, aniso=aniso)
+    rng = np.random.default_rng(seed + 50)
+    w = wl.Workload("zfk_rand", nx, ny, nz, 0.5, 0.01, wl.ZFK, [0.13], 1.0, 0.3 if aniso else 1.0, mask=mask,
+                    fibres=fib, ic_fields={0: rng.random((nz, ny, nx))}, theta=0.5)
+    osim, G = _pair(bbx, w, 60, 8, 4)
+    _check_state(osim, G, w)
+
+
+def test_isotropic_2d_fhn_ragged_sheet(bbx):
+    w = wl.fhn_sheet(131, 77)
+    osim, G = _pair(bbx, w, 100, 16, 1)
+    _check_state(osim, G, w)
+
+
+def test_stimulus_current(bbx):
+    w = wl.fhn_sheet(70, 50)
+    w.ic_fields = {}
+    reg = np.zeros(w.shape, np.uint8)
+    reg[0, 20:30, 10:20] = 1
+    osim, G = _pair(bbx, w, 100, stim=(reg, 1.5, 0.2, 0.6))
+    _check_state(osim, G, w)
+
+
+def test_totals_fused_and_standalone(bbx):
+    w = wl.br_shell(48)
+    osim, G = _pair(bbx, w, 20, 8, 8)
+    g = osim.grid
+    for v in range(osim.S):
+        got = G.total(v)
+        ref = g.total(G.read_state(v).astype(np.float64))
+        assert got == pytest.approx(ref, rel=1e-12, abs=1e-300)
+    ref0 = g.total(G.read_state(0).astype(np.float64))
+    assert G.step_total() == pytest.approx(ref0, rel=1e-12)
+
+
+def test_conservation_uniform_fibres_masked_diffusion(bbx):
+    mask, _ = wl.random_geometry(70, 30, 12, 9, tissue_frac=0.8, aniso=False)
+    fib = np.zeros((12, 30, 70, 3), np.float32)
+    fib[...] = np.array([0.6, -0.3, 0.74], np.float32)
+    rng = np.random.default_rng(3)
+    u0 = rng.random((12, 30, 70)).astype(np.float32)
+    G = bbx.Grid(70, 30, 12, 0.5, mask)
+    G.set_fibres(fib, 1.0, 0.25)
+    G.set_ionic_model(bbx.BBX_DIFFUSION)
+    G.write_state(0, u0)
+    T0 = G.total(0)
+    G.step(0.02, 300)
+    T1 = G.total(0)
+    u1 = G.read_state(0)
+    tis = mask != 0
+    # no-flux boundaries conserve the tissue total; FP32 round-off only
+    assert abs(T1 - T0) <= 1e-5 * np.abs(u0[tis]).sum()
+    assert u1[tis].std() < 0.5 * u0[tis].std()  # and it did diffuse
+
+
+def test_homogeneous_tissue_stays_homogeneous_bitwise(bbx):
+    mask, fib = wl.random_geometry(50, 20, 9, 11, tissue_frac=0.7)
+    G = bbx.Grid(50, 20, 9, 0.3, mask)
+    G.set_fibres(fib, 1.0, 0.2)
+    G.set_ionic_model(bbx.BBX_BARKLEY)
+    G.write_state(0, np.full((9, 20, 50), 0.9, np.float32))
+    G.write_state(1, np.full((9, 20, 50), 0.1, np.float32))
+    G.step(0.005, 150)
+    u = G.read_state(0)[mask != 0]
+    assert np.all(u == u[0])
+
+
+def test_edge_cases(bbx):
+    # single node, isotropic and anisotropic
+    for fib in (None, np.array([[[[0.0, 0.0, 2.0]]]], np.float32)):
+        G = bbx.Grid(1, 1, 1, 0.3)
+        G.set_fibres(fib, 1.0, 0.5)
+        G.set_ionic_model(bbx.BBX_FHN)
+        G.write_state(0, np.array([[[1.7]]], np.float32))
+        G.step(0.01, 10)
+        y = np.array([1.7, oracle.rest_state(oracle.FHN)[1]], np.float32).astype(np.float64)
+        for _ in range(10):
+            y = oracle.cell_update(oracle.FHN, y, dt=0.01)
+        assert abs(G.read_state(0)[0, 0, 0] - y[0]) < 1e-5
+    # no tissue at all: stepping is a no-op
+    G = bbx.Grid(40, 10, 3, 0.3, np.zeros((3, 10, 40), np.uint8))
+    G.set_ionic_model(bbx.BBX_BARKLEY)
+    G.step(0.005, 5)
+    assert G.step_total() == 0.0 and G.get_info()["n_bricks"] == 0
+    # isolated tissue nodes behave as single cells
+    m = np.zeros((5, 6, 7), np.uint8)
+    m[0, 0, 0] = m[2, 3, 4] = m[4, 5, 6] = 1
+    G = bbx.Grid(7, 6, 5, 0.3, m)
+    G.set_fibres(np.ones((5, 6, 7, 3), np.float32), 1.0, 0.1)
+    G.set_ionic_model(bbx.BBX_BARKLEY)
+    G.write_state(0, np.full((5, 6, 7), 0.9, np.float32))
+    G.step(0.005, 50)
+    u = G.read_state(0)[m != 0]
+    assert np.all(u == u[0])
+    # one-node-thick 3D sheet (nz = 1 plane inside a 3-plane box)
+    m = np.zeros((3, 20, 70), np.uint8)
+    m[1] = 1
+    w = wl.Workload("sheet", 70, 20, 3, 0.4, 0.01, wl.ZFK, [0.13], 1.0, 0.3, mask=m,
+                    fibres=wl.rotational_fibres(70, 20, 3),
+                    ic_fields={0: np.random.default_rng(0).random((3, 20, 70))}, theta=0.5)
+    osim, G = _pair(bbx, w, 50, 4, 2)
+    _check_state(osim, G, w)
+
+
+def test_errors_are_reported(bbx):
+    G = bbx.Grid(16, 8, 4, 0.3)
+    with pytest.raises(bbx.BbxError) as e:
+        G.step(0.01, 1)
+    assert e.value.code == bbx.BBX_ERR_STATE
+    G.set_ionic_model(bbx.BBX_FHN)
+    with pytest.raises(bbx.BbxError) as e:
+        G.step(1.0, 1)
+    assert e.value.code == bbx.BBX_ERR_UNSTABLE
+    fib = np.ones((4, 8, 16, 3), np.float32)
+    fib[1, 2, 3] = 0
+    with pytest.raises(bbx.BbxError) as e:
+        G.set_fibres(fib, 1.0, 0.2)
+    assert e.value.code == bbx.BBX_ERR_FIBRE
+    assert G.get_info()["anisotropic"] == 0
+
+
+def test_bounded_wait_reports_timeout_and_recovers(bbx):
+    # Fault injection on the host side of the protocol: one CTA waits for
+    # bytes no copy delivers; its bounded wait runs out and the step records
+    # a timeout instead of hanging.  The context stays usable.
+    w = wl.barkley_slab(64, 32, 16)
+    G = _gpu_grid(bbx, w, 8, 8)
+    G.debug_poison_first_load(1)
+    G.step(w.dt, 1)
+    with pytest.raises(bbx.BbxError) as e:
+        G.read_state(0)
+    assert e.value.code == bbx.BBX_ERR_TIMEOUT
+    G.debug_poison_first_load(0)
+    G.clear_device_error()
+    osim, G2 = _pair(bbx, w, 20, 8, 8)
+    _check_state(osim, G2, w)
+
+
+def test_checkpoint_resume_is_bit_identical(bbx):
+    w = wl.barkley_slab(80, 24, 12)
+    rest = oracle.rest_state(w.model, w.params)
+    st0 = w.initial_state(rest).astype(np.float32)
+    A = _gpu_grid(bbx, w, 8, 4)
+    A.write_all(st0)
+    A.step(w.dt, 60)
+    mid, act, (t, n) = A.read_all(), A.read_activation(), A.get_time()
+    A.step(w.dt, 60)
+    B = _gpu_grid(bbx, w, 8, 4)
+    B.write_all(mid)
+    B.write_activation(act)
+    B.set_time(t, n)
+    B.step(w.dt, 60)
+    assert np.array_equal(A.read_all(), B.read_all())
+    assert np.array_equal(A.read_activation(), B.read_activation())
+
+
+def test_bound_torch_buffers(bbx):
+    import torch
+    w = wl.barkley_slab(64, 20, 6)
+    G = _gpu_grid(bbx, w, 8, 6)
+    info = G.get_info()
+    n = info["nvars"] * info["nz"] * info["ny"] * info["px"]
+    a = torch.zeros(n, dtype=torch.float32, device="cuda")
+    b = torch.zeros(n, dtype=torch.float32, device="cuda")
+    G.bind_state(a, b)
+    rest = oracle.rest_state(w.model, w.params)
+    st0 = w.initial_state(rest).astype(np.float32)
+    G.write_all(st0)
+    G.step(w.dt, 3)
+    torch.cuda.synchronize()
+    cur = a if G.state_device_ptr(0) == a.data_ptr() else b
+    u = cur.view(info["nvars"], info["nz"], info["ny"], info["px"])[0, :, :, :info["nx"]].cpu().numpy()
+    assert np.array_equal(u, G.read_state(0))
+
+
+def test_full_size_slab_one_step_sampled(bbx):
+    """The 256x256x64 rotating-fibre Barkley slab at full size, in the
+    autotuned launch configuration the benchmark uses: one step from the
+    seeded initial state, checked node by node at sampled nodes."""
+    w = wl.barkley_slab()
+    rest = oracle.rest_state(w.model, w.params)
+    st0 = w.initial_state(rest).astype(np.float32)
+    G = _gpu_grid(bbx, w)
+    G.write_all(st0)
+    G.autotune(w.dt)
+    G.step(w.dt, 1)
+    got = G.read_all()
+    rng = np.random.default_rng(77)
+    reg = w.ic_region
+    edge = np.zeros_like(reg)
+    edge[:, :, 1:] |= reg[:, :, 1:] != reg[:, :, :-1]
+    edge[:, 1:, :] |= reg[:, 1:, :] != reg[:, :-1, :]
+    edge[1:, :, :] |= reg[1:, :, :] != reg[:-1, :, :]
+    cand = np.flatnonzero(edge)
+    cells = np.concatenate([rng.choice(cand, 1500, replace=False), rng.integers(0, w.n_cells, 500)])
+    og = oracle.Grid(w.nx, w.ny, w.nz, w.h, w.mask, w.fibres, w.D_par, w.D_perp)
+    osim = oracle.Sim(og, w.model, par=w.params, theta=w.theta, state=st0.astype(np.float64))
+    ref = osim.step_cells(w.dt, cells)
+    flat = got.reshape(got.shape[0], -1)
+    for v in range(2):
+        e = np.abs(flat[v, cells] - ref[:, v]).max() / max(np.abs(ref[:, v]).max(), 1e-30)
+        assert e <= 1e-5, (v, e)
