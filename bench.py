@@ -178,6 +178,40 @@ def run_reference(args):
     return 0
 
 
+def run_e2e(G, w, st0, S, args, dist, dev, ws, n_tissue):
+    """Steps through the C ABI with host buffers: write u and v from pinned
+    host memory, one step, read u and v back into pinned host memory."""
+    import torch
+    pin_in = [torch.from_numpy(st0[v].copy()).pin_memory() for v in range(S)]
+    pin_out = [torch.empty(st0[v].shape, dtype=torch.float32).pin_memory() for v in range(S)]
+    e2e_steps = max(3, min(args.steps, 20))
+    for _ in range(2):
+        for v in range(S):
+            G.write_state(v, pin_in[v])
+        G.step(w.dt, 1)
+        for v in range(S):
+            G.read_state(v, out=pin_out[v])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for v in range(S):
+            G.write_state(v, pin_in[v])
+        G.step(w.dt, 1)
+        for v in range(S):
+            G.read_state(v, out=pin_out[v])
+    torch.cuda.synchronize()
+    e_wall = time.perf_counter() - e0
+    if dist:
+        t = torch.tensor([e_wall], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_wall = float(t.item())
+    e2e_value = n_tissue * e2e_steps * ws / e_wall
+    bytes_io = S * w.n_cells * 4
+    return {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": bytes_io,
+            "d2h_bytes_per_step": bytes_io, "steps": e2e_steps}
+
 def run_bbx(args):
     import numpy as np
     import torch
@@ -199,7 +233,12 @@ def run_bbx(args):
     G.set_ionic_model(w.model, w.params)
     G.set_threshold(w.theta)
     G.write_all(st0)
-    tune_ms = G.autotune(w.dt)
+    if args.tile:
+        ty, tz = (int(v) for v in args.tile.split(","))
+        G.set_tiling(ty, tz)
+        tune_ms = None
+    else:
+        tune_ms = G.autotune(w.dt)
     info = G.get_info()
     n_tissue = info["n_tissue"]
     S = info["nvars"]
@@ -239,34 +278,8 @@ def run_bbx(args):
     ms_step = dev_ms / args.steps
     value = n_tissue * args.steps * ws / (dev_ms * 1e-3)
 
-    # end to end through the C ABI with host buffers
-    pin_in = [torch.from_numpy(st0[v].copy()).pin_memory() for v in range(S)]
-    pin_out = [torch.empty(st0[v].shape, dtype=torch.float32).pin_memory() for v in range(S)]
-    e2e_steps = max(3, min(args.steps, 20))
-    for _ in range(2):
-        for v in range(S):
-            G.write_state(v, pin_in[v])
-        G.step(w.dt, 1)
-        for v in range(S):
-            G.read_state(v, out=pin_out[v])
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    e0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        for v in range(S):
-            G.write_state(v, pin_in[v])
-        G.step(w.dt, 1)
-        for v in range(S):
-            G.read_state(v, out=pin_out[v])
-    torch.cuda.synchronize()
-    e_wall = time.perf_counter() - e0
-    if dist:
-        t = torch.tensor([e_wall], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_wall = float(t.item())
-    e2e_value = n_tissue * e2e_steps * ws / e_wall
-    bytes_io = S * w.n_cells * 4
+    e2e = None if args.no_e2e else run_e2e(G, w, st0, S, args, dist, dev, ws, n_tissue)
+
 
     peak, peak_kind = load_peaks()
     achieved = B_alg * n_tissue / (ms_step * 1e-3) / 1e9
@@ -287,8 +300,7 @@ def run_bbx(args):
                      "traffic": load_traffic("barkley_slab_256x256x64"), "peak_kind": peak_kind,
                      "bytes_per_cell": B_alg},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": bytes_io,
-                "d2h_bytes_per_step": bytes_io, "steps": e2e_steps},
+        "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clk,
         "tissue_total_V": total_v,
@@ -311,6 +323,8 @@ def main():
     ap.add_argument("--impl", default="bbx", choices=["bbx", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tile", default=None, help="TY,TZ brick shape instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

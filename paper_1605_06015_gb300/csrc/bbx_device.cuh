@@ -39,17 +39,22 @@ struct StepArgs {
     int nx, ny, nz, px;
     long long plane;  // px * ny
     long long vol;    // px * ny * nz
-    int nbx, nby, zb;
-    const int* bricks;  // active brick ids, or nullptr = all bricks in order
-    int n_bricks;
+    // Work schedule: CTA c marches through pieces[cta_off[c] .. cta_off[c+1]),
+    // each piece = (x0, y0, z0, z1): one 64 x TY column of the grid over the
+    // z-range [z0, z1).  The host balances the planes per CTA.
+    const int4* pieces;
+    const int* cta_off;
     float* dst;  // destination state buffer (var v at dst + v*vol)
     int32_t* act;
     float theta;
     int step_next;  // n+1 for this step
     const uint8_t* stim;
     float stim_amp;  // 0: stimulus off for this step
-    float dt, inv_h2;
-    float Dperp, dD, Diso;  // anisotropic: D = Dperp I + dD f f^T; isotropic: Diso I
+    float dt;
+    // diffusion constants over h^2: anisotropic D = Dperp I + (Dpar-Dperp) f f^T
+    // gives c_perp = Dperp/h^2, c_d = (Dpar-Dperp)/h^2, c_dh = c_d/2 (edge
+    // weights), c_s = c_d/4 (Wtilde); isotropic D gives c_iso = D/h^2.
+    float c_perp, c_d, c_dh, c_s, c_iso;
     float mp[8];            // model parameters (already in kernel form)
     double* partials;       // >= gridDim.x doubles
     unsigned int* ticket;   // zero between launches
@@ -299,13 +304,21 @@ struct Model<BBX_BR> {
 // shared-memory plan of the step kernel
 // ---------------------------------------------------------------------------
 
-constexpr int kTileX = 64;
+constexpr int kTileX = 64;  // nodes per brick along x (two warps)
+constexpr int kCY = 4;      // nodes per thread along y
 constexpr int align128(int b) { return (b + 127) & ~127; }
+
+// Tissue-mask byte on the device: bit 0 = tissue, bit 1 = tissue node whose
+// 18 stencil neighbours are all tissue inside the array ("interior").
+enum : uint8_t { MASK_TISSUE = 1, MASK_INTERIOR = 2 };
 
 template <int MODEL, bool MASKED, bool ANISO, int TY>
 struct Plan {
     static constexpr int S = Model<MODEL>::S;
     static constexpr int TX = kTileX;
+    static constexpr int CY = kCY;
+    static constexpr int RY = TY / CY;  // thread rows
+    static constexpr int THREADS = TX * RY;
     static constexpr int UW = TX + 8;   // x from x0-4 to x0+TX+3 (16-byte aligned start)
     static constexpr int UH = TY + 2;   // y from y0-1 to y0+TY
     static constexpr int MW = TX + 32;  // mask bytes: x from x0-16 (16-byte aligned start)
@@ -318,42 +331,126 @@ struct Plan {
     static constexpr int M_OFF = F_OFF + align128(F_RAW);
     static constexpr int S_OFF = M_OFF + align128(M_RAW);
     static constexpr int STAGE = S_OFF + align128(S_RAW);
-    static constexpr uint32_t TX_BYTES = U_RAW + F_RAW + M_RAW + S_RAW;
-    static constexpr int NS_FIT = (200 * 1024) / STAGE;
-    static constexpr int NS = NS_FIT > 6 ? 6 : (NS_FIT < 4 ? 4 : NS_FIT);
+    static constexpr uint32_t TX_BYTES = U_RAW + F_RAW + M_RAW + S_RAW;  // plane computed in this brick
+    static constexpr uint32_t TX_BYTES_HALO = U_RAW + F_RAW + M_RAW;     // z-halo plane: no other vars
+    static constexpr int NS_FIT = (110 * 1024) / STAGE;
+    static constexpr int NS = NS_FIT > 8 ? 8 : (NS_FIT < 4 ? 4 : NS_FIT);
     static constexpr int SMEM = 128 + NS * STAGE + NS * 8;
-    static constexpr int THREADS = TX * TY;
+    static_assert(TY % CY == 0, "tile rows must be a multiple of the rows per thread");
 };
 
-struct Brick {
-    int x0, y0, z0, z1;
+struct F3 {
+    float x, y, z;
 };
 
-__device__ __forceinline__ Brick decode_brick(const StepArgs& a, int i) {
-    const int id = a.bricks ? a.bricks[i] : i;
-    const int bx = id % a.nbx;
-    const int r = id / a.nbx;
-    const int by = r % a.nby;
-    const int bz = r / a.nby;
-    Brick b;
-    b.x0 = bx * kTileX;
-    b.y0 = by;  // scaled by TY in the kernel
-    b.z0 = bz * a.zb;
-    b.z1 = min(b.z0 + a.zb, a.nz);
-    return b;
+// Neighbour values of one node: faces, then the 12 edges of the 19-point
+// stencil ("pm" = x+1,y-1 etc.).
+struct Nb {
+    float u0, xp, xm, yp, ym, zp, zm;
+    float pp, mm, pm, mp;          // (x,y) edges
+    float xpzp, xmzm, xpzm, xmzp;  // (x,z) edges
+    float ypzp, ymzm, ypzm, ymzp;  // (y,z) edges
+};
+
+// (L u)_p for a node whose 18 neighbours are all tissue: the weights of
+// Eq. (Lu) with psi = 1 everywhere, in difference form.  c_perp = Dperp/h^2,
+// c_d = (Dpar-Dperp)/h^2, c_dh = c_d/2, c_s = c_d/4.
+template <bool ANISO>
+__device__ __forceinline__ float lap_interior(const StepArgs& a, const Nb& n, F3 f, F3 fxp, F3 fxm, F3 fyp,
+                                              F3 fym, F3 fzp, F3 fzm) {
+    if (!ANISO) {
+        return a.c_iso * (((n.xp + n.xm) + (n.yp + n.ym)) + (n.zp + n.zm) - 6.0f * n.u0);
+    }
+    const float Dxx = fmaf(a.c_d, f.x * f.x, a.c_perp);
+    const float Dyy = fmaf(a.c_d, f.y * f.y, a.c_perp);
+    const float Dzz = fmaf(a.c_d, f.z * f.z, a.c_perp);
+    const float hx = a.c_dh * f.x;
+    const float Dxy = hx * f.y, Dxz = hx * f.z, Dyz = a.c_dh * f.y * f.z;
+    // S_k = sum_j (ff^T)_jk at p+q_j minus at p-q_j (the Dperp parts cancel)
+    float sx = fxp.x * fxp.x, sy = fxp.x * fxp.y, sz = fxp.x * fxp.z;
+    sx = fmaf(-fxm.x, fxm.x, sx); sy = fmaf(-fxm.x, fxm.y, sy); sz = fmaf(-fxm.x, fxm.z, sz);
+    sx = fmaf(fyp.y, fyp.x, sx); sy = fmaf(fyp.y, fyp.y, sy); sz = fmaf(fyp.y, fyp.z, sz);
+    sx = fmaf(-fym.y, fym.x, sx); sy = fmaf(-fym.y, fym.y, sy); sz = fmaf(-fym.y, fym.z, sz);
+    sx = fmaf(fzp.z, fzp.x, sx); sy = fmaf(fzp.z, fzp.y, sy); sz = fmaf(fzp.z, fzp.z, sz);
+    sx = fmaf(-fzm.z, fzm.x, sx); sy = fmaf(-fzm.z, fzm.y, sy); sz = fmaf(-fzm.z, fzm.z, sz);
+    const float two_u = 2.0f * n.u0;
+    float L = Dxx * ((n.xp + n.xm) - two_u);
+    L = fmaf(Dyy, (n.yp + n.ym) - two_u, L);
+    L = fmaf(Dzz, (n.zp + n.zm) - two_u, L);
+    float dv = sx * (n.xp - n.xm);
+    dv = fmaf(sy, n.yp - n.ym, dv);
+    dv = fmaf(sz, n.zp - n.zm, dv);
+    L = fmaf(a.c_s, dv, L);
+    L = fmaf(Dxy, (n.pp + n.mm) - (n.pm + n.mp), L);
+    L = fmaf(Dxz, (n.xpzp + n.xmzm) - (n.xpzm + n.xmzp), L);
+    L = fmaf(Dyz, (n.ypzp + n.ymzm) - (n.ypzm + n.ymzp), L);
+    return L;
 }
+
+// Grid indicator psi of the 18 neighbours (bit order: xp xm yp ym zp zm, then
+// pp mm pm mp, xpzp xmzm xpzm xmzp, ypzp ymzm ypzm ymzp).
+struct Psi {
+    bool xp, xm, yp, ym, zp, zm;
+    bool pp, mm, pm, mp;
+    bool xpzp, xmzm, xpzm, xmzp;
+    bool ypzp, ymzm, ypzm, ymzp;
+};
+
+// (L u)_p for any tissue node: every weight carries its psi (a void or
+// out-of-array neighbour contributes nothing) and, in Wtilde, a void
+// neighbour's tensor is replaced by D^p.
+template <bool ANISO>
+__device__ __forceinline__ float lap_general(const StepArgs& a, const Nb& n, const Psi& q, F3 f, F3 fxp, F3 fxm,
+                                             F3 fyp, F3 fym, F3 fzp, F3 fzm) {
+    auto d = [&](bool ps, float uq) { return ps ? (uq - n.u0) : 0.0f; };
+    const float exp_ = d(q.xp, n.xp), exm = d(q.xm, n.xm), eyp = d(q.yp, n.yp), eym = d(q.ym, n.ym);
+    const float ezp = d(q.zp, n.zp), ezm = d(q.zm, n.zm);
+    if (!ANISO) {
+        return a.c_iso * (((exp_ + exm) + (eyp + eym)) + (ezp + ezm));
+    }
+    const float Dxx = fmaf(a.c_d, f.x * f.x, a.c_perp);
+    const float Dyy = fmaf(a.c_d, f.y * f.y, a.c_perp);
+    const float Dzz = fmaf(a.c_d, f.z * f.z, a.c_perp);
+    const float hx = a.c_dh * f.x;
+    const float Dxy = hx * f.y, Dxz = hx * f.z, Dyz = a.c_dh * f.y * f.z;
+    if (!q.xp) fxp = f;
+    if (!q.xm) fxm = f;
+    if (!q.yp) fyp = f;
+    if (!q.ym) fym = f;
+    if (!q.zp) fzp = f;
+    if (!q.zm) fzm = f;
+    float sx = fxp.x * fxp.x, sy = fxp.x * fxp.y, sz = fxp.x * fxp.z;
+    sx = fmaf(-fxm.x, fxm.x, sx); sy = fmaf(-fxm.x, fxm.y, sy); sz = fmaf(-fxm.x, fxm.z, sz);
+    sx = fmaf(fyp.y, fyp.x, sx); sy = fmaf(fyp.y, fyp.y, sy); sz = fmaf(fyp.y, fyp.z, sz);
+    sx = fmaf(-fym.y, fym.x, sx); sy = fmaf(-fym.y, fym.y, sy); sz = fmaf(-fym.y, fym.z, sz);
+    sx = fmaf(fzp.z, fzp.x, sx); sy = fmaf(fzp.z, fzp.y, sy); sz = fmaf(fzp.z, fzp.z, sz);
+    sx = fmaf(-fzm.z, fzm.x, sx); sy = fmaf(-fzm.z, fzm.y, sy); sz = fmaf(-fzm.z, fzm.z, sz);
+    float L = Dxx * (exp_ + exm);
+    L = fmaf(Dyy, eyp + eym, L);
+    L = fmaf(Dzz, ezp + ezm, L);
+    float dv = (q.xp && q.xm) ? sx * (n.xp - n.xm) : 0.0f;
+    if (q.yp && q.ym) dv = fmaf(sy, n.yp - n.ym, dv);
+    if (q.zp && q.zm) dv = fmaf(sz, n.zp - n.zm, dv);
+    L = fmaf(a.c_s, dv, L);
+    L = fmaf(Dxy, (d(q.pp, n.pp) + d(q.mm, n.mm)) - (d(q.pm, n.pm) + d(q.mp, n.mp)), L);
+    L = fmaf(Dxz, (d(q.xpzp, n.xpzp) + d(q.xmzm, n.xmzm)) - (d(q.xpzm, n.xpzm) + d(q.xmzp, n.xmzp)), L);
+    L = fmaf(Dyz, (d(q.ypzp, n.ypzp) + d(q.ymzm, n.ymzm)) - (d(q.ypzm, n.ypzm) + d(q.ymzp, n.ymzp)), L);
+    return L;
+}
+
 
 // ---------------------------------------------------------------------------
 // the fused step kernel
 // ---------------------------------------------------------------------------
 
 template <int MODEL, bool MASKED, bool ANISO, int TY>
-__global__ void __launch_bounds__(kTileX * TY)
+__global__ void __launch_bounds__(kTileX * (TY / kCY))
 step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_s,
             const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ CUtensorMap tm_m,
             const StepArgs a) {
     using P = Plan<MODEL, MASKED, ANISO, TY>;
-    constexpr int S = P::S, TX = P::TX, UW = P::UW, MW = P::MW, NS = P::NS;
+    constexpr int S = P::S, TX = P::TX, UW = P::UW, MW = P::MW, NS = P::NS, CY = P::CY;
+    constexpr int FC = UW * P::UH;  // fibre component stride in a stage
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem =
@@ -362,7 +459,7 @@ step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CU
     __shared__ double red_scratch[32];
 
     const int tid = threadIdx.x;
-    const int tx = tid % TX, ty = tid / TX;
+    const int tx = tid % TX, row0 = (tid / TX) * CY;
 
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
@@ -375,33 +472,32 @@ step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CU
     __syncthreads();
 
     // ---- producer state (thread 0 only) ----
-    int p_iter = 0, p_off = 0, issued = 0;
+    const int piece_begin = a.cta_off[blockIdx.x], piece_end = a.cta_off[blockIdx.x + 1];
+    int p_piece = piece_begin, p_off = 0, issued = 0;
     auto issue_next = [&]() -> bool {
-        const int bi = blockIdx.x + p_iter * gridDim.x;
-        if (bi >= a.n_bricks) return false;
-        Brick b = decode_brick(a, bi);
-        const int y0 = b.y0 * TY;
-        const int nload = b.z1 - b.z0 + 2;
-        const int z = b.z0 - 1 + p_off;
+        if (p_piece >= piece_end) return false;
+        const int4 pc = a.pieces[p_piece];
+        const int nload = pc.w - pc.z + 2;
+        const int z = pc.z - 1 + p_off;
+        const bool halo = (p_off == 0) || (p_off == nload - 1);
         const int slot = issued % NS;
         uint64_t* bar = &bars[slot];
         unsigned char* st = smem + slot * P::STAGE;
         if (a.poison_first_load && blockIdx.x == 0 && issued == 0) {
-            // fault injection: expect bytes that no copy will deliver
-            mbar_arrive_expect_tx(bar, 16);
+            mbar_arrive_expect_tx(bar, 16);  // fault injection: bytes no copy delivers
         } else if (z < 0 || z >= a.nz) {
             mbar_arrive(bar);  // plane outside the array: nothing to load
         } else {
-            mbar_arrive_expect_tx(bar, P::TX_BYTES);
-            tma_load_3d(st + P::U_OFF, &tm_u, b.x0 - 4, y0 - 1, z, bar);
-            if (ANISO) tma_load_4d(st + P::F_OFF, &tm_f, b.x0 - 4, y0 - 1, z, 0, bar);
-            if (MASKED) tma_load_3d(st + P::M_OFF, &tm_m, b.x0 - 16, y0 - 1, z, bar);
-            if (S > 1) tma_load_4d(st + P::S_OFF, &tm_s, b.x0, y0, z, 1, bar);
+            mbar_arrive_expect_tx(bar, (halo || S == 1) ? P::TX_BYTES_HALO : P::TX_BYTES);
+            tma_load_3d(st + P::U_OFF, &tm_u, pc.x - 4, pc.y - 1, z, bar);
+            if (ANISO) tma_load_4d(st + P::F_OFF, &tm_f, pc.x - 4, pc.y - 1, z, 0, bar);
+            if (MASKED) tma_load_3d(st + P::M_OFF, &tm_m, pc.x - 16, pc.y - 1, z, bar);
+            if (S > 1 && !halo) tma_load_4d(st + P::S_OFF, &tm_s, pc.x, pc.y, z, 1, bar);
         }
         ++issued;
         if (++p_off == nload) {
             p_off = 0;
-            ++p_iter;
+            ++p_piece;
         }
         return true;
     };
@@ -416,14 +512,16 @@ step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CU
     int jb = 0;  // load index of the first plane of the current brick
     const float theta = a.theta;
 
-    for (int it = 0;; ++it) {
-        const int bi = blockIdx.x + it * gridDim.x;
-        if (bi >= a.n_bricks) break;
-        const Brick b = decode_brick(a, bi);
-        const int y0 = b.y0 * TY;
-        const int x = b.x0 + tx, y = y0 + ty;
-        const bool in_xy = (x < a.nx) && (y < a.ny);
-        const int ncomp = b.z1 - b.z0;
+    float mp[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) mp[i] = a.mp[i];
+
+    for (int pi = piece_begin; pi < piece_end; ++pi) {
+        const int4 pc = a.pieces[pi];
+        const int x = pc.x + tx;
+        const int yb = pc.y + row0;  // y of this thread's first node
+        const bool x_in = x < a.nx;
+        const int ncomp = pc.w - pc.z;
 
         for (int w = 0; w < 2; ++w) {
             const int j = jb + w;
@@ -434,127 +532,130 @@ step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CU
                 const int j = jb + t + 2;
                 if (!mbar_wait_bounded(&bars[j % NS], (j / NS) & 1, a.wait_limit)) timed_out = true;
             }
-            const int k = b.z0 + t;
+            const int k = pc.z + t;
             const unsigned char* stp = smem + ((jb + t) % NS) * P::STAGE;
             const unsigned char* stc = smem + ((jb + t + 1) % NS) * P::STAGE;
             const unsigned char* stn = smem + ((jb + t + 2) % NS) * P::STAGE;
             const float* Up = reinterpret_cast<const float*>(stp + P::U_OFF);
             const float* Uc = reinterpret_cast<const float*>(stc + P::U_OFF);
             const float* Un = reinterpret_cast<const float*>(stn + P::U_OFF);
-            const int c = (ty + 1) * UW + (tx + 4);
-            const bool zp_ok = k > 0, zn_ok = k + 1 < a.nz;
+            const float* Fp = reinterpret_cast<const float*>(stp + P::F_OFF);
+            const float* Fc = reinterpret_cast<const float*>(stc + P::F_OFF);
+            const float* Fn = reinterpret_cast<const float*>(stn + P::F_OFF);
+            const unsigned char* Mp = stp + P::M_OFF;
+            const unsigned char* Mc = stc + P::M_OFF;
+            const unsigned char* Mn = stn + P::M_OFF;
+            const float* Sv = reinterpret_cast<const float*>(stc + P::S_OFF);
+            const bool zn_ok = k + 1 < a.nz, zp_ok = k > 0;
+            const int c0 = (row0 + 1) * UW + (tx + 4);   // stage index of node (x, yb)
+            const int m0 = (row0 + 1) * MW + (tx + 16);  // mask index of node (x, yb)
 
-            // psi of the 18 neighbours
-            bool ps_c, ps_xp, ps_xm, ps_yp, ps_ym, ps_zp, ps_zm;
-            bool ps_pp, ps_mm, ps_pm, ps_mp;        // (x,y) edges in plane k
-            bool ps_xpzp, ps_xmzm, ps_xpzm, ps_xmzp;  // (x,z) edges
-            bool ps_ypzp, ps_ymzm, ps_ypzm, ps_ymzp;  // (y,z) edges
-            if (MASKED) {
-                const unsigned char* Mp = stp + P::M_OFF;
-                const unsigned char* Mc = stc + P::M_OFF;
-                const unsigned char* Mn = stn + P::M_OFF;
-                const int m = (ty + 1) * MW + (tx + 16);
-                ps_c = Mc[m] != 0;
-                ps_xp = Mc[m + 1] != 0;
-                ps_xm = Mc[m - 1] != 0;
-                ps_yp = Mc[m + MW] != 0;
-                ps_ym = Mc[m - MW] != 0;
-                ps_zp = zn_ok && Mn[m] != 0;
-                ps_zm = zp_ok && Mp[m] != 0;
-                ps_pp = Mc[m + MW + 1] != 0;
-                ps_mm = Mc[m - MW - 1] != 0;
-                ps_pm = Mc[m - MW + 1] != 0;
-                ps_mp = Mc[m + MW - 1] != 0;
-                ps_xpzp = zn_ok && Mn[m + 1] != 0;
-                ps_xmzm = zp_ok && Mp[m - 1] != 0;
-                ps_xpzm = zp_ok && Mp[m + 1] != 0;
-                ps_xmzp = zn_ok && Mn[m - 1] != 0;
-                ps_ypzp = zn_ok && Mn[m + MW] != 0;
-                ps_ymzm = zp_ok && Mp[m - MW] != 0;
-                ps_ypzm = zp_ok && Mp[m + MW] != 0;
-                ps_ymzp = zn_ok && Mn[m - MW] != 0;
-            } else {
-                const bool xp = x + 1 < a.nx, xm = x > 0, yp = y + 1 < a.ny, ym = y > 0;
-                ps_c = true;
-                ps_xp = xp; ps_xm = xm; ps_yp = yp; ps_ym = ym;
-                ps_zp = zn_ok; ps_zm = zp_ok;
-                ps_pp = xp && yp; ps_mm = xm && ym; ps_pm = xp && ym; ps_mp = xm && yp;
-                ps_xpzp = xp && zn_ok; ps_xmzm = xm && zp_ok; ps_xpzm = xp && zp_ok; ps_xmzp = xm && zn_ok;
-                ps_ypzp = yp && zn_ok; ps_ymzm = ym && zp_ok; ps_ypzm = yp && zp_ok; ps_ymzp = ym && zn_ok;
-            }
-
-            if (in_xy && ps_c) {
-                const float up = Uc[c];
-                auto dlt = [&](bool ps, float uq) { return ps ? (uq - up) : 0.0f; };
-                const float e_xp = dlt(ps_xp, Uc[c + 1]), e_xm = dlt(ps_xm, Uc[c - 1]);
-                const float e_yp = dlt(ps_yp, Uc[c + UW]), e_ym = dlt(ps_ym, Uc[c - UW]);
-                const float e_zp = dlt(ps_zp, Un[c]), e_zm = dlt(ps_zm, Up[c]);
-                float L;
-                if (ANISO) {
-                    const float* Fp = reinterpret_cast<const float*>(stp + P::F_OFF);
-                    const float* Fc = reinterpret_cast<const float*>(stc + P::F_OFF);
-                    const float* Fn = reinterpret_cast<const float*>(stn + P::F_OFF);
-                    constexpr int FC = UW * P::UH;  // component stride
-                    const float fx = Fc[c], fy = Fc[c + FC], fz = Fc[c + 2 * FC];
-                    const float dD = a.dD, Dperp = a.Dperp;
-                    const float Dxx = Dperp + dD * fx * fx, Dyy = Dperp + dD * fy * fy, Dzz = Dperp + dD * fz * fz;
-                    const float Dxy = dD * fx * fy, Dxz = dD * fx * fz, Dyz = dD * fy * fz;
-                    // S_k = sum_j (D^{p+q_j}_jk - D^{p-q_j}_jk); a void neighbour
-                    // takes D^p.  The Dperp delta_jk parts cancel.
-                    float Sx = 0.f, Sy = 0.f, Sz = 0.f;
-                    auto acc_nb = [&](bool ps, const float* F, int off, int jdir, float sgn) {
-                        float gx = fx, gy = fy, gz = fz;
-                        if (ps) {
-                            gx = F[off];
-                            gy = F[off + FC];
-                            gz = F[off + 2 * FC];
+            if (x_in) {
+                auto fib = [&](const float* F, int o) { return F3{F[o], F[o + FC], F[o + 2 * FC]}; };
+                // phase 1: the stencil for the CY nodes of this thread.  Shared
+                // loads slide down the column: rows r-1, r, r+1 of the own, left
+                // and right columns of plane k, and of the own column of planes
+                // k+-1 (and the fibres of the own column), live in registers;
+                // each row is read once.
+                float Lr[CY], u0r[CY];
+                bool live[CY];
+                float wC[3], wL[3], wR[3], wN[3], wP[3];
+                F3 wF[3];
+                {
+#pragma unroll
+                    for (int w = 0; w < 2; ++w) {
+                        const int o = c0 + (w - 1) * UW;
+                        wC[w] = Uc[o]; wL[w] = Uc[o - 1]; wR[w] = Uc[o + 1];
+                        wN[w] = Un[o]; wP[w] = Up[o];
+                        if (ANISO) wF[w] = fib(Fc, o);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < CY; ++r) {
+                    const int y = yb + r;
+                    const int c = c0 + r * UW;
+                    const int m = m0 + r * MW;
+                    {
+                        const int o = c + UW;  // row r+1
+                        wC[2] = Uc[o]; wL[2] = Uc[o - 1]; wR[2] = Uc[o + 1];
+                        wN[2] = Un[o]; wP[2] = Up[o];
+                        if (ANISO) wF[2] = fib(Fc, o);
+                    }
+                    bool tissue = y < a.ny, interior;
+                    if (MASKED) {
+                        const unsigned char mc = Mc[m];
+                        tissue = tissue && (mc & MASK_TISSUE) != 0;
+                        interior = (mc & MASK_INTERIOR) != 0;
+                    } else {
+                        interior = (x > 0) && (x + 1 < a.nx) && (y > 0) && (y + 1 < a.ny) && zp_ok && zn_ok;
+                    }
+                    live[r] = tissue;
+                    u0r[r] = wC[1];
+                    Lr[r] = 0.0f;
+                    Nb n;
+                    n.u0 = wC[1];
+                    n.xp = wR[1]; n.xm = wL[1]; n.yp = wC[2]; n.ym = wC[0];
+                    n.zp = wN[1]; n.zm = wP[1];
+                    F3 f = {0.f, 0.f, 0.f}, fxp = f, fxm = f, fyp = f, fym = f, fzp = f, fzm = f;
+                    if (ANISO) {
+                        n.pp = wR[2]; n.mm = wL[0]; n.pm = wR[0]; n.mp = wL[2];
+                        n.xpzp = Un[c + 1]; n.xmzm = Up[c - 1]; n.xpzm = Up[c + 1]; n.xmzp = Un[c - 1];
+                        n.ypzp = wN[2]; n.ymzm = wP[0]; n.ypzm = wP[2]; n.ymzp = wN[0];
+                        f = wF[1];
+                        fxp = fib(Fc, c + 1); fxm = fib(Fc, c - 1);
+                        fyp = wF[2]; fym = wF[0];
+                        fzp = fib(Fn, c); fzm = fib(Fp, c);
+                    }
+                    if (tissue) {
+                        if (interior) {
+                            Lr[r] = lap_interior<ANISO>(a, n, f, fxp, fxm, fyp, fym, fzp, fzm);
+                        } else {
+                            Psi q;
+                            if (MASKED) {
+                                q.xp = Mc[m + 1] != 0; q.xm = Mc[m - 1] != 0;
+                                q.yp = Mc[m + MW] != 0; q.ym = Mc[m - MW] != 0;
+                                q.zp = zn_ok && Mn[m] != 0; q.zm = zp_ok && Mp[m] != 0;
+                                q.pp = Mc[m + MW + 1] != 0; q.mm = Mc[m - MW - 1] != 0;
+                                q.pm = Mc[m - MW + 1] != 0; q.mp = Mc[m + MW - 1] != 0;
+                                q.xpzp = zn_ok && Mn[m + 1] != 0; q.xmzm = zp_ok && Mp[m - 1] != 0;
+                                q.xpzm = zp_ok && Mp[m + 1] != 0; q.xmzp = zn_ok && Mn[m - 1] != 0;
+                                q.ypzp = zn_ok && Mn[m + MW] != 0; q.ymzm = zp_ok && Mp[m - MW] != 0;
+                                q.ypzm = zp_ok && Mp[m + MW] != 0; q.ymzp = zn_ok && Mn[m - MW] != 0;
+                            } else {
+                                const bool xp = x + 1 < a.nx, xm = x > 0, yp = y + 1 < a.ny, ym = y > 0;
+                                q.xp = xp; q.xm = xm; q.yp = yp; q.ym = ym; q.zp = zn_ok; q.zm = zp_ok;
+                                q.pp = xp && yp; q.mm = xm && ym; q.pm = xp && ym; q.mp = xm && yp;
+                                q.xpzp = xp && zn_ok; q.xmzm = xm && zp_ok; q.xpzm = xp && zp_ok; q.xmzp = xm && zn_ok;
+                                q.ypzp = yp && zn_ok; q.ymzm = ym && zp_ok; q.ypzm = yp && zp_ok; q.ymzp = ym && zn_ok;
+                            }
+                            Lr[r] = lap_general<ANISO>(a, n, q, f, fxp, fxm, fyp, fym, fzp, fzm);
                         }
-                        const float gj = (jdir == 0) ? gx : ((jdir == 1) ? gy : gz);
-                        const float s = sgn * gj;
-                        Sx += s * gx;
-                        Sy += s * gy;
-                        Sz += s * gz;
-                    };
-                    acc_nb(ps_xp, Fc, c + 1, 0, 1.f);
-                    acc_nb(ps_xm, Fc, c - 1, 0, -1.f);
-                    acc_nb(ps_yp, Fc, c + UW, 1, 1.f);
-                    acc_nb(ps_ym, Fc, c - UW, 1, -1.f);
-                    acc_nb(ps_zp, Fn, c, 2, 1.f);
-                    acc_nb(ps_zm, Fp, c, 2, -1.f);
-                    Sx *= dD; Sy *= dD; Sz *= dD;
-                    const float faces = Dxx * (e_xp + e_xm) + Dyy * (e_yp + e_ym) + Dzz * (e_zp + e_zm);
-                    const float divt = 0.25f * ((ps_xp && ps_xm ? Sx * (Uc[c + 1] - Uc[c - 1]) : 0.f) +
-                                                (ps_yp && ps_ym ? Sy * (Uc[c + UW] - Uc[c - UW]) : 0.f) +
-                                                (ps_zp && ps_zm ? Sz * (Un[c] - Up[c]) : 0.f));
-                    const float exy = dlt(ps_pp, Uc[c + UW + 1]) + dlt(ps_mm, Uc[c - UW - 1]) -
-                                      dlt(ps_pm, Uc[c - UW + 1]) - dlt(ps_mp, Uc[c + UW - 1]);
-                    const float exz = dlt(ps_xpzp, Un[c + 1]) + dlt(ps_xmzm, Up[c - 1]) -
-                                      dlt(ps_xpzm, Up[c + 1]) - dlt(ps_xmzp, Un[c - 1]);
-                    const float eyz = dlt(ps_ypzp, Un[c + UW]) + dlt(ps_ymzm, Up[c - UW]) -
-                                      dlt(ps_ypzm, Up[c + UW]) - dlt(ps_ymzp, Un[c - UW]);
-                    const float edges = 0.5f * (Dxy * exy + Dxz * exz + Dyz * eyz);
-                    L = a.inv_h2 * (faces + divt + edges);
-                } else {
-                    L = a.Diso * a.inv_h2 * ((e_xp + e_xm) + (e_yp + e_ym) + (e_zp + e_zm));
+                    }
+                    // slide the window down one row
+                    wC[0] = wC[1]; wC[1] = wC[2]; wL[0] = wL[1]; wL[1] = wL[2]; wR[0] = wR[1]; wR[1] = wR[2];
+                    wN[0] = wN[1]; wN[1] = wN[2]; wP[0] = wP[1]; wP[1] = wP[2];
+                    if (ANISO) { wF[0] = wF[1]; wF[1] = wF[2]; }
                 }
-
-                float yv[S];
-                yv[0] = up;
-                if (S > 1) {
-                    const float* Sv = reinterpret_cast<const float*>(stc + P::S_OFF);
+                // phase 2: reaction, stores, activation, tissue sum
 #pragma unroll
-                    for (int v = 1; v < S; ++v) yv[v] = Sv[(v - 1) * TX * TY + ty * TX + tx];
-                }
-                const long long gi = (long long)k * a.plane + (long long)y * a.px + x;
-                float Is = 0.0f;
-                if (a.stim_amp != 0.0f && a.stim[gi]) Is = a.stim_amp;
-                Model<MODEL>::update(a.mp, yv, L, Is, a.dt);
+                for (int r = 0; r < CY; ++r) {
+                    if (!live[r]) continue;
+                    const int y = yb + r;
+                    float yv[S];
+                    yv[0] = u0r[r];
 #pragma unroll
-                for (int v = 0; v < S; ++v) a.dst[(long long)v * a.vol + gi] = yv[v];
-                if (up < theta && theta <= yv[0]) {
-                    if (a.act[gi] == BBX_ACT_NONE) a.act[gi] = a.step_next;
+                    for (int v = 1; v < S; ++v) yv[v] = Sv[(v - 1) * TX * TY + (row0 + r) * TX + tx];
+                    const long long gi = (long long)k * a.plane + (long long)y * a.px + x;
+                    float Is = 0.0f;
+                    if (a.stim_amp != 0.0f && a.stim[gi]) Is = a.stim_amp;
+                    Model<MODEL>::update(mp, yv, Lr[r], Is, a.dt);
+#pragma unroll
+                    for (int v = 0; v < S; ++v) a.dst[(long long)v * a.vol + gi] = yv[v];
+                    if (u0r[r] < theta && theta <= yv[0]) {
+                        if (a.act[gi] == BBX_ACT_NONE) a.act[gi] = a.step_next;
+                    }
+                    two_sum_add(vsum, yv[0]);
                 }
-                two_sum_add(vsum, yv[0]);
             }
 
             abort = __syncthreads_or(timed_out);

@@ -3,6 +3,7 @@
 // double-precision tissue reduction.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -139,6 +140,36 @@ __global__ void k_fibres(const float* __restrict__ in, int nx, int ny, int nz, i
         out[gi] = ox;
         out[vol + gi] = oy;
         out[2 * vol + gi] = oz;
+    }
+}
+
+// Device mask byte: bit 0 tissue, bit 1 set when all 18 neighbours of the
+// 19-point stencil (faces and edges) are tissue nodes inside the array.
+__global__ void k_mask_interior(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, int nx, int ny, int nz,
+                                int px, long long plane) {
+    const long long n = (long long)nx * ny * nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = int(i % nx);
+        const long long r = i / nx;
+        const int y = int(r % ny);
+        const int z = int(r / ny);
+        const long long gi = z * plane + (long long)y * px + x;
+        uint8_t m = in[gi] ? MASK_TISSUE : 0;
+        if (m) {
+            bool all = true;
+            for (int dz = -1; dz <= 1 && all; ++dz)
+                for (int dy = -1; dy <= 1 && all; ++dy)
+                    for (int dx = -1; dx <= 1 && all; ++dx) {
+                        const int nnz = (dx != 0) + (dy != 0) + (dz != 0);
+                        if (nnz == 0 || nnz == 3) continue;
+                        const int X = x + dx, Y = y + dy, Z = z + dz;
+                        if (X < 0 || Y < 0 || Z < 0 || X >= nx || Y >= ny || Z >= nz) all = false;
+                        else if (!in[Z * plane + (long long)Y * px + X]) all = false;
+                    }
+            if (all) m |= MASK_INTERIOR;
+        }
+        out[gi] = m;
     }
 }
 
@@ -299,6 +330,11 @@ struct bbx_grid {
     int nbx = 0, nby = 0, nbz = 0;
     int* d_bricks = nullptr;
     long long n_bricks = 0;
+    std::vector<int> h_bricks;      // host copy of the active brick ids (masked grids)
+    int4* d_pieces = nullptr;       // balanced per-CTA work schedule
+    int* d_cta_off = nullptr;
+    size_t pieces_cap = 0, off_cap = 0;
+    long long n_planes = 0;         // column-planes in the schedule
 
     double* d_partials = nullptr;
     unsigned int* d_ticket = nullptr;
@@ -365,6 +401,86 @@ int build_bricks(bbx_grid* g) {
     cudaFree(d_count);
     if (e != cudaSuccess) return BBX_ERR_CUDA;
     g->n_bricks = cnt;
+    g->h_bricks.resize((size_t)cnt);
+    if (cnt > 0) {
+        if (cudaMemcpy(g->h_bricks.data(), g->d_bricks, sizeof(int) * cnt, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return BBX_ERR_CUDA;
+    }
+    return BBX_OK;
+}
+
+// Balanced work schedule for `ctas` CTAs: the active columns (64 x TY nodes
+// in x, y) with their active z-runs are concatenated column by column, and
+// each CTA receives an equal share of the column-planes as contiguous pieces,
+// so no CTA idles while others finish a last brick.
+int build_schedule(bbx_grid* g, int ctas) {
+    struct Seg {
+        int x0, y0, z0, z1;
+    };
+    std::vector<Seg> segs;
+    if (!g->d_mask) {
+        for (int by = 0; by < g->nby; ++by)
+            for (int bx = 0; bx < g->nbx; ++bx) segs.push_back({bx * kTileX, by * g->ty, 0, g->nz});
+    } else {
+        // brick ids are bx + nbx*(by + nby*bz); regroup by column, z ascending
+        const long long ncol = (long long)g->nbx * g->nby;
+        std::vector<std::vector<int>> col((size_t)ncol);
+        for (int id : g->h_bricks) col[(size_t)(id % ncol)].push_back((int)(id / ncol));
+        for (long long cidx = 0; cidx < ncol; ++cidx) {
+            const std::vector<int>& zs = col[(size_t)cidx];
+            const int bx = (int)(cidx % g->nbx), by = (int)(cidx / g->nbx);
+            size_t i = 0;
+            while (i < zs.size()) {
+                size_t j = i;
+                while (j + 1 < zs.size() && zs[j + 1] == zs[j] + 1) ++j;
+                segs.push_back({bx * kTileX, by * g->ty, zs[i] * g->zb, std::min((zs[j] + 1) * g->zb, g->nz)});
+                i = j + 1;
+            }
+        }
+    }
+    long long T = 0;
+    for (const Seg& sg : segs) T += sg.z1 - sg.z0;
+    g->n_planes = T;
+    if (T == 0) return BBX_OK;
+    if (ctas > T) ctas = (int)T;
+    std::vector<int4> pieces;
+    std::vector<int> off((size_t)ctas + 1, 0);
+    size_t si = 0;
+    long long consumed = 0;  // planes of segs[si] already handed out
+    for (int c = 0; c < ctas; ++c) {
+        off[c] = (int)pieces.size();
+        long long need = (long long)(c + 1) * T / ctas - (long long)c * T / ctas;
+        while (need > 0 && si < segs.size()) {
+            const Seg& sg = segs[si];
+            const long long avail = (sg.z1 - sg.z0) - consumed;
+            const long long take = std::min(avail, need);
+            const int z0 = sg.z0 + (int)consumed;
+            pieces.push_back(make_int4(sg.x0, sg.y0, z0, z0 + (int)take));
+            need -= take;
+            consumed += take;
+            if (consumed == sg.z1 - sg.z0) {
+                ++si;
+                consumed = 0;
+            }
+        }
+    }
+    off[ctas] = (int)pieces.size();
+    if (pieces.size() > g->pieces_cap) {
+        cudaFree(g->d_pieces);
+        g->d_pieces = nullptr;
+        if (dmalloc(&g->d_pieces, sizeof(int4) * pieces.size()) != cudaSuccess) return BBX_ERR_NOMEM;
+        g->pieces_cap = pieces.size();
+    }
+    if (off.size() > g->off_cap) {
+        cudaFree(g->d_cta_off);
+        g->d_cta_off = nullptr;
+        if (dmalloc(&g->d_cta_off, sizeof(int) * off.size()) != cudaSuccess) return BBX_ERR_NOMEM;
+        g->off_cap = off.size();
+    }
+    if (cudaMemcpy(g->d_pieces, pieces.data(), sizeof(int4) * pieces.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g->d_cta_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return BBX_ERR_CUDA;
+    g->grid_ctas = ctas;
     return BBX_OK;
 }
 
@@ -383,10 +499,12 @@ int prepare(bbx_grid* g) {
         return BBX_ERR_UNSUPPORTED;
     long long ctas = (long long)per_sm * g->num_sms;
     if (ctas > kMaxPartials) ctas = kMaxPartials;
-    if (ctas > g->n_bricks) ctas = g->n_bricks;
-    if (ctas < 1) ctas = 1;
-    g->grid_ctas = (int)ctas;
+    g->grid_ctas = 1;
     g->kern = k;
+    {
+        int rc = build_schedule(g, (int)ctas);
+        if (rc) return rc;
+    }
 
     const int ty = g->ty;
     const cuuint64_t fdims3[3] = {(cuuint64_t)g->nx, (cuuint64_t)g->ny, (cuuint64_t)g->nz};
@@ -482,6 +600,8 @@ void bbx_destroy_grid(bbx_grid* g) {
     cudaFree(g->d_mp);
     cudaFree(g->d_stim);
     cudaFree(g->d_bricks);
+    cudaFree(g->d_pieces);
+    cudaFree(g->d_cta_off);
     cudaFree(g->d_partials);
     cudaFree(g->d_ticket);
     cudaFree(g->d_total);
@@ -546,8 +666,23 @@ int bbx_create_grid(bbx_grid** out, int nx, int ny, int nz, double h, const uint
             // store 0/1 exactly
             std::vector<uint8_t> m01(ncell);
             for (long long i = 0; i < ncell; ++i) m01[i] = mask_host[i] ? 1 : 0;
-            if ((rc = copy_in(g, g->d_mask, m01.data(), 1)) != BBX_OK) break;
-            if (cudaStreamSynchronize(g->stream) != cudaSuccess) {
+            uint8_t* tmp = nullptr;
+            if (dmalloc(&tmp, (size_t)g->vol) != cudaSuccess) {
+                rc = BBX_ERR_NOMEM;
+                break;
+            }
+            if (cudaMemsetAsync(tmp, 0, (size_t)g->vol, g->stream) != cudaSuccess ||
+                (rc = copy_in(g, tmp, m01.data(), 1)) != BBX_OK) {
+                cudaFree(tmp);
+                if (rc == BBX_OK) rc = BBX_ERR_CUDA;
+                break;
+            }
+            k_mask_interior<<<n_blocks_for(ncell, 256), 256, 0, g->stream>>>(tmp, g->d_mask, nx, ny, nz, g->px,
+                                                                             g->plane);
+            const cudaError_t e1 = cudaGetLastError();
+            const cudaError_t e2 = cudaStreamSynchronize(g->stream);
+            cudaFree(tmp);
+            if (e1 != cudaSuccess || e2 != cudaSuccess) {
                 rc = BBX_ERR_CUDA;
                 break;
             }
@@ -749,7 +884,7 @@ int bbx_step(bbx_grid* g, double dt, int n_steps) {
         int rc = prepare(g);
         if (rc) return rc;
     }
-    if (g->n_bricks == 0) {
+    if (g->n_bricks == 0 || g->n_planes == 0) {
         // no tissue: nothing moves, only time advances
         g->t += dt * n_steps;
         g->n += n_steps;
@@ -767,19 +902,21 @@ int bbx_step(bbx_grid* g, double dt, int n_steps) {
     a.px = g->px;
     a.plane = g->plane;
     a.vol = g->vol;
-    a.nbx = g->nbx;
-    a.nby = g->nby;
-    a.zb = g->zb;
-    a.bricks = g->d_bricks;
-    a.n_bricks = (int)g->n_bricks;
+    a.pieces = g->d_pieces;
+    a.cta_off = g->d_cta_off;
     a.act = g->d_act;
     a.theta = (float)g->theta;
     a.stim = g->d_stim;
     a.dt = (float)dt;
-    a.inv_h2 = (float)(1.0 / (g->h * g->h));
-    a.Dperp = (float)g->Dperp;
-    a.dD = (float)(g->Dpar - g->Dperp);
-    a.Diso = (float)g->Dpar;
+    {
+        const double ih2 = 1.0 / (g->h * g->h);
+        const double cd = (g->Dpar - g->Dperp) * ih2;
+        a.c_perp = (float)(g->Dperp * ih2);
+        a.c_d = (float)cd;
+        a.c_dh = (float)(0.5 * cd);
+        a.c_s = (float)(0.25 * cd);
+        a.c_iso = (float)(g->Dpar * ih2);
+    }
     model_kernel_params(g->model, g->par, a.mp);
     a.partials = g->d_partials;
     a.ticket = g->d_ticket;
@@ -941,8 +1078,8 @@ int bbx_autotune(bbx_grid* g, double dt, double* best_ms) {
     cudaEventCreate(&e1);
     const int tys[3] = {4, 8, 16};
     std::vector<int> zbs;
-    if (g->nz == 1) {
-        zbs.push_back(1);
+    if (g->nz == 1 || !g->d_mask) {
+        zbs.push_back(g->zb);  // unmasked columns are marched whole; only the tile rows matter
     } else {
         for (int z : {4, 8, 16, 32, 64})
             if (z <= g->nz) zbs.push_back(z);

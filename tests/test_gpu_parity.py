@@ -320,7 +320,7 @@ def test_full_size_slab_one_step_sampled(bbx):
     edge[:, 1:, :] |= reg[:, 1:, :] != reg[:, :-1, :]
     edge[1:, :, :] |= reg[1:, :, :] != reg[:-1, :, :]
     cand = np.flatnonzero(edge)
-    cells = np.concatenate([rng.choice(cand, 1500, replace=False), rng.integers(0, w.n_cells, 500)])
+    cells = np.concatenate([rng.choice(cand, min(1500, cand.size), replace=False), rng.integers(0, w.n_cells, 500)])
     og = oracle.Grid(w.nx, w.ny, w.nz, w.h, w.mask, w.fibres, w.D_par, w.D_perp)
     osim = oracle.Sim(og, w.model, par=w.params, theta=w.theta, state=st0.astype(np.float64))
     ref = osim.step_cells(w.dt, cells)
