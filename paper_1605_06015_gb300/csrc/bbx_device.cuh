@@ -166,10 +166,12 @@ __device__ __forceinline__ double block_sum_double(double v, double* scratch32) 
     return s;
 }
 
-// Per-CTA partial -> deterministic grid total by the last CTA to finish.
+// Per-CTA partial -> deterministic grid total by the last CTA to finish.  The
+// last CTA sums the partials with all its threads (fixed strided order, then
+// a fixed tree), so the result does not depend on which CTA finished last.
 __device__ __forceinline__ void grid_total_finalize(double block_partial, double* partials,
                                                     unsigned int* ticket, double* out, int* err,
-                                                    bool flag_nonfinite) {
+                                                    bool flag_nonfinite, double* scratch32) {
     __shared__ bool last;
     if (threadIdx.x == 0) {
         partials[blockIdx.x] = block_partial;
@@ -179,11 +181,14 @@ __device__ __forceinline__ void grid_total_finalize(double block_partial, double
         last = (t == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        double s = 0.0;
-        for (unsigned int b = 0; b < gridDim.x; ++b) s += ((volatile double*)partials)[b];
-        *out = s;
+    if (!last) return;
+    __threadfence();
+    double s = 0.0;
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += __ldcg(&partials[b]);
+    __syncthreads();  // scratch32 may still be read by the caller's block sum
+    const double total = block_sum_double(s, scratch32);
+    if (threadIdx.x == 0) {
+        *out = total;
         *ticket = 0u;
     }
 }
@@ -387,6 +392,43 @@ __device__ __forceinline__ float lap_interior(const StepArgs& a, const Nb& n, F3
     return L;
 }
 
+// (L u)_p for a node of an unmasked grid whose y and z neighbours are inside
+// the array; px, mx in {0, 1} are psi of the x+1 and x-1 neighbours (0 only
+// at the array's x faces).  Out-of-array fibres read as the node's own (the
+// fibre field is stored with a clamped x-padding), which is the replacement
+// of a void neighbour's tensor by D^p.
+template <bool ANISO>
+__device__ __forceinline__ float lap_xbound(const StepArgs& a, const Nb& n, float px, float mx, F3 f, F3 fxp,
+                                            F3 fxm, F3 fyp, F3 fym, F3 fzp, F3 fzm) {
+    const float ex = px * (n.xp - n.u0) + mx * (n.xm - n.u0);
+    if (!ANISO) {
+        return a.c_iso * ((ex + (n.yp + n.ym)) + (n.zp + n.zm) - 4.0f * n.u0);
+    }
+    const float Dxx = fmaf(a.c_d, f.x * f.x, a.c_perp);
+    const float Dyy = fmaf(a.c_d, f.y * f.y, a.c_perp);
+    const float Dzz = fmaf(a.c_d, f.z * f.z, a.c_perp);
+    const float hx = a.c_dh * f.x;
+    const float Dxy = hx * f.y, Dxz = hx * f.z, Dyz = a.c_dh * f.y * f.z;
+    float sx = fxp.x * fxp.x, sy = fxp.x * fxp.y, sz = fxp.x * fxp.z;
+    sx = fmaf(-fxm.x, fxm.x, sx); sy = fmaf(-fxm.x, fxm.y, sy); sz = fmaf(-fxm.x, fxm.z, sz);
+    sx = fmaf(fyp.y, fyp.x, sx); sy = fmaf(fyp.y, fyp.y, sy); sz = fmaf(fyp.y, fyp.z, sz);
+    sx = fmaf(-fym.y, fym.x, sx); sy = fmaf(-fym.y, fym.y, sy); sz = fmaf(-fym.y, fym.z, sz);
+    sx = fmaf(fzp.z, fzp.x, sx); sy = fmaf(fzp.z, fzp.y, sy); sz = fmaf(fzp.z, fzp.z, sz);
+    sx = fmaf(-fzm.z, fzm.x, sx); sy = fmaf(-fzm.z, fzm.y, sy); sz = fmaf(-fzm.z, fzm.z, sz);
+    const float two_u = 2.0f * n.u0;
+    float L = Dxx * ex;
+    L = fmaf(Dyy, (n.yp + n.ym) - two_u, L);
+    L = fmaf(Dzz, (n.zp + n.zm) - two_u, L);
+    float dv = (px * mx) * sx * (n.xp - n.xm);
+    dv = fmaf(sy, n.yp - n.ym, dv);
+    dv = fmaf(sz, n.zp - n.zm, dv);
+    L = fmaf(a.c_s, dv, L);
+    L = fmaf(Dxy, px * (n.pp - n.pm) + mx * (n.mm - n.mp), L);
+    L = fmaf(Dxz, px * (n.xpzp - n.xpzm) + mx * (n.xmzm - n.xmzp), L);
+    L = fmaf(Dyz, (n.ypzp + n.ymzm) - (n.ypzm + n.ymzp), L);
+    return L;
+}
+
 // Grid indicator psi of the 18 neighbours (bit order: xp xm yp ym zp zm, then
 // pp mm pm mp, xpzp xmzm xpzm xmzp, ypzp ymzm ypzm ymzp).
 struct Psi {
@@ -490,7 +532,7 @@ step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CU
         } else {
             mbar_arrive_expect_tx(bar, (halo || S == 1) ? P::TX_BYTES_HALO : P::TX_BYTES);
             tma_load_3d(st + P::U_OFF, &tm_u, pc.x - 4, pc.y - 1, z, bar);
-            if (ANISO) tma_load_4d(st + P::F_OFF, &tm_f, pc.x - 4, pc.y - 1, z, 0, bar);
+            if (ANISO) tma_load_4d(st + P::F_OFF, &tm_f, pc.x, pc.y - 1, z, 0, bar);  // fibre x offset 4
             if (MASKED) tma_load_3d(st + P::M_OFF, &tm_m, pc.x - 16, pc.y - 1, z, bar);
             if (S > 1 && !halo) tma_load_4d(st + P::S_OFF, &tm_s, pc.x, pc.y, z, 1, bar);
         }
@@ -552,6 +594,7 @@ step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CU
 
             if (x_in) {
                 auto fib = [&](const float* F, int o) { return F3{F[o], F[o + FC], F[o + 2 * FC]}; };
+                const float psx_p = (x + 1 < a.nx) ? 1.0f : 0.0f, psx_m = (x > 0) ? 1.0f : 0.0f;
                 // phase 1: the stencil for the CY nodes of this thread.  Shared
                 // loads slide down the column: rows r-1, r, r+1 of the own, left
                 // and right columns of plane k, and of the own column of planes
@@ -587,7 +630,8 @@ step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CU
                         tissue = tissue && (mc & MASK_TISSUE) != 0;
                         interior = (mc & MASK_INTERIOR) != 0;
                     } else {
-                        interior = (x > 0) && (x + 1 < a.nx) && (y > 0) && (y + 1 < a.ny) && zp_ok && zn_ok;
+                        // warp-uniform: y and z are shared by the lanes of a warp
+                        interior = (y > 0) && (y + 1 < a.ny) && zp_ok && zn_ok;
                     }
                     live[r] = tissue;
                     u0r[r] = wC[1];
@@ -608,7 +652,10 @@ step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CU
                     }
                     if (tissue) {
                         if (interior) {
-                            Lr[r] = lap_interior<ANISO>(a, n, f, fxp, fxm, fyp, fym, fzp, fzm);
+                            if (MASKED)
+                                Lr[r] = lap_interior<ANISO>(a, n, f, fxp, fxm, fyp, fym, fzp, fzm);
+                            else
+                                Lr[r] = lap_xbound<ANISO>(a, n, psx_p, psx_m, f, fxp, fxm, fyp, fym, fzp, fzm);
                         } else {
                             Psi q;
                             if (MASKED) {
@@ -681,7 +728,7 @@ step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CU
 
     const double mine = (double)vsum.hi + (double)vsum.lo;
     const double bs = block_sum_double(mine, red_scratch);
-    grid_total_finalize(bs, a.partials, a.ticket, a.total_out, a.err, true);
+    grid_total_finalize(bs, a.partials, a.ticket, a.total_out, a.err, true, red_scratch);
 }
 
 // host-visible description of one compiled step kernel

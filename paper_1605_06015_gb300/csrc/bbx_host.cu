@@ -111,25 +111,30 @@ bool encode(CUtensorMap* m, CUtensorMapDataType dt, int rank, void* base, const 
 // set-up kernels
 // ------------------------------------------------------------------------
 
-// Normalise interleaved fibres into the pitched SoA field [3][nz][ny][px];
-// zero vector at a tissue node -> error bit.  Void nodes get 0.
-__global__ void k_fibres(const float* __restrict__ in, int nx, int ny, int nz, int px, long long plane,
-                         long long vol, const uint8_t* __restrict__ mask, float* __restrict__ out, int* err) {
-    const long long n = (long long)nx * ny * nz;
+// Normalise interleaved fibres into the SoA field [3][nz][ny][pxf] whose rows
+// are stored from x = -4 (storage column x + 4) with the x-padding filled by
+// the nearest in-array fibre (clamped); a zero vector at a tissue node sets
+// the error bit.  Void nodes get 0.
+__global__ void k_fibres(const float* __restrict__ in, int nx, int ny, int nz, int pxf, long long fplane,
+                         long long fvol, const uint8_t* __restrict__ mask, int px, long long plane,
+                         float* __restrict__ out, int* err) {
+    const long long n = (long long)pxf * ny * nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const int x = int(i % nx);
-        const long long r = i / nx;
+        const int xs = int(i % pxf);
+        const long long r = i / pxf;
         const int y = int(r % ny);
         const int z = int(r / ny);
-        const long long gi = z * plane + (long long)y * px + x;
-        const bool tissue = mask ? mask[gi] != 0 : true;
-        const float fx = in[3 * i], fy = in[3 * i + 1], fz = in[3 * i + 2];
+        const int x = min(max(xs - 4, 0), nx - 1);
+        const bool real = (xs - 4) == x;
+        const long long src = (long long)x + (long long)nx * (y + (long long)ny * z);
+        const bool tissue = mask ? mask[z * plane + (long long)y * px + x] != 0 : true;
+        const float fx = in[3 * src], fy = in[3 * src + 1], fz = in[3 * src + 2];
         const float n2 = fx * fx + fy * fy + fz * fz;
         float ox = 0.f, oy = 0.f, oz = 0.f;
         if (tissue) {
             if (!(n2 > 0.0f) || !isfinite(n2)) {
-                atomicOr(err, kErrFibre);
+                if (real) atomicOr(err, kErrFibre);
             } else {
                 const float nr = __fsqrt_rn(n2);
                 ox = __fdiv_rn(fx, nr);
@@ -137,9 +142,10 @@ __global__ void k_fibres(const float* __restrict__ in, int nx, int ny, int nz, i
                 oz = __fdiv_rn(fz, nr);
             }
         }
-        out[gi] = ox;
-        out[vol + gi] = oy;
-        out[2 * vol + gi] = oz;
+        const long long o = z * fplane + (long long)y * pxf + xs;
+        out[o] = ox;
+        out[fvol + o] = oy;
+        out[2 * fvol + o] = oz;
     }
 }
 
@@ -282,7 +288,7 @@ __global__ void k_total(const float* __restrict__ u, const uint8_t* __restrict__
         if (!mask || mask[gi]) two_sum_add(acc, u[gi]);
     }
     const double bs = block_sum_double((double)acc.hi + (double)acc.lo, scratch);
-    grid_total_finalize(bs, partials, ticket, out, err, false);
+    grid_total_finalize(bs, partials, ticket, out, err, false, scratch);
 }
 
 template <typename T>
@@ -305,7 +311,9 @@ struct bbx_grid {
 
     uint8_t* d_mask = nullptr;
     long long n_tissue = 0;
-    float* d_fib = nullptr;
+    float* d_fib = nullptr;  // [3][nz][ny][pxf], x stored from -4 (clamped padding)
+    int pxf = 0;
+    long long fplane = 0, fvol = 0;
     bool aniso = false;
     double Dpar = 1.0, Dperp = 1.0;
 
@@ -524,9 +532,10 @@ int prepare(bbx_grid* g) {
         }
     }
     if (g->aniso) {
-        const cuuint64_t fd4[4] = {(cuuint64_t)g->nx, (cuuint64_t)g->ny, (cuuint64_t)g->nz, 3};
+        const cuuint64_t fd4[4] = {(cuuint64_t)g->pxf, (cuuint64_t)g->ny, (cuuint64_t)g->nz, 3};
+        const cuuint64_t fstr4[3] = {(cuuint64_t)g->pxf * 4, (cuuint64_t)g->fplane * 4, (cuuint64_t)g->fvol * 4};
         const cuuint32_t fbox[4] = {(cuuint32_t)(kTileX + 8), (cuuint32_t)(ty + 2), 1, 3};
-        if (!encode(&g->tm_f, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->d_fib, fd4, str4, fbox)) return BBX_ERR_CUDA;
+        if (!encode(&g->tm_f, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->d_fib, fd4, fstr4, fbox)) return BBX_ERR_CUDA;
     } else {
         g->tm_f = g->tm_u[0];
     }
@@ -710,18 +719,19 @@ int bbx_set_fibres(bbx_grid* g, const float* f, double D_par, double D_perp) {
     } else {
         float* tmp = nullptr;
         float* fib = nullptr;
+        const int pxf = (g->nx + 8 + 31) / 32 * 32;
+        const long long fplane = (long long)pxf * g->ny, fvol = fplane * g->nz;
         if (dmalloc(&tmp, sizeof(float) * 3 * g->ncell) != cudaSuccess) return BBX_ERR_NOMEM;
-        if (dmalloc(&fib, sizeof(float) * 3 * g->vol) != cudaSuccess) {
+        if (dmalloc(&fib, sizeof(float) * 3 * fvol) != cudaSuccess) {
             cudaFree(tmp);
             return BBX_ERR_NOMEM;
         }
         int rc = BBX_OK, err = 0;
         cudaError_t e = cudaMemcpyAsync(tmp, f, sizeof(float) * 3 * g->ncell, cudaMemcpyHostToDevice, g->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(fib, 0, sizeof(float) * 3 * g->vol, g->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream);
         if (e == cudaSuccess) {
-            k_fibres<<<n_blocks_for(g->ncell, 256), 256, 0, g->stream>>>(tmp, g->nx, g->ny, g->nz, g->px, g->plane,
-                                                                          g->vol, g->d_mask, fib, g->d_err);
+            k_fibres<<<n_blocks_for(fvol, 256), 256, 0, g->stream>>>(tmp, g->nx, g->ny, g->nz, pxf, fplane, fvol,
+                                                                      g->d_mask, g->px, g->plane, fib, g->d_err);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaMemcpyAsync(&err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream);
@@ -736,6 +746,9 @@ int bbx_set_fibres(bbx_grid* g, const float* f, double D_par, double D_perp) {
         }
         cudaFree(g->d_fib);
         g->d_fib = fib;
+        g->pxf = pxf;
+        g->fplane = fplane;
+        g->fvol = fvol;
         g->aniso = true;
         g->Dpar = D_par;
         g->Dperp = D_perp;
