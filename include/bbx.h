@@ -176,8 +176,9 @@ int bbx_get_info(bbx_grid* g, bbx_info* out);
  * *count receives the number of bricks.  Synchronises. */
 int bbx_read_active_bricks(bbx_grid* g, int32_t* out, size_t cap, long long* count);
 
-/* Choose the brick shape of the step kernel: tile_y in {4, 8, 16} rows of 64
- * nodes, and tile_z >= 1 planes per brick.  Rebuilds the brick list. */
+/* Choose the brick shape of the step kernel: tile_y in {8, 16, 32} rows of 64
+ * nodes, and tile_z >= 1 planes per brick (the z-granularity at which idle
+ * bricks of a masked grid are elided).  Rebuilds the brick list. */
 int bbx_set_tiling(bbx_grid* g, int tile_y, int tile_z);
 
 /* Time candidate brick shapes with CUDA events on the grid's stream (a few

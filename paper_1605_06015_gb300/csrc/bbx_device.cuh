@@ -309,8 +309,8 @@ struct Model<BBX_BR> {
 // shared-memory plan of the step kernel
 // ---------------------------------------------------------------------------
 
-constexpr int kTileX = 64;  // nodes per brick along x (two warps)
-constexpr int kCY = 4;      // nodes per thread along y
+constexpr int kTileX = 64;  // nodes per brick along x: 32 threads x 2 nodes
+constexpr int kRowsOfThreads = 8;  // thread rows per CTA (256 threads)
 constexpr int align128(int b) { return (b + 127) & ~127; }
 
 // Tissue-mask byte on the device: bit 0 = tissue, bit 1 = tissue node whose
@@ -321,9 +321,9 @@ template <int MODEL, bool MASKED, bool ANISO, int TY>
 struct Plan {
     static constexpr int S = Model<MODEL>::S;
     static constexpr int TX = kTileX;
-    static constexpr int CY = kCY;
-    static constexpr int RY = TY / CY;  // thread rows
-    static constexpr int THREADS = TX * RY;
+    static constexpr int RY = kRowsOfThreads;
+    static constexpr int CY = TY / RY;  // nodes per thread along y (each a pair in x)
+    static constexpr int THREADS = 32 * RY;
     static constexpr int UW = TX + 8;   // x from x0-4 to x0+TX+3 (16-byte aligned start)
     static constexpr int UH = TY + 2;   // y from y0-1 to y0+TY
     static constexpr int MW = TX + 32;  // mask bytes: x from x0-16 (16-byte aligned start)
@@ -336,12 +336,12 @@ struct Plan {
     static constexpr int M_OFF = F_OFF + align128(F_RAW);
     static constexpr int S_OFF = M_OFF + align128(M_RAW);
     static constexpr int STAGE = S_OFF + align128(S_RAW);
-    static constexpr uint32_t TX_BYTES = U_RAW + F_RAW + M_RAW + S_RAW;  // plane computed in this brick
+    static constexpr uint32_t TX_BYTES = U_RAW + F_RAW + M_RAW + S_RAW;  // plane computed in this piece
     static constexpr uint32_t TX_BYTES_HALO = U_RAW + F_RAW + M_RAW;     // z-halo plane: no other vars
     static constexpr int NS_FIT = (110 * 1024) / STAGE;
     static constexpr int NS = NS_FIT > 8 ? 8 : (NS_FIT < 4 ? 4 : NS_FIT);
     static constexpr int SMEM = 128 + NS * STAGE + NS * 8;
-    static_assert(TY % CY == 0, "tile rows must be a multiple of the rows per thread");
+    static_assert(TY % RY == 0 && CY >= 1, "tile rows must be a multiple of the thread rows");
 };
 
 struct F3 {
@@ -486,12 +486,13 @@ __device__ __forceinline__ float lap_general(const StepArgs& a, const Nb& n, con
 // ---------------------------------------------------------------------------
 
 template <int MODEL, bool MASKED, bool ANISO, int TY>
-__global__ void __launch_bounds__(kTileX * (TY / kCY))
+__global__ void __launch_bounds__(32 * kRowsOfThreads)
 step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_s,
             const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ CUtensorMap tm_m,
             const StepArgs a) {
     using P = Plan<MODEL, MASKED, ANISO, TY>;
     constexpr int S = P::S, TX = P::TX, UW = P::UW, MW = P::MW, NS = P::NS, CY = P::CY;
+    static_assert(TX == 64, "pair mapping assumes 64-node rows");
     constexpr int FC = UW * P::UH;  // fibre component stride in a stage
 
     extern __shared__ unsigned char smem_raw[];
@@ -501,7 +502,7 @@ step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CU
     __shared__ double red_scratch[32];
 
     const int tid = threadIdx.x;
-    const int tx = tid % TX, row0 = (tid / TX) * CY;
+    const int tx = tid % 32, row0 = (tid / 32) * CY;  // node pair (x, x+1) = x0 + 2 tx
 
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
@@ -560,8 +561,8 @@ step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CU
 
     for (int pi = piece_begin; pi < piece_end; ++pi) {
         const int4 pc = a.pieces[pi];
-        const int x = pc.x + tx;
-        const int yb = pc.y + row0;  // y of this thread's first node
+        const int x = pc.x + 2 * tx;  // first node of this thread's pair
+        const int yb = pc.y + row0;   // y of this thread's first row
         const bool x_in = x < a.nx;
         const int ncomp = pc.w - pc.z;
 
@@ -589,29 +590,29 @@ step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CU
             const unsigned char* Mn = stn + P::M_OFF;
             const float* Sv = reinterpret_cast<const float*>(stc + P::S_OFF);
             const bool zn_ok = k + 1 < a.nz, zp_ok = k > 0;
-            const int c0 = (row0 + 1) * UW + (tx + 4);   // stage index of node (x, yb)
-            const int m0 = (row0 + 1) * MW + (tx + 16);  // mask index of node (x, yb)
+            const int c0 = (row0 + 1) * UW + (2 * tx + 4);   // stage index of node (x, yb), even
+            const int m0 = (row0 + 1) * MW + (2 * tx + 16);  // mask index of node (x, yb)
 
             if (x_in) {
-                auto fib = [&](const float* F, int o) { return F3{F[o], F[o + FC], F[o + 2 * FC]}; };
-                const float psx_p = (x + 1 < a.nx) ? 1.0f : 0.0f, psx_m = (x > 0) ? 1.0f : 0.0f;
-                // phase 1: the stencil for the CY nodes of this thread.  Shared
-                // loads slide down the column: rows r-1, r, r+1 of the own, left
-                // and right columns of plane k, and of the own column of planes
-                // k+-1 (and the fibres of the own column), live in registers;
-                // each row is read once.
-                float Lr[CY], u0r[CY];
-                bool live[CY];
-                float wC[3], wL[3], wR[3], wN[3], wP[3];
-                F3 wF[3];
-                {
+                auto ld2 = [&](const float* U, int o) { return *reinterpret_cast<const float2*>(U + o); };
+                const bool x1_in = x + 1 < a.nx;
+                // psi of the x neighbours of the two nodes (unmasked grids)
+                const float px0 = x1_in ? 1.0f : 0.0f, mx0 = (x > 0) ? 1.0f : 0.0f;
+                const float px1 = (x + 2 < a.nx) ? 1.0f : 0.0f, mx1 = 1.0f;
+
+                // phase 1: the stencil for the 2 x CY nodes of this thread.
+                // Sliding window down the rows: plane k at x-2..x+3 (three
+                // float2), own pair of planes k+-1, own pair of fibres.
+                float Lr[CY][2], u0r[CY][2];
+                bool live[CY][2];
+                float2 wA[3], wB[3], wC[3], wN[3], wP[3];
+                float2 wFx[3], wFy[3], wFz[3];
 #pragma unroll
-                    for (int w = 0; w < 2; ++w) {
-                        const int o = c0 + (w - 1) * UW;
-                        wC[w] = Uc[o]; wL[w] = Uc[o - 1]; wR[w] = Uc[o + 1];
-                        wN[w] = Un[o]; wP[w] = Up[o];
-                        if (ANISO) wF[w] = fib(Fc, o);
-                    }
+                for (int w = 0; w < 2; ++w) {
+                    const int o = c0 + (w - 1) * UW;
+                    wA[w] = ld2(Uc, o - 2); wB[w] = ld2(Uc, o); wC[w] = ld2(Uc, o + 2);
+                    wN[w] = ld2(Un, o); wP[w] = ld2(Up, o);
+                    if (ANISO) { wFx[w] = ld2(Fc, o); wFy[w] = ld2(Fc + FC, o); wFz[w] = ld2(Fc + 2 * FC, o); }
                 }
 #pragma unroll
                 for (int r = 0; r < CY; ++r) {
@@ -620,88 +621,151 @@ step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CU
                     const int m = m0 + r * MW;
                     {
                         const int o = c + UW;  // row r+1
-                        wC[2] = Uc[o]; wL[2] = Uc[o - 1]; wR[2] = Uc[o + 1];
-                        wN[2] = Un[o]; wP[2] = Up[o];
-                        if (ANISO) wF[2] = fib(Fc, o);
+                        wA[2] = ld2(Uc, o - 2); wB[2] = ld2(Uc, o); wC[2] = ld2(Uc, o + 2);
+                        wN[2] = ld2(Un, o); wP[2] = ld2(Up, o);
+                        if (ANISO) { wFx[2] = ld2(Fc, o); wFy[2] = ld2(Fc + FC, o); wFz[2] = ld2(Fc + 2 * FC, o); }
                     }
-                    bool tissue = y < a.ny, interior;
+                    bool tis[2] = {y < a.ny, y < a.ny && x1_in}, intr[2];
                     if (MASKED) {
-                        const unsigned char mc = Mc[m];
-                        tissue = tissue && (mc & MASK_TISSUE) != 0;
-                        interior = (mc & MASK_INTERIOR) != 0;
+                        const unsigned char mc0 = Mc[m], mc1 = Mc[m + 1];
+                        tis[0] = tis[0] && (mc0 & MASK_TISSUE);
+                        tis[1] = tis[1] && (mc1 & MASK_TISSUE);
+                        intr[0] = (mc0 & MASK_INTERIOR) != 0;
+                        intr[1] = (mc1 & MASK_INTERIOR) != 0;
                     } else {
-                        // warp-uniform: y and z are shared by the lanes of a warp
-                        interior = (y > 0) && (y + 1 < a.ny) && zp_ok && zn_ok;
+                        intr[0] = intr[1] = (y > 0) && (y + 1 < a.ny) && zp_ok && zn_ok;  // warp-uniform
                     }
-                    live[r] = tissue;
-                    u0r[r] = wC[1];
-                    Lr[r] = 0.0f;
-                    Nb n;
-                    n.u0 = wC[1];
-                    n.xp = wR[1]; n.xm = wL[1]; n.yp = wC[2]; n.ym = wC[0];
-                    n.zp = wN[1]; n.zm = wP[1];
-                    F3 f = {0.f, 0.f, 0.f}, fxp = f, fxm = f, fyp = f, fym = f, fzp = f, fzm = f;
+                    Nb n[2];
+                    F3 f[2], fxp[2], fxm[2], fyp[2], fym[2], fzp[2], fzm[2];
+                    n[0].u0 = wB[1].x; n[0].xp = wB[1].y; n[0].xm = wA[1].y;
+                    n[0].yp = wB[2].x; n[0].ym = wB[0].x; n[0].zp = wN[1].x; n[0].zm = wP[1].x;
+                    n[1].u0 = wB[1].y; n[1].xp = wC[1].x; n[1].xm = wB[1].x;
+                    n[1].yp = wB[2].y; n[1].ym = wB[0].y; n[1].zp = wN[1].y; n[1].zm = wP[1].y;
                     if (ANISO) {
-                        n.pp = wR[2]; n.mm = wL[0]; n.pm = wR[0]; n.mp = wL[2];
-                        n.xpzp = Un[c + 1]; n.xmzm = Up[c - 1]; n.xpzm = Up[c + 1]; n.xmzp = Un[c - 1];
-                        n.ypzp = wN[2]; n.ymzm = wP[0]; n.ypzm = wP[2]; n.ymzp = wN[0];
-                        f = wF[1];
-                        fxp = fib(Fc, c + 1); fxm = fib(Fc, c - 1);
-                        fyp = wF[2]; fym = wF[0];
-                        fzp = fib(Fn, c); fzm = fib(Fp, c);
+                        const float2 nA = ld2(Un, c - 2), nC = ld2(Un, c + 2);
+                        const float2 pA = ld2(Up, c - 2), pC = ld2(Up, c + 2);
+                        n[0].pp = wB[2].y; n[0].mm = wA[0].y; n[0].pm = wB[0].y; n[0].mp = wA[2].y;
+                        n[0].xpzp = wN[1].y; n[0].xmzm = pA.y; n[0].xpzm = wP[1].y; n[0].xmzp = nA.y;
+                        n[0].ypzp = wN[2].x; n[0].ymzm = wP[0].x; n[0].ypzm = wP[2].x; n[0].ymzp = wN[0].x;
+                        n[1].pp = wC[2].x; n[1].mm = wB[0].x; n[1].pm = wC[0].x; n[1].mp = wB[2].x;
+                        n[1].xpzp = nC.x; n[1].xmzm = wP[1].x; n[1].xpzm = pC.x; n[1].xmzp = wN[1].x;
+                        n[1].ypzp = wN[2].y; n[1].ymzm = wP[0].y; n[1].ypzm = wP[2].y; n[1].ymzp = wN[0].y;
+                        const float2 fAx = ld2(Fc, c - 2), fAy = ld2(Fc + FC, c - 2), fAz = ld2(Fc + 2 * FC, c - 2);
+                        const float2 fCx = ld2(Fc, c + 2), fCy = ld2(Fc + FC, c + 2), fCz = ld2(Fc + 2 * FC, c + 2);
+                        const float2 fNx = ld2(Fn, c), fNy = ld2(Fn + FC, c), fNz = ld2(Fn + 2 * FC, c);
+                        const float2 fPx = ld2(Fp, c), fPy = ld2(Fp + FC, c), fPz = ld2(Fp + 2 * FC, c);
+                        f[0] = F3{wFx[1].x, wFy[1].x, wFz[1].x};
+                        f[1] = F3{wFx[1].y, wFy[1].y, wFz[1].y};
+                        fxp[0] = f[1];
+                        fxm[0] = F3{fAx.y, fAy.y, fAz.y};
+                        fxp[1] = F3{fCx.x, fCy.x, fCz.x};
+                        fxm[1] = f[0];
+                        fyp[0] = F3{wFx[2].x, wFy[2].x, wFz[2].x};
+                        fyp[1] = F3{wFx[2].y, wFy[2].y, wFz[2].y};
+                        fym[0] = F3{wFx[0].x, wFy[0].x, wFz[0].x};
+                        fym[1] = F3{wFx[0].y, wFy[0].y, wFz[0].y};
+                        fzp[0] = F3{fNx.x, fNy.x, fNz.x};
+                        fzp[1] = F3{fNx.y, fNy.y, fNz.y};
+                        fzm[0] = F3{fPx.x, fPy.x, fPz.x};
+                        fzm[1] = F3{fPx.y, fPy.y, fPz.y};
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            f[e] = F3{0.f, 0.f, 0.f};
+                            fxp[e] = fxm[e] = fyp[e] = fym[e] = fzp[e] = fzm[e] = f[e];
+                        }
                     }
-                    if (tissue) {
-                        if (interior) {
-                            if (MASKED)
-                                Lr[r] = lap_interior<ANISO>(a, n, f, fxp, fxm, fyp, fym, fzp, fzm);
-                            else
-                                Lr[r] = lap_xbound<ANISO>(a, n, psx_p, psx_m, f, fxp, fxm, fyp, fym, fzp, fzm);
-                        } else {
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        live[r][e] = tis[e];
+                        u0r[r][e] = n[e].u0;
+                        // fast formula for every node (values of void or
+                        // out-of-array nodes are finite and never stored) ...
+                        if (MASKED)
+                            Lr[r][e] = lap_interior<ANISO>(a, n[e], f[e], fxp[e], fxm[e], fyp[e], fym[e], fzp[e],
+                                                           fzm[e]);
+                        else
+                            Lr[r][e] = lap_xbound<ANISO>(a, n[e], e ? px1 : px0, e ? mx1 : mx0, f[e], fxp[e],
+                                                         fxm[e], fyp[e], fym[e], fzp[e], fzm[e]);
+                    }
+                    // ... and the general one where a y/z neighbour (or, in a
+                    // masked grid, any neighbour) may be void: rare, and
+                    // warp-uniform on unmasked grids
+                    if (!((intr[0] || !tis[0]) && (intr[1] || !tis[1]))) {
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            if (!tis[e] || intr[e]) continue;
+                            const int xe = x + e, me = m + e;
                             Psi q;
                             if (MASKED) {
-                                q.xp = Mc[m + 1] != 0; q.xm = Mc[m - 1] != 0;
-                                q.yp = Mc[m + MW] != 0; q.ym = Mc[m - MW] != 0;
-                                q.zp = zn_ok && Mn[m] != 0; q.zm = zp_ok && Mp[m] != 0;
-                                q.pp = Mc[m + MW + 1] != 0; q.mm = Mc[m - MW - 1] != 0;
-                                q.pm = Mc[m - MW + 1] != 0; q.mp = Mc[m + MW - 1] != 0;
-                                q.xpzp = zn_ok && Mn[m + 1] != 0; q.xmzm = zp_ok && Mp[m - 1] != 0;
-                                q.xpzm = zp_ok && Mp[m + 1] != 0; q.xmzp = zn_ok && Mn[m - 1] != 0;
-                                q.ypzp = zn_ok && Mn[m + MW] != 0; q.ymzm = zp_ok && Mp[m - MW] != 0;
-                                q.ypzm = zp_ok && Mp[m + MW] != 0; q.ymzp = zn_ok && Mn[m - MW] != 0;
+                                q.xp = Mc[me + 1] != 0; q.xm = Mc[me - 1] != 0;
+                                q.yp = Mc[me + MW] != 0; q.ym = Mc[me - MW] != 0;
+                                q.zp = zn_ok && Mn[me] != 0; q.zm = zp_ok && Mp[me] != 0;
+                                q.pp = Mc[me + MW + 1] != 0; q.mm = Mc[me - MW - 1] != 0;
+                                q.pm = Mc[me - MW + 1] != 0; q.mp = Mc[me + MW - 1] != 0;
+                                q.xpzp = zn_ok && Mn[me + 1] != 0; q.xmzm = zp_ok && Mp[me - 1] != 0;
+                                q.xpzm = zp_ok && Mp[me + 1] != 0; q.xmzp = zn_ok && Mn[me - 1] != 0;
+                                q.ypzp = zn_ok && Mn[me + MW] != 0; q.ymzm = zp_ok && Mp[me - MW] != 0;
+                                q.ypzm = zp_ok && Mp[me + MW] != 0; q.ymzp = zn_ok && Mn[me - MW] != 0;
                             } else {
-                                const bool xp = x + 1 < a.nx, xm = x > 0, yp = y + 1 < a.ny, ym = y > 0;
+                                const bool xp = xe + 1 < a.nx, xm = xe > 0, yp = y + 1 < a.ny, ym = y > 0;
                                 q.xp = xp; q.xm = xm; q.yp = yp; q.ym = ym; q.zp = zn_ok; q.zm = zp_ok;
                                 q.pp = xp && yp; q.mm = xm && ym; q.pm = xp && ym; q.mp = xm && yp;
                                 q.xpzp = xp && zn_ok; q.xmzm = xm && zp_ok; q.xpzm = xp && zp_ok; q.xmzp = xm && zn_ok;
                                 q.ypzp = yp && zn_ok; q.ymzm = ym && zp_ok; q.ypzm = yp && zp_ok; q.ymzp = ym && zn_ok;
                             }
-                            Lr[r] = lap_general<ANISO>(a, n, q, f, fxp, fxm, fyp, fym, fzp, fzm);
+                            Lr[r][e] = lap_general<ANISO>(a, n[e], q, f[e], fxp[e], fxm[e], fyp[e], fym[e], fzp[e],
+                                                          fzm[e]);
                         }
                     }
                     // slide the window down one row
-                    wC[0] = wC[1]; wC[1] = wC[2]; wL[0] = wL[1]; wL[1] = wL[2]; wR[0] = wR[1]; wR[1] = wR[2];
+                    wA[0] = wA[1]; wA[1] = wA[2]; wB[0] = wB[1]; wB[1] = wB[2]; wC[0] = wC[1]; wC[1] = wC[2];
                     wN[0] = wN[1]; wN[1] = wN[2]; wP[0] = wP[1]; wP[1] = wP[2];
-                    if (ANISO) { wF[0] = wF[1]; wF[1] = wF[2]; }
+                    if (ANISO) {
+                        wFx[0] = wFx[1]; wFx[1] = wFx[2]; wFy[0] = wFy[1]; wFy[1] = wFy[2];
+                        wFz[0] = wFz[1]; wFz[1] = wFz[2];
+                    }
                 }
-                // phase 2: reaction, stores, activation, tissue sum
+
+                // phase 2: reaction, stores, activation, tissue sum (predicated)
+                const bool stim_on = a.stim_amp != 0.0f;
 #pragma unroll
                 for (int r = 0; r < CY; ++r) {
-                    if (!live[r]) continue;
                     const int y = yb + r;
-                    float yv[S];
-                    yv[0] = u0r[r];
+                    const long long gi = (long long)k * a.plane + (long long)y * a.px + x;  // even
+                    float yv[2][S];
 #pragma unroll
-                    for (int v = 1; v < S; ++v) yv[v] = Sv[(v - 1) * TX * TY + (row0 + r) * TX + tx];
-                    const long long gi = (long long)k * a.plane + (long long)y * a.px + x;
-                    float Is = 0.0f;
-                    if (a.stim_amp != 0.0f && a.stim[gi]) Is = a.stim_amp;
-                    Model<MODEL>::update(mp, yv, Lr[r], Is, a.dt);
+                    for (int e = 0; e < 2; ++e) yv[e][0] = u0r[r][e];
 #pragma unroll
-                    for (int v = 0; v < S; ++v) a.dst[(long long)v * a.vol + gi] = yv[v];
-                    if (u0r[r] < theta && theta <= yv[0]) {
-                        if (a.act[gi] == BBX_ACT_NONE) a.act[gi] = a.step_next;
+                    for (int v = 1; v < S; ++v) {
+                        const float2 sv = *reinterpret_cast<const float2*>(Sv + (v - 1) * TX * TY + (row0 + r) * TX + 2 * tx);
+                        yv[0][v] = sv.x;
+                        yv[1][v] = sv.y;
                     }
-                    two_sum_add(vsum, yv[0]);
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        float Is = 0.0f;
+                        if (stim_on && live[r][e] && a.stim[gi + e]) Is = a.stim_amp;
+                        Model<MODEL>::update(mp, yv[e], Lr[r][e], Is, a.dt);
+                    }
+                    if (live[r][0] && live[r][1]) {
+#pragma unroll
+                        for (int v = 0; v < S; ++v)
+                            *reinterpret_cast<float2*>(a.dst + (long long)v * a.vol + gi) = make_float2(yv[0][v], yv[1][v]);
+                    } else if (live[r][0] || live[r][1]) {
+#pragma unroll
+                        for (int e = 0; e < 2; ++e)
+                            if (live[r][e])
+#pragma unroll
+                                for (int v = 0; v < S; ++v) a.dst[(long long)v * a.vol + gi + e] = yv[e][v];
+                    }
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        if (live[r][e] && u0r[r][e] < theta && theta <= yv[e][0]) {
+                            if (a.act[gi + e] == BBX_ACT_NONE) a.act[gi + e] = a.step_next;
+                        }
+                        two_sum_add(vsum, live[r][e] ? yv[e][0] : 0.0f);
+                    }
                 }
             }
 

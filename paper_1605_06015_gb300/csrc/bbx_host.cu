@@ -361,6 +361,7 @@ namespace {
 
 int fail_cuda(cudaError_t e) {
     (void)e;
+    cudaGetLastError();  // do not let a failed call's error surface in a later launch check
     return BBX_ERR_CUDA;
 }
 
@@ -499,12 +500,22 @@ int prepare(bbx_grid* g) {
     if (!get_encoder()) return BBX_ERR_CUDA;
     StepKernel k = lookup_kernel(g->model, g->d_mask != nullptr, g->aniso, g->ty);
     if (!k.fn) return BBX_ERR_UNSUPPORTED;
-    if (cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem) != cudaSuccess)
+    int smem_optin = 0;
+    if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device) != cudaSuccess) {
+        cudaGetLastError();
         return BBX_ERR_CUDA;
+    }
+    if (k.smem + 2048 > smem_optin) return BBX_ERR_UNSUPPORTED;  // this tile shape does not fit this model
+    if (cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem) != cudaSuccess) {
+        cudaGetLastError();
+        return BBX_ERR_CUDA;
+    }
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, k.threads, k.smem) != cudaSuccess ||
-        per_sm < 1)
+        per_sm < 1) {
+        cudaGetLastError();
         return BBX_ERR_UNSUPPORTED;
+    }
     long long ctas = (long long)per_sm * g->num_sms;
     if (ctas > kMaxPartials) ctas = kMaxPartials;
     g->grid_ctas = 1;
@@ -638,7 +649,7 @@ int bbx_create_grid(bbx_grid** out, int nx, int ny, int nz, double h, const uint
     g->ncell = ncell;
     g->stream = static_cast<cudaStream_t>(cuda_stream);
     g->zb = (nz == 1) ? 1 : 16;
-    g->ty = 8;
+    g->ty = 16;
     int rc = BBX_OK;
     do {
         if (cudaGetDevice(&g->device) != cudaSuccess ||
@@ -1051,13 +1062,19 @@ int bbx_read_active_bricks(bbx_grid* g, int32_t* out, size_t cap, long long* cou
 }
 
 int bbx_set_tiling(bbx_grid* g, int tile_y, int tile_z) {
-    if (!g || (tile_y != 4 && tile_y != 8 && tile_y != 16) || tile_z < 1) return BBX_ERR_ARG;
+    if (!g || (tile_y != 8 && tile_y != 16 && tile_y != 32) || tile_z < 1) return BBX_ERR_ARG;
+    const int old_ty = g->ty, old_zb = g->zb;
     g->ty = tile_y;
     g->zb = tile_z > g->nz ? g->nz : tile_z;
     int rc = build_bricks(g);
-    if (rc) return rc;
-    if (g->model) return prepare(g);
-    return BBX_OK;
+    if (rc == BBX_OK && g->model) rc = prepare(g);
+    if (rc == BBX_ERR_UNSUPPORTED) {
+        // keep the previous, working tile shape
+        g->ty = old_ty;
+        g->zb = old_zb;
+        if (build_bricks(g) == BBX_OK && g->model) prepare(g);
+    }
+    return rc;
 }
 
 int bbx_state_device_ptr(bbx_grid* g, int var, void** p) {
@@ -1089,7 +1106,7 @@ int bbx_autotune(bbx_grid* g, double dt, double* best_ms) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int tys[3] = {4, 8, 16};
+    const int tys[3] = {8, 16, 32};
     std::vector<int> zbs;
     if (g->nz == 1 || !g->d_mask) {
         zbs.push_back(g->zb);  // unmasked columns are marched whole; only the tile rows matter
