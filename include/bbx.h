@@ -186,6 +186,47 @@ int bbx_set_tiling(bbx_grid* g, int tile_y, int tile_z);
  * be NULL) receives its time per step. */
 int bbx_autotune(bbx_grid* g, double dt, double* best_ms);
 
+/* Set the time step used by bbx_batch_step (bbx_step sets it too).  Errors:
+ * BBX_ERR_STATE (no model), BBX_ERR_ARG (dt <= 0), BBX_ERR_UNSTABLE. */
+int bbx_set_timestep(bbx_grid* g, double dt);
+
+/* ---- batches of independent grids ------------------------------------- */
+/* Many independent grids of uneven sizes and parameters (parameter sweeps)
+ * advanced together.  Grids of one kernel type (model, masked, anisotropic)
+ * share one persistent launch with a balanced schedule over all their
+ * columns; the launches of the different types of a step run side by side,
+ * each on a share of the GPU proportional to its work.  Steps are replayed
+ * from a CUDA graph captured on first use.  Not part of the paper: its
+ * parameter studies ran one job per simulation. */
+typedef struct bbx_batch bbx_batch;
+
+/* Borrow n grids (distinct, each with a model and a time step, all created
+ * on the same stream and device).  The grids must outlive the batch and must
+ * not be stepped on their own while a batch step is in flight.  Changing a
+ * member's settings is allowed between batch steps (the batch is rebuilt).
+ * Errors: BBX_ERR_ARG, BBX_ERR_STATE (a member without model or time step),
+ * BBX_ERR_UNSUPPORTED, BBX_ERR_NOMEM, BBX_ERR_CUDA. */
+int bbx_batch_create(bbx_batch** out, bbx_grid* const* grids, int n);
+
+/* Advance every member by n_steps steps of its own time step (asynchronous
+ * on the members' stream).  Each member's time, step counter, activation map
+ * and tissue total advance exactly as with bbx_step. */
+int bbx_batch_step(bbx_batch* b, int n_steps);
+
+/* Synchronise the batch's stream and report sticky device errors of batch
+ * steps (BBX_ERR_NAN, BBX_ERR_TIMEOUT). */
+int bbx_batch_sync(bbx_batch* b);
+
+/* Time the tile rows {8, 16, 32} of each kernel type on a few steps (member
+ * states restored afterwards) and keep the fastest.  best_ms may be NULL. */
+int bbx_batch_autotune(bbx_batch* b, double* best_ms);
+
+/* Number of kernel-type groups and their tile rows (up to cap entries). */
+int bbx_batch_info(bbx_batch* b, int* n_groups, int* tile_y, int cap);
+
+/* Release the batch (the grids are not touched).  NULL is ignored. */
+void bbx_batch_destroy(bbx_batch* b);
+
 /* Device pointer of the current buffer of one state variable (pitched
  * layout), for callers that keep data on the GPU. */
 int bbx_state_device_ptr(bbx_grid* g, int var, void** dev_ptr);

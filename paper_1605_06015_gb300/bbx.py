@@ -74,6 +74,12 @@ def _load():
         "bbx_state_device_ptr": [P, I, ctypes.POINTER(P)],
         "bbx_debug_poison_first_load": [P, I],
         "bbx_clear_device_error": [P],
+        "bbx_set_timestep": [P, D],
+        "bbx_batch_create": [ctypes.POINTER(P), ctypes.POINTER(P), I],
+        "bbx_batch_step": [P, I],
+        "bbx_batch_sync": [P],
+        "bbx_batch_autotune": [P, ctypes.POINTER(D)],
+        "bbx_batch_info": [P, ctypes.POINTER(I), ctypes.POINTER(I), I],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -81,6 +87,8 @@ def _load():
         fn.restype = I
     L.bbx_destroy_grid.argtypes = [P]
     L.bbx_destroy_grid.restype = None
+    L.bbx_batch_destroy.argtypes = [P]
+    L.bbx_batch_destroy.restype = None
     L.bbx_status_string.argtypes = [I]
     L.bbx_status_string.restype = ctypes.c_char_p
     return L
@@ -131,16 +139,21 @@ def bbx_status_string(code):
     return _lib.bbx_status_string(int(code)).decode()
 
 
+_shapes = {}  # grid handle -> (n, (nz, ny, nx)), filled at creation
+
+
 def bbx_create_grid(nx, ny, nz, h, mask=None, stream=None):
     g = ctypes.c_void_p()
     n = nx * ny * nz
     mp, keep = _hostptr(None if mask is None else (np.asarray(mask) != 0), np.uint8, n)
     _check(_lib.bbx_create_grid(ctypes.byref(g), int(nx), int(ny), int(nz), float(h), mp,
                                 _stream_handle(stream)), "bbx_create_grid")
+    _shapes[g.value] = (n, (nz, ny, nx))
     return g
 
 
 def bbx_destroy_grid(g):
+    _shapes.pop(getattr(g, "value", g), None)
     _lib.bbx_destroy_grid(g)
 
 
@@ -151,6 +164,9 @@ def bbx_get_info(g):
 
 
 def _ncell(g):
+    key = getattr(g, "value", g)
+    if key in _shapes:
+        return _shapes[key]
     i = bbx_get_info(g)
     return i["nx"] * i["ny"] * i["nz"], (i["nz"], i["ny"], i["nx"])
 
@@ -275,6 +291,75 @@ def bbx_debug_poison_first_load(g, on):
 
 def bbx_clear_device_error(g):
     _check(_lib.bbx_clear_device_error(g), "bbx_clear_device_error")
+
+
+def bbx_set_timestep(g, dt):
+    _check(_lib.bbx_set_timestep(g, float(dt)), "bbx_set_timestep")
+
+
+def bbx_batch_create(grids):
+    """grids: sequence of grid handles (or Grid objects)."""
+    hs = [getattr(x, "g", x) for x in grids]
+    arr = (ctypes.c_void_p * len(hs))(*[h.value if hasattr(h, "value") else h for h in hs])
+    b = ctypes.c_void_p()
+    _check(_lib.bbx_batch_create(ctypes.byref(b), arr, len(hs)), "bbx_batch_create")
+    return b
+
+
+def bbx_batch_step(b, n_steps=1):
+    _check(_lib.bbx_batch_step(b, int(n_steps)), "bbx_batch_step")
+
+
+def bbx_batch_sync(b):
+    _check(_lib.bbx_batch_sync(b), "bbx_batch_sync")
+
+
+def bbx_batch_autotune(b):
+    ms = ctypes.c_double()
+    _check(_lib.bbx_batch_autotune(b, ctypes.byref(ms)), "bbx_batch_autotune")
+    return ms.value
+
+
+def bbx_batch_info(b):
+    n = ctypes.c_int()
+    tys = (ctypes.c_int * 64)()
+    _check(_lib.bbx_batch_info(b, ctypes.byref(n), tys, 64), "bbx_batch_info")
+    return {"n_groups": n.value, "tile_y": list(tys[:min(n.value, 64)])}
+
+
+def bbx_batch_destroy(b):
+    _lib.bbx_batch_destroy(b)
+
+
+class Batch:
+    """Owner of a batch handle; keeps its member Grid objects alive."""
+
+    def __init__(self, grids):
+        self.grids = list(grids)
+        self.b = bbx_batch_create(self.grids)
+
+    def step(self, n_steps=1):
+        bbx_batch_step(self.b, n_steps)
+
+    def sync(self):
+        bbx_batch_sync(self.b)
+
+    def autotune(self):
+        return bbx_batch_autotune(self.b)
+
+    def info(self):
+        return bbx_batch_info(self.b)
+
+    def close(self):
+        if self.b:
+            bbx_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Grid:

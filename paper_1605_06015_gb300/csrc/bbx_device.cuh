@@ -35,33 +35,59 @@ namespace bbx {
 
 enum : int { ERRBIT_TIMEOUT = 1, ERRBIT_NAN = 2 };
 
-struct StepArgs {
+// Device-updated state of one grid: written only by the last CTA of a step.
+struct TissueDyn {
+    double t;       // model time t_n
+    double total;   // tissue sum of V after the most recent step
+    long long n;    // steps taken
+    int cur;        // buffer holding the current state (0 or 1)
+    int pad;
+};
+
+// Host-written description of one grid for the step kernel (in device memory,
+// so that one launch, or one graph node, can serve any number of grids).
+struct TissueArgs {  // (CUtensorMap members impose its alignment)
+    CUtensorMap tm_u[2];  // V of buffer b with halo (box TX+8 x TY+2)
+    CUtensorMap tm_s[2];  // non-diffusing variables of buffer b (box TX x TY x S-1)
+    CUtensorMap tm_f;     // unit fibres, x stored from -4 with clamped padding
+    CUtensorMap tm_m;     // tissue mask bytes
+    float* state[2];      // the ping-pong buffers, var v at state[b] + v*vol
+    int32_t* act;         // activation steps
+    const uint8_t* stim;  // stimulus region (nullptr: none)
+    TissueDyn* dyn;
+    long long plane, vol;  // px*ny, px*ny*nz
+    double t_on, t_off;    // stimulus window, compared with t_n
+    double dt_d;           // time step, for t_{n+1} = t_n + dt
     int nx, ny, nz, px;
-    long long plane;  // px * ny
-    long long vol;    // px * ny * nz
-    // Work schedule: CTA c marches through pieces[cta_off[c] .. cta_off[c+1]),
-    // each piece = (x0, y0, z0, z1): one 64 x TY column of the grid over the
-    // z-range [z0, z1).  The host balances the planes per CTA.
-    const int4* pieces;
-    const int* cta_off;
-    float* dst;  // destination state buffer (var v at dst + v*vol)
-    int32_t* act;
-    float theta;
-    int step_next;  // n+1 for this step
-    const uint8_t* stim;
-    float stim_amp;  // 0: stimulus off for this step
-    float dt;
+    float dt, theta, stim_amp;
     // diffusion constants over h^2: anisotropic D = Dperp I + (Dpar-Dperp) f f^T
     // gives c_perp = Dperp/h^2, c_d = (Dpar-Dperp)/h^2, c_dh = c_d/2 (edge
     // weights), c_s = c_d/4 (Wtilde); isotropic D gives c_iso = D/h^2.
     float c_perp, c_d, c_dh, c_s, c_iso;
-    float mp[8];            // model parameters (already in kernel form)
-    double* partials;       // >= gridDim.x doubles
-    unsigned int* ticket;   // zero between launches
-    double* total_out;      // tissue sum of the new V
-    int* err;               // sticky error bits
-    long long wait_limit;   // clock64 cycles a wait may spin before giving up
-    int poison_first_load;  // fault injection: CTA 0's first plane never completes
+    float mp[8];  // model parameters in kernel form
+};
+
+// One launch: a balanced schedule of pieces over the grids of one kernel type.
+// CTA c marches through pieces[cta_off[c] .. cta_off[c+1]); a piece
+// (x0, y0, z0, z1) is one 64 x TY column of grid piece_tissue[i] over the
+// z-range [z0, z1).
+struct LaunchArgs {
+    const TissueArgs* tissues;
+    const int4* pieces;
+    const int* piece_tissue;
+    const int* cta_off;
+    const int* tissue_off;     // grid t owns pieces tissue_pieces[tissue_off[t] .. tissue_off[t+1])
+    const int* tissue_pieces;  // (for the per-grid sums, in a fixed order)
+    int n_tissues;
+    double* partials;          // one per piece
+    unsigned int* ticket;      // zero between launches
+    int* err;                  // sticky error bits
+    long long wait_limit;      // clock64 cycles a wait may spin before giving up
+    int poison_first_load;     // fault injection: CTA 0's first plane never completes
+};
+
+struct Coef {
+    float c_perp, c_d, c_dh, c_s, c_iso;
 };
 
 // ---------------------------------------------------------------------------
@@ -191,6 +217,36 @@ __device__ __forceinline__ void grid_total_finalize(double block_partial, double
         *out = total;
         *ticket = 0u;
     }
+}
+
+// End of a step, in the last CTA to finish: per-grid totals from the
+// per-piece partials (fixed order), then t += dt, n += 1 and the buffer
+// parity flip of every grid of the launch.
+__device__ __forceinline__ void step_finalize(const LaunchArgs& L, double* scratch32) {
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int t = atomicAdd(L.ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int ti = threadIdx.x; ti < L.n_tissues; ti += blockDim.x) {
+        double s = 0.0;
+        for (int k = __ldcg(&L.tissue_off[ti]); k < __ldcg(&L.tissue_off[ti + 1]); ++k)
+            s += __ldcg(&L.partials[__ldcg(&L.tissue_pieces[k])]);
+        const TissueArgs* T = L.tissues + ti;
+        TissueDyn* d = T->dyn;
+        if (!isfinite(s)) atomicOr(L.err, ERRBIT_NAN);
+        d->total = s;
+        d->t = d->t + T->dt_d;
+        d->n = d->n + 1;
+        d->cur = d->cur ^ 1;
+    }
+    (void)scratch32;
+    if (threadIdx.x == 0) *L.ticket = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -361,7 +417,7 @@ struct Nb {
 // Eq. (Lu) with psi = 1 everywhere, in difference form.  c_perp = Dperp/h^2,
 // c_d = (Dpar-Dperp)/h^2, c_dh = c_d/2, c_s = c_d/4.
 template <bool ANISO>
-__device__ __forceinline__ float lap_interior(const StepArgs& a, const Nb& n, F3 f, F3 fxp, F3 fxm, F3 fyp,
+__device__ __forceinline__ float lap_interior(const Coef& a, const Nb& n, F3 f, F3 fxp, F3 fxm, F3 fyp,
                                               F3 fym, F3 fzp, F3 fzm) {
     if (!ANISO) {
         return a.c_iso * (((n.xp + n.xm) + (n.yp + n.ym)) + (n.zp + n.zm) - 6.0f * n.u0);
@@ -398,7 +454,7 @@ __device__ __forceinline__ float lap_interior(const StepArgs& a, const Nb& n, F3
 // fibre field is stored with a clamped x-padding), which is the replacement
 // of a void neighbour's tensor by D^p.
 template <bool ANISO>
-__device__ __forceinline__ float lap_xbound(const StepArgs& a, const Nb& n, float px, float mx, F3 f, F3 fxp,
+__device__ __forceinline__ float lap_xbound(const Coef& a, const Nb& n, float px, float mx, F3 f, F3 fxp,
                                             F3 fxm, F3 fyp, F3 fym, F3 fzp, F3 fzm) {
     const float ex = px * (n.xp - n.u0) + mx * (n.xm - n.u0);
     if (!ANISO) {
@@ -442,7 +498,7 @@ struct Psi {
 // out-of-array neighbour contributes nothing) and, in Wtilde, a void
 // neighbour's tensor is replaced by D^p.
 template <bool ANISO>
-__device__ __forceinline__ float lap_general(const StepArgs& a, const Nb& n, const Psi& q, F3 f, F3 fxp, F3 fxm,
+__device__ __forceinline__ float lap_general(const Coef& a, const Nb& n, const Psi& q, F3 f, F3 fxp, F3 fxm,
                                              F3 fyp, F3 fym, F3 fzp, F3 fzm) {
     auto d = [&](bool ps, float uq) { return ps ? (uq - n.u0) : 0.0f; };
     const float exp_ = d(q.xp, n.xp), exm = d(q.xm, n.xm), eyp = d(q.yp, n.yp), eym = d(q.ym, n.ym);
@@ -485,11 +541,20 @@ __device__ __forceinline__ float lap_general(const StepArgs& a, const Nb& n, con
 // the fused step kernel
 // ---------------------------------------------------------------------------
 
+// Per-piece view of the grid being stepped (loaded from its TissueArgs).
+struct PieceCtx : Coef {
+    int nx, ny, nz, px;
+    long long plane, vol;
+    float* dst;
+    int32_t* act;
+    const uint8_t* stim;
+    float stim_amp, dt, theta;
+    int step_next;
+};
+
 template <int MODEL, bool MASKED, bool ANISO, int TY>
-__global__ void __launch_bounds__(32 * kRowsOfThreads)
-step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_s,
-            const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ CUtensorMap tm_m,
-            const StepArgs a) {
+__global__ void __launch_bounds__(32 * kRowsOfThreads, (MASKED && ANISO) || TY == 32 ? 1 : 2)
+step_kernel(const __grid_constant__ LaunchArgs L) {
     using P = Plan<MODEL, MASKED, ANISO, TY>;
     constexpr int S = P::S, TX = P::TX, UW = P::UW, MW = P::MW, NS = P::NS, CY = P::CY;
     static_assert(TX == 64, "pair mapping assumes 64-node rows");
@@ -507,35 +572,33 @@ step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CU
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
         mbar_init_fence();
-        prefetch_map(&tm_u);
-        if (S > 1) prefetch_map(&tm_s);
-        if (ANISO) prefetch_map(&tm_f);
-        if (MASKED) prefetch_map(&tm_m);
     }
     __syncthreads();
 
     // ---- producer state (thread 0 only) ----
-    const int piece_begin = a.cta_off[blockIdx.x], piece_end = a.cta_off[blockIdx.x + 1];
+    const int piece_begin = L.cta_off[blockIdx.x], piece_end = L.cta_off[blockIdx.x + 1];
     int p_piece = piece_begin, p_off = 0, issued = 0;
     auto issue_next = [&]() -> bool {
         if (p_piece >= piece_end) return false;
-        const int4 pc = a.pieces[p_piece];
+        const int4 pc = L.pieces[p_piece];
+        const TissueArgs* T = L.tissues + L.piece_tissue[p_piece];
+        const int src = T->dyn->cur;
         const int nload = pc.w - pc.z + 2;
         const int z = pc.z - 1 + p_off;
         const bool halo = (p_off == 0) || (p_off == nload - 1);
         const int slot = issued % NS;
         uint64_t* bar = &bars[slot];
         unsigned char* st = smem + slot * P::STAGE;
-        if (a.poison_first_load && blockIdx.x == 0 && issued == 0) {
+        if (L.poison_first_load && blockIdx.x == 0 && issued == 0) {
             mbar_arrive_expect_tx(bar, 16);  // fault injection: bytes no copy delivers
-        } else if (z < 0 || z >= a.nz) {
+        } else if (z < 0 || z >= T->nz) {
             mbar_arrive(bar);  // plane outside the array: nothing to load
         } else {
             mbar_arrive_expect_tx(bar, (halo || S == 1) ? P::TX_BYTES_HALO : P::TX_BYTES);
-            tma_load_3d(st + P::U_OFF, &tm_u, pc.x - 4, pc.y - 1, z, bar);
-            if (ANISO) tma_load_4d(st + P::F_OFF, &tm_f, pc.x, pc.y - 1, z, 0, bar);  // fibre x offset 4
-            if (MASKED) tma_load_3d(st + P::M_OFF, &tm_m, pc.x - 16, pc.y - 1, z, bar);
-            if (S > 1 && !halo) tma_load_4d(st + P::S_OFF, &tm_s, pc.x, pc.y, z, 1, bar);
+            tma_load_3d(st + P::U_OFF, &T->tm_u[src], pc.x - 4, pc.y - 1, z, bar);
+            if (ANISO) tma_load_4d(st + P::F_OFF, &T->tm_f, pc.x, pc.y - 1, z, 0, bar);  // fibre x offset 4
+            if (MASKED) tma_load_3d(st + P::M_OFF, &T->tm_m, pc.x - 16, pc.y - 1, z, bar);
+            if (S > 1 && !halo) tma_load_4d(st + P::S_OFF, &T->tm_s[src], pc.x, pc.y, z, 1, bar);
         }
         ++issued;
         if (++p_off == nload) {
@@ -552,15 +615,32 @@ step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CU
     // ---- consumer ----
     F2 vsum = {0.0f, 0.0f};
     bool timed_out = false, abort = false;
-    int jb = 0;  // load index of the first plane of the current brick
-    const float theta = a.theta;
-
-    float mp[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) mp[i] = a.mp[i];
+    int jb = 0;  // load index of the first plane of the current piece
 
     for (int pi = piece_begin; pi < piece_end; ++pi) {
-        const int4 pc = a.pieces[pi];
+        const int4 pc = L.pieces[pi];
+        PieceCtx a;
+        float mp[8];
+        float theta;
+        {
+            const TissueArgs* T = L.tissues + L.piece_tissue[pi];
+            const TissueDyn* D = T->dyn;
+            const int src = D->cur;
+            const double tn = D->t;
+            a.nx = T->nx; a.ny = T->ny; a.nz = T->nz; a.px = T->px;
+            a.plane = T->plane; a.vol = T->vol;
+            a.dst = T->state[src ^ 1];
+            a.act = T->act;
+            a.stim = T->stim;
+            a.stim_amp = (T->stim && T->stim_amp != 0.0f && tn >= T->t_on && tn < T->t_off) ? T->stim_amp : 0.0f;
+            a.dt = T->dt;
+            a.theta = T->theta;
+            a.step_next = (int)(D->n + 1);
+            a.c_perp = T->c_perp; a.c_d = T->c_d; a.c_dh = T->c_dh; a.c_s = T->c_s; a.c_iso = T->c_iso;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) mp[i] = T->mp[i];
+            theta = a.theta;
+        }
         const int x = pc.x + 2 * tx;  // first node of this thread's pair
         const int yb = pc.y + row0;   // y of this thread's first row
         const bool x_in = x < a.nx;
@@ -568,12 +648,12 @@ step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CU
 
         for (int w = 0; w < 2; ++w) {
             const int j = jb + w;
-            if (!mbar_wait_bounded(&bars[j % NS], (j / NS) & 1, a.wait_limit)) timed_out = true;
+            if (!mbar_wait_bounded(&bars[j % NS], (j / NS) & 1, L.wait_limit)) timed_out = true;
         }
         for (int t = 0; t < ncomp; ++t) {
             {
                 const int j = jb + t + 2;
-                if (!mbar_wait_bounded(&bars[j % NS], (j / NS) & 1, a.wait_limit)) timed_out = true;
+                if (!mbar_wait_bounded(&bars[j % NS], (j / NS) & 1, L.wait_limit)) timed_out = true;
             }
             const int k = pc.z + t;
             const unsigned char* stp = smem + ((jb + t) % NS) * P::STAGE;
@@ -779,24 +859,26 @@ step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CU
         }
         if (abort) break;
         jb += ncomp + 2;
+        {
+            const double bs = block_sum_double((double)vsum.hi + (double)vsum.lo, red_scratch);
+            if (tid == 0) L.partials[pi] = bs;
+            vsum.hi = vsum.lo = 0.0f;
+            __syncthreads();  // red_scratch is reused by the next piece
+        }
     }
 
     if (abort && tid == 0) {
         // Give loads still in flight a bounded chance to land before exit.
-        atomicOr(a.err, ERRBIT_TIMEOUT);
+        atomicOr(L.err, ERRBIT_TIMEOUT);
         for (int j = jb; j < issued; ++j) {
-            if (a.poison_first_load && blockIdx.x == 0 && j == 0) continue;
-            (void)mbar_wait_bounded(&bars[j % NS], (j / NS) & 1, a.wait_limit);
+            if (L.poison_first_load && blockIdx.x == 0 && j == 0) continue;
+            (void)mbar_wait_bounded(&bars[j % NS], (j / NS) & 1, L.wait_limit);
         }
     }
-
-    const double mine = (double)vsum.hi + (double)vsum.lo;
-    const double bs = block_sum_double(mine, red_scratch);
-    grid_total_finalize(bs, a.partials, a.ticket, a.total_out, a.err, true, red_scratch);
+    step_finalize(L, red_scratch);
 }
 
 // host-visible description of one compiled step kernel
-typedef void (*StepFn)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, StepArgs);
 struct StepKernel {
     const void* fn;
     int smem;

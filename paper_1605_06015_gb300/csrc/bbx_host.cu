@@ -299,6 +299,177 @@ cudaError_t dmalloc(T** p, size_t bytes) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// launch plans: a balanced schedule of pieces over a list of grids
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct Seg {
+    int tissue, x0, y0, z0, z1;
+};
+
+struct LaunchPlan {
+    StepKernel k = {nullptr, 0, 0, 0};
+    int ctas = 0;
+    int n_tissues = 0;
+    long long n_planes = 0;
+    int4* d_pieces = nullptr;
+    int* d_piece_tissue = nullptr;
+    int* d_cta_off = nullptr;
+    int* d_tissue_off = nullptr;
+    int* d_tissue_pieces = nullptr;
+    double* d_partials = nullptr;
+    unsigned int* d_ticket = nullptr;
+    size_t cap_pieces = 0, cap_cta = 0, cap_tis = 0;
+
+    void release() {
+        cudaFree(d_pieces);
+        cudaFree(d_piece_tissue);
+        cudaFree(d_cta_off);
+        cudaFree(d_tissue_off);
+        cudaFree(d_tissue_pieces);
+        cudaFree(d_partials);
+        cudaFree(d_ticket);
+        *this = LaunchPlan();
+    }
+};
+
+template <typename T>
+int upload(T** d, size_t* cap, const std::vector<T>& h) {
+    const size_t n = h.size() ? h.size() : 1;
+    if (n > *cap) {
+        cudaFree(*d);
+        *d = nullptr;
+        if (dmalloc(d, sizeof(T) * n) != cudaSuccess) {
+            cudaGetLastError();
+            *cap = 0;
+            return BBX_ERR_NOMEM;
+        }
+        *cap = n;
+    }
+    if (!h.empty() && cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return BBX_ERR_CUDA;
+    }
+    return BBX_OK;
+}
+
+// Each CTA receives an equal share of the column-planes of all segments (in
+// segment order) as contiguous pieces, so that no CTA idles while others
+// finish; per grid, the pieces are listed for the fixed-order totals.
+int build_plan(LaunchPlan* lp, const std::vector<Seg>& segs, int n_tissues, int ctas) {
+    long long T = 0;
+    for (const Seg& sg : segs) T += sg.z1 - sg.z0;
+    lp->n_planes = T;
+    lp->n_tissues = n_tissues;
+    if (ctas > T) ctas = (int)std::max<long long>(T, 1);
+    std::vector<int4> pieces;
+    std::vector<int> ptis, off((size_t)ctas + 1, 0);
+    size_t si = 0;
+    long long consumed = 0;
+    for (int c = 0; c < ctas; ++c) {
+        off[c] = (int)pieces.size();
+        long long need = (long long)(c + 1) * T / ctas - (long long)c * T / ctas;
+        while (need > 0 && si < segs.size()) {
+            const Seg& sg = segs[si];
+            const long long avail = (sg.z1 - sg.z0) - consumed;
+            const long long take = std::min(avail, need);
+            const int z0 = sg.z0 + (int)consumed;
+            pieces.push_back(make_int4(sg.x0, sg.y0, z0, z0 + (int)take));
+            ptis.push_back(sg.tissue);
+            need -= take;
+            consumed += take;
+            if (consumed == sg.z1 - sg.z0) {
+                ++si;
+                consumed = 0;
+            }
+        }
+    }
+    off[ctas] = (int)pieces.size();
+    std::vector<int> toff((size_t)n_tissues + 1, 0), tlist(pieces.size());
+    for (int t : ptis) toff[(size_t)t + 1]++;
+    for (int t = 0; t < n_tissues; ++t) toff[(size_t)t + 1] += toff[t];
+    {
+        std::vector<int> fill(toff.begin(), toff.end() - 1);
+        for (size_t i = 0; i < ptis.size(); ++i) tlist[(size_t)fill[(size_t)ptis[i]]++] = (int)i;
+    }
+    int rc;
+    size_t cap_pt = lp->cap_pieces, cap_tl = lp->cap_pieces, cap_part = lp->cap_pieces;
+    if ((rc = upload(&lp->d_pieces, &lp->cap_pieces, pieces))) return rc;
+    if ((rc = upload(&lp->d_piece_tissue, &cap_pt, ptis))) return rc;
+    if ((rc = upload(&lp->d_tissue_pieces, &cap_tl, tlist))) return rc;
+    if ((rc = upload(&lp->d_cta_off, &lp->cap_cta, off))) return rc;
+    if ((rc = upload(&lp->d_tissue_off, &lp->cap_tis, toff))) return rc;
+    std::vector<double> zeros(pieces.size(), 0.0);
+    if ((rc = upload(&lp->d_partials, &cap_part, zeros))) return rc;
+    if (!lp->d_ticket) {
+        if (dmalloc(&lp->d_ticket, sizeof(unsigned int)) != cudaSuccess) {
+            cudaGetLastError();
+            return BBX_ERR_NOMEM;
+        }
+        if (cudaMemset(lp->d_ticket, 0, sizeof(unsigned int)) != cudaSuccess) {
+            cudaGetLastError();
+            return BBX_ERR_CUDA;
+        }
+    }
+    lp->ctas = ctas;
+    return BBX_OK;
+}
+
+LaunchArgs launch_args(const LaunchPlan& lp, const TissueArgs* d_tissues, int* d_err, int poison) {
+    LaunchArgs L;
+    memset(&L, 0, sizeof(L));
+    L.tissues = d_tissues;
+    L.pieces = lp.d_pieces;
+    L.piece_tissue = lp.d_piece_tissue;
+    L.cta_off = lp.d_cta_off;
+    L.tissue_off = lp.d_tissue_off;
+    L.tissue_pieces = lp.d_tissue_pieces;
+    L.n_tissues = lp.n_tissues;
+    L.partials = lp.d_partials;
+    L.ticket = lp.d_ticket;
+    L.err = d_err;
+    L.poison_first_load = poison;
+    L.wait_limit = poison ? kPoisonWaitLimit : kWaitLimitCycles;
+    return L;
+}
+
+cudaError_t launch(const LaunchPlan& lp, const LaunchArgs& L, cudaStream_t s) {
+    if (lp.n_planes == 0) return cudaSuccess;
+    void* args[] = {(void*)&L};
+    return cudaLaunchKernel(lp.k.fn, dim3(lp.ctas), dim3(lp.k.threads), args, (size_t)lp.k.smem, s);
+}
+
+// Select the kernel for a configuration, check it fits, and return the CTA
+// budget (resident CTAs on the whole GPU).
+int select_kernel(int model, bool masked, bool aniso, int ty, int device, int num_sms, StepKernel* out,
+                  int* ctas) {
+    StepKernel k = lookup_kernel(model, masked, aniso, ty);
+    if (!k.fn) return BBX_ERR_UNSUPPORTED;
+    int smem_optin = 0;
+    if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
+        cudaGetLastError();
+        return BBX_ERR_CUDA;
+    }
+    if (k.smem + 2048 > smem_optin) return BBX_ERR_UNSUPPORTED;  // this tile shape does not fit this model
+    if (cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem) != cudaSuccess) {
+        cudaGetLastError();
+        return BBX_ERR_CUDA;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, k.threads, k.smem) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        return BBX_ERR_UNSUPPORTED;
+    }
+    *out = k;
+    *ctas = per_sm * num_sms;
+    return BBX_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
 // the grid object
 // ---------------------------------------------------------------------------
 
@@ -320,40 +491,34 @@ struct bbx_grid {
     int model = 0, S = 0;
     double par[8] = {0};
     double theta = 0.0;
+    double dt = 0.0;
     float* d_state[2] = {nullptr, nullptr};
     bool bound = false;
-    int cur = 0;
     int32_t* d_act = nullptr;
     float* d_rest = nullptr;  // 8 floats
     float* d_mp = nullptr;    // 8 floats
 
     uint8_t* d_stim = nullptr;
     double stim_amp = 0, t_on = 0, t_off = 0;
-
-    double t = 0.0;
-    long long n = 0;
     bool stepped = false;
 
-    int ty = 8, zb = 16;
+    int ty = 16, zb = 16;
     int nbx = 0, nby = 0, nbz = 0;
     int* d_bricks = nullptr;
     long long n_bricks = 0;
-    std::vector<int> h_bricks;      // host copy of the active brick ids (masked grids)
-    int4* d_pieces = nullptr;       // balanced per-CTA work schedule
-    int* d_cta_off = nullptr;
-    size_t pieces_cap = 0, off_cap = 0;
-    long long n_planes = 0;         // column-planes in the schedule
+    std::vector<int> h_bricks;  // host copy of the active brick ids (masked grids)
 
-    double* d_partials = nullptr;
+    TissueArgs h_t;                // host copy of the kernel's view of this grid
+    TissueArgs* d_t = nullptr;     // device copy
+    TissueDyn* d_dyn = nullptr;    // device-updated time, step, parity, total
+    LaunchPlan lp;                 // single-grid launch
+    bool ready = false;            // h_t, d_t and lp match the current settings
+    unsigned long long version = 1;  // bumped whenever the kernel's view changes
+
+    double* d_partials = nullptr;  // bbx_total scratch
     unsigned int* d_ticket = nullptr;
-    double* d_total = nullptr;   // written by each step
-    double* d_total2 = nullptr;  // written by bbx_total
+    double* d_total2 = nullptr;
     int* d_err = nullptr;
-
-    CUtensorMap tm_u[2], tm_s[2], tm_f, tm_m;
-    bool maps_ok = false;
-    StepKernel kern = {nullptr, 0, 0, 0};
-    int grid_ctas = 0;
     int poison = 0;
 };
 
@@ -389,14 +554,19 @@ int build_bricks(bbx_grid* g) {
         cudaFree(g->d_bricks);
         g->d_bricks = nullptr;
     }
+    g->h_bricks.clear();
     if (!g->d_mask) {
         g->n_bricks = nb;
         return BBX_OK;
     }
     uint8_t* flags = nullptr;
     long long* d_count = nullptr;
-    if (dmalloc(&flags, nb) != cudaSuccess) return BBX_ERR_NOMEM;
+    if (dmalloc(&flags, nb) != cudaSuccess) {
+            cudaGetLastError();
+            return BBX_ERR_NOMEM;
+        }
     if (dmalloc(&g->d_bricks, sizeof(int) * nb) != cudaSuccess || dmalloc(&d_count, sizeof(long long)) != cudaSuccess) {
+        cudaGetLastError();
         cudaFree(flags);
         return BBX_ERR_NOMEM;
     }
@@ -408,167 +578,159 @@ int build_bricks(bbx_grid* g) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     cudaFree(flags);
     cudaFree(d_count);
-    if (e != cudaSuccess) return BBX_ERR_CUDA;
+    if (e != cudaSuccess) return fail_cuda(e);
     g->n_bricks = cnt;
     g->h_bricks.resize((size_t)cnt);
-    if (cnt > 0) {
-        if (cudaMemcpy(g->h_bricks.data(), g->d_bricks, sizeof(int) * cnt, cudaMemcpyDeviceToHost) != cudaSuccess)
-            return BBX_ERR_CUDA;
-    }
+    if (cnt > 0) BBX_CUDA(cudaMemcpy(g->h_bricks.data(), g->d_bricks, sizeof(int) * cnt, cudaMemcpyDeviceToHost));
     return BBX_OK;
 }
 
-// Balanced work schedule for `ctas` CTAs: the active columns (64 x TY nodes
-// in x, y) with their active z-runs are concatenated column by column, and
-// each CTA receives an equal share of the column-planes as contiguous pieces,
-// so no CTA idles while others finish a last brick.
-int build_schedule(bbx_grid* g, int ctas) {
-    struct Seg {
-        int x0, y0, z0, z1;
-    };
-    std::vector<Seg> segs;
+// Active columns (64 x ty nodes) of a grid with their active z-runs, for the
+// given tile rows (the brick list must have been built for g->ty).
+void grid_segments(const bbx_grid* g, int tissue, std::vector<Seg>* segs) {
     if (!g->d_mask) {
         for (int by = 0; by < g->nby; ++by)
-            for (int bx = 0; bx < g->nbx; ++bx) segs.push_back({bx * kTileX, by * g->ty, 0, g->nz});
-    } else {
-        // brick ids are bx + nbx*(by + nby*bz); regroup by column, z ascending
-        const long long ncol = (long long)g->nbx * g->nby;
-        std::vector<std::vector<int>> col((size_t)ncol);
-        for (int id : g->h_bricks) col[(size_t)(id % ncol)].push_back((int)(id / ncol));
-        for (long long cidx = 0; cidx < ncol; ++cidx) {
-            const std::vector<int>& zs = col[(size_t)cidx];
-            const int bx = (int)(cidx % g->nbx), by = (int)(cidx / g->nbx);
-            size_t i = 0;
-            while (i < zs.size()) {
-                size_t j = i;
-                while (j + 1 < zs.size() && zs[j + 1] == zs[j] + 1) ++j;
-                segs.push_back({bx * kTileX, by * g->ty, zs[i] * g->zb, std::min((zs[j] + 1) * g->zb, g->nz)});
-                i = j + 1;
-            }
+            for (int bx = 0; bx < g->nbx; ++bx) segs->push_back({tissue, bx * kTileX, by * g->ty, 0, g->nz});
+        return;
+    }
+    const long long ncol = (long long)g->nbx * g->nby;
+    std::vector<std::vector<int>> col((size_t)ncol);
+    for (int id : g->h_bricks) col[(size_t)(id % ncol)].push_back((int)(id / ncol));
+    for (long long c = 0; c < ncol; ++c) {
+        const std::vector<int>& zs = col[(size_t)c];
+        const int bx = (int)(c % g->nbx), by = (int)(c / g->nbx);
+        size_t i = 0;
+        while (i < zs.size()) {
+            size_t j = i;
+            while (j + 1 < zs.size() && zs[j + 1] == zs[j] + 1) ++j;
+            segs->push_back({tissue, bx * kTileX, by * g->ty, zs[i] * g->zb, std::min((zs[j] + 1) * g->zb, g->nz)});
+            i = j + 1;
         }
     }
-    long long T = 0;
-    for (const Seg& sg : segs) T += sg.z1 - sg.z0;
-    g->n_planes = T;
-    if (T == 0) return BBX_OK;
-    if (ctas > T) ctas = (int)T;
-    std::vector<int4> pieces;
-    std::vector<int> off((size_t)ctas + 1, 0);
-    size_t si = 0;
-    long long consumed = 0;  // planes of segs[si] already handed out
-    for (int c = 0; c < ctas; ++c) {
-        off[c] = (int)pieces.size();
-        long long need = (long long)(c + 1) * T / ctas - (long long)c * T / ctas;
-        while (need > 0 && si < segs.size()) {
-            const Seg& sg = segs[si];
-            const long long avail = (sg.z1 - sg.z0) - consumed;
-            const long long take = std::min(avail, need);
-            const int z0 = sg.z0 + (int)consumed;
-            pieces.push_back(make_int4(sg.x0, sg.y0, z0, z0 + (int)take));
-            need -= take;
-            consumed += take;
-            if (consumed == sg.z1 - sg.z0) {
-                ++si;
-                consumed = 0;
-            }
-        }
-    }
-    off[ctas] = (int)pieces.size();
-    if (pieces.size() > g->pieces_cap) {
-        cudaFree(g->d_pieces);
-        g->d_pieces = nullptr;
-        if (dmalloc(&g->d_pieces, sizeof(int4) * pieces.size()) != cudaSuccess) return BBX_ERR_NOMEM;
-        g->pieces_cap = pieces.size();
-    }
-    if (off.size() > g->off_cap) {
-        cudaFree(g->d_cta_off);
-        g->d_cta_off = nullptr;
-        if (dmalloc(&g->d_cta_off, sizeof(int) * off.size()) != cudaSuccess) return BBX_ERR_NOMEM;
-        g->off_cap = off.size();
-    }
-    if (cudaMemcpy(g->d_pieces, pieces.data(), sizeof(int4) * pieces.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(g->d_cta_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-        return BBX_ERR_CUDA;
-    g->grid_ctas = ctas;
-    return BBX_OK;
 }
 
-// Tensor maps and kernel choice for the current model / tiling / buffers.
-int prepare(bbx_grid* g) {
-    g->maps_ok = false;
-    if (!g->model || !g->d_state[0]) return BBX_ERR_STATE;
+// The kernel's view of a grid for tile rows `ty` (tensor maps depend on it).
+int encode_targs(const bbx_grid* g, int ty, TissueArgs* t) {
     if (!get_encoder()) return BBX_ERR_CUDA;
-    StepKernel k = lookup_kernel(g->model, g->d_mask != nullptr, g->aniso, g->ty);
-    if (!k.fn) return BBX_ERR_UNSUPPORTED;
-    int smem_optin = 0;
-    if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device) != cudaSuccess) {
-        cudaGetLastError();
-        return BBX_ERR_CUDA;
-    }
-    if (k.smem + 2048 > smem_optin) return BBX_ERR_UNSUPPORTED;  // this tile shape does not fit this model
-    if (cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem) != cudaSuccess) {
-        cudaGetLastError();
-        return BBX_ERR_CUDA;
-    }
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, k.threads, k.smem) != cudaSuccess ||
-        per_sm < 1) {
-        cudaGetLastError();
-        return BBX_ERR_UNSUPPORTED;
-    }
-    long long ctas = (long long)per_sm * g->num_sms;
-    if (ctas > kMaxPartials) ctas = kMaxPartials;
-    g->grid_ctas = 1;
-    g->kern = k;
-    {
-        int rc = build_schedule(g, (int)ctas);
-        if (rc) return rc;
-    }
-
-    const int ty = g->ty;
-    const cuuint64_t fdims3[3] = {(cuuint64_t)g->nx, (cuuint64_t)g->ny, (cuuint64_t)g->nz};
-    const cuuint64_t fstr3[2] = {(cuuint64_t)g->px * 4, (cuuint64_t)g->plane * 4};
+    memset((void*)t, 0, sizeof(TissueArgs));
+    const cuuint64_t dims3[3] = {(cuuint64_t)g->nx, (cuuint64_t)g->ny, (cuuint64_t)g->nz};
+    const cuuint64_t str3[2] = {(cuuint64_t)g->px * 4, (cuuint64_t)g->plane * 4};
     const cuuint32_t ubox[3] = {(cuuint32_t)(kTileX + 8), (cuuint32_t)(ty + 2), 1};
     const cuuint64_t sdims4[4] = {(cuuint64_t)g->nx, (cuuint64_t)g->ny, (cuuint64_t)g->nz, (cuuint64_t)g->S};
     const cuuint64_t str4[3] = {(cuuint64_t)g->px * 4, (cuuint64_t)g->plane * 4, (cuuint64_t)g->vol * 4};
     const cuuint32_t sbox[4] = {(cuuint32_t)kTileX, (cuuint32_t)ty, 1, (cuuint32_t)(g->S > 1 ? g->S - 1 : 1)};
     for (int b = 0; b < 2; ++b) {
-        if (!encode(&g->tm_u[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, g->d_state[b], fdims3, fstr3, ubox))
+        if (!encode(&t->tm_u[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, g->d_state[b], dims3, str3, ubox))
             return BBX_ERR_CUDA;
         if (g->S > 1) {
-            if (!encode(&g->tm_s[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->d_state[b], sdims4, str4, sbox))
+            if (!encode(&t->tm_s[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->d_state[b], sdims4, str4, sbox))
                 return BBX_ERR_CUDA;
         } else {
-            g->tm_s[b] = g->tm_u[b];
+            t->tm_s[b] = t->tm_u[b];
         }
     }
     if (g->aniso) {
         const cuuint64_t fd4[4] = {(cuuint64_t)g->pxf, (cuuint64_t)g->ny, (cuuint64_t)g->nz, 3};
         const cuuint64_t fstr4[3] = {(cuuint64_t)g->pxf * 4, (cuuint64_t)g->fplane * 4, (cuuint64_t)g->fvol * 4};
         const cuuint32_t fbox[4] = {(cuuint32_t)(kTileX + 8), (cuuint32_t)(ty + 2), 1, 3};
-        if (!encode(&g->tm_f, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->d_fib, fd4, fstr4, fbox)) return BBX_ERR_CUDA;
+        if (!encode(&t->tm_f, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->d_fib, fd4, fstr4, fbox)) return BBX_ERR_CUDA;
     } else {
-        g->tm_f = g->tm_u[0];
+        t->tm_f = t->tm_u[0];
     }
     if (g->d_mask) {
         const cuuint64_t mstr[2] = {(cuuint64_t)g->px, (cuuint64_t)g->plane};
         const cuuint32_t mbox[3] = {(cuuint32_t)(kTileX + 32), (cuuint32_t)(ty + 2), 1};
-        if (!encode(&g->tm_m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, g->d_mask, fdims3, mstr, mbox)) return BBX_ERR_CUDA;
+        if (!encode(&t->tm_m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, g->d_mask, dims3, mstr, mbox)) return BBX_ERR_CUDA;
     } else {
-        g->tm_m = g->tm_u[0];
+        t->tm_m = t->tm_u[0];
     }
-    g->maps_ok = true;
+    t->state[0] = g->d_state[0];
+    t->state[1] = g->d_state[1];
+    t->act = g->d_act;
+    t->stim = g->d_stim;
+    t->dyn = g->d_dyn;
+    t->plane = g->plane;
+    t->vol = g->vol;
+    t->t_on = g->t_on;
+    t->t_off = g->t_off;
+    t->dt_d = g->dt;
+    t->nx = g->nx;
+    t->ny = g->ny;
+    t->nz = g->nz;
+    t->px = g->px;
+    t->dt = (float)g->dt;
+    t->theta = (float)g->theta;
+    t->stim_amp = g->d_stim ? (float)g->stim_amp : 0.0f;
+    const double ih2 = 1.0 / (g->h * g->h);
+    const double cd = (g->Dpar - g->Dperp) * ih2;
+    t->c_perp = (float)(g->Dperp * ih2);
+    t->c_d = (float)cd;
+    t->c_dh = (float)(0.5 * cd);
+    t->c_s = (float)(0.25 * cd);
+    t->c_iso = (float)(g->Dpar * ih2);
+    model_kernel_params(g->model, g->par, t->mp);
     return BBX_OK;
 }
 
-int check_sticky(bbx_grid* g) {
-    int err = 0;
-    BBX_CUDA(cudaMemcpyAsync(&err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+// Bring h_t, d_t and the single-grid launch plan in line with the settings.
+int prepare(bbx_grid* g) {
+    g->ready = false;
+    ++g->version;
+    if (!g->model || !g->d_state[0]) return BBX_ERR_STATE;
+    StepKernel k;
+    int ctas = 0;
+    int rc = select_kernel(g->model, g->d_mask != nullptr, g->aniso, g->ty, g->device, g->num_sms, &k, &ctas);
+    if (rc) return rc;
+    if ((rc = encode_targs(g, g->ty, &g->h_t))) return rc;
+    BBX_CUDA(cudaMemcpyAsync(g->d_t, &g->h_t, sizeof(TissueArgs), cudaMemcpyHostToDevice, g->stream));
+    std::vector<Seg> segs;
+    grid_segments(g, 0, &segs);
+    g->lp.k = k;
+    if ((rc = build_plan(&g->lp, segs, 1, ctas))) return rc;
     BBX_CUDA(cudaStreamSynchronize(g->stream));
+    g->ready = true;
+    return BBX_OK;
+}
+
+// Refresh only the scalar fields of the kernel's view (threshold, stimulus,
+// time step) without rebuilding the plan.
+int refresh_targs(bbx_grid* g) {
+    if (!g->ready) return prepare(g);
+    ++g->version;
+    g->h_t.t_on = g->t_on;
+    g->h_t.t_off = g->t_off;
+    g->h_t.dt_d = g->dt;
+    g->h_t.dt = (float)g->dt;
+    g->h_t.theta = (float)g->theta;
+    g->h_t.stim = g->d_stim;
+    g->h_t.stim_amp = g->d_stim ? (float)g->stim_amp : 0.0f;
+    BBX_CUDA(cudaMemcpyAsync(g->d_t, &g->h_t, sizeof(TissueArgs), cudaMemcpyHostToDevice, g->stream));
+    BBX_CUDA(cudaStreamSynchronize(g->stream));
+    return BBX_OK;
+}
+
+int read_dyn(bbx_grid* g, TissueDyn* d) {
+    BBX_CUDA(cudaMemcpyAsync(d, g->d_dyn, sizeof(TissueDyn), cudaMemcpyDeviceToHost, g->stream));
+    BBX_CUDA(cudaStreamSynchronize(g->stream));
+    return BBX_OK;
+}
+
+int write_dyn(bbx_grid* g, const TissueDyn& d) {
+    BBX_CUDA(cudaMemcpyAsync(g->d_dyn, &d, sizeof(TissueDyn), cudaMemcpyHostToDevice, g->stream));
+    BBX_CUDA(cudaStreamSynchronize(g->stream));
+    return BBX_OK;
+}
+
+int check_sticky_ptr(cudaStream_t s, int* d_err) {
+    int err = 0;
+    BBX_CUDA(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BBX_CUDA(cudaStreamSynchronize(s));
     if (err & ERRBIT_TIMEOUT) return BBX_ERR_TIMEOUT;
     if (err & ERRBIT_NAN) return BBX_ERR_NAN;
     return BBX_OK;
 }
+
+int check_sticky(bbx_grid* g) { return check_sticky_ptr(g->stream, g->d_err); }
 
 int copy_in(bbx_grid* g, void* dst, const void* src, size_t elem) {
     BBX_CUDA(cudaMemcpy2DAsync(dst, (size_t)g->px * elem, src, (size_t)g->nx * elem, (size_t)g->nx * elem,
@@ -579,6 +741,24 @@ int copy_in(bbx_grid* g, void* dst, const void* src, size_t elem) {
 int copy_out(bbx_grid* g, void* dst, const void* src, size_t elem) {
     BBX_CUDA(cudaMemcpy2DAsync(dst, (size_t)g->nx * elem, src, (size_t)g->px * elem, (size_t)g->nx * elem,
                                (size_t)g->ny * g->nz, cudaMemcpyDeviceToHost, g->stream));
+    return BBX_OK;
+}
+
+// Forward Euler stability of the diffusion part: Gershgorin bound on the
+// spectrum of the discrete operator, |lambda| <= (4 tr D + 2 |Dpar - Dperp|)/h^2.
+bool stable(const bbx_grid* g, double dt) {
+    const double trD = g->aniso ? (g->Dpar + 2.0 * g->Dperp) : 3.0 * g->Dpar;
+    const double dD = g->aniso ? std::fabs(g->Dpar - g->Dperp) : 0.0;
+    return dt * (4.0 * trD + 2.0 * dD) <= 2.0 * g->h * g->h;
+}
+
+int set_dt(bbx_grid* g, double dt) {
+    if (!(dt > 0.0) || !std::isfinite(dt)) return BBX_ERR_ARG;
+    if (!stable(g, dt)) return BBX_ERR_UNSTABLE;
+    if (dt != g->dt || !g->ready) {
+        g->dt = dt;
+        return refresh_targs(g);
+    }
     return BBX_OK;
 }
 
@@ -620,13 +800,14 @@ void bbx_destroy_grid(bbx_grid* g) {
     cudaFree(g->d_mp);
     cudaFree(g->d_stim);
     cudaFree(g->d_bricks);
-    cudaFree(g->d_pieces);
-    cudaFree(g->d_cta_off);
+    cudaFree(g->d_t);
+    cudaFree(g->d_dyn);
+    g->lp.release();
     cudaFree(g->d_partials);
     cudaFree(g->d_ticket);
-    cudaFree(g->d_total);
     cudaFree(g->d_total2);
     cudaFree(g->d_err);
+    cudaGetLastError();
     delete g;
 }
 
@@ -654,20 +835,25 @@ int bbx_create_grid(bbx_grid** out, int nx, int ny, int nz, double h, const uint
     do {
         if (cudaGetDevice(&g->device) != cudaSuccess ||
             cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) {
+            cudaGetLastError();
             rc = BBX_ERR_CUDA;
             break;
         }
         if (dmalloc(&g->d_partials, sizeof(double) * kMaxPartials) != cudaSuccess ||
             dmalloc(&g->d_ticket, sizeof(unsigned int)) != cudaSuccess ||
-            dmalloc(&g->d_total, sizeof(double)) != cudaSuccess ||
             dmalloc(&g->d_total2, sizeof(double)) != cudaSuccess || dmalloc(&g->d_err, sizeof(int)) != cudaSuccess ||
             dmalloc(&g->d_rest, sizeof(float) * 8) != cudaSuccess ||
-            dmalloc(&g->d_mp, sizeof(float) * 8) != cudaSuccess) {
+            dmalloc(&g->d_mp, sizeof(float) * 8) != cudaSuccess ||
+            dmalloc(&g->d_t, sizeof(TissueArgs)) != cudaSuccess ||
+            dmalloc(&g->d_dyn, sizeof(TissueDyn)) != cudaSuccess) {
+            cudaGetLastError();
             rc = BBX_ERR_NOMEM;
             break;
         }
         if (cudaMemsetAsync(g->d_ticket, 0, sizeof(unsigned int), g->stream) != cudaSuccess ||
-            cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream) != cudaSuccess) {
+            cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream) != cudaSuccess ||
+            cudaMemsetAsync(g->d_dyn, 0, sizeof(TissueDyn), g->stream) != cudaSuccess) {
+            cudaGetLastError();
             rc = BBX_ERR_CUDA;
             break;
         }
@@ -676,23 +862,26 @@ int bbx_create_grid(bbx_grid** out, int nx, int ny, int nz, double h, const uint
             for (long long i = 0; i < ncell; ++i) nt += mask_host[i] != 0;
             g->n_tissue = nt;
             if (dmalloc(&g->d_mask, (size_t)g->vol) != cudaSuccess) {
+                cudaGetLastError();
                 rc = BBX_ERR_NOMEM;
                 break;
             }
             if (cudaMemsetAsync(g->d_mask, 0, (size_t)g->vol, g->stream) != cudaSuccess) {
+                cudaGetLastError();
                 rc = BBX_ERR_CUDA;
                 break;
             }
-            // store 0/1 exactly
             std::vector<uint8_t> m01(ncell);
             for (long long i = 0; i < ncell; ++i) m01[i] = mask_host[i] ? 1 : 0;
             uint8_t* tmp = nullptr;
             if (dmalloc(&tmp, (size_t)g->vol) != cudaSuccess) {
+                cudaGetLastError();
                 rc = BBX_ERR_NOMEM;
                 break;
             }
             if (cudaMemsetAsync(tmp, 0, (size_t)g->vol, g->stream) != cudaSuccess ||
                 (rc = copy_in(g, tmp, m01.data(), 1)) != BBX_OK) {
+                cudaGetLastError();
                 cudaFree(tmp);
                 if (rc == BBX_OK) rc = BBX_ERR_CUDA;
                 break;
@@ -703,6 +892,7 @@ int bbx_create_grid(bbx_grid** out, int nx, int ny, int nz, double h, const uint
             const cudaError_t e2 = cudaStreamSynchronize(g->stream);
             cudaFree(tmp);
             if (e1 != cudaSuccess || e2 != cudaSuccess) {
+                cudaGetLastError();
                 rc = BBX_ERR_CUDA;
                 break;
             }
@@ -732,8 +922,12 @@ int bbx_set_fibres(bbx_grid* g, const float* f, double D_par, double D_perp) {
         float* fib = nullptr;
         const int pxf = (g->nx + 8 + 31) / 32 * 32;
         const long long fplane = (long long)pxf * g->ny, fvol = fplane * g->nz;
-        if (dmalloc(&tmp, sizeof(float) * 3 * g->ncell) != cudaSuccess) return BBX_ERR_NOMEM;
+        if (dmalloc(&tmp, sizeof(float) * 3 * g->ncell) != cudaSuccess) {
+            cudaGetLastError();
+            return BBX_ERR_NOMEM;
+        }
         if (dmalloc(&fib, sizeof(float) * 3 * fvol) != cudaSuccess) {
+            cudaGetLastError();
             cudaFree(tmp);
             return BBX_ERR_NOMEM;
         }
@@ -749,7 +943,7 @@ int bbx_set_fibres(bbx_grid* g, const float* f, double D_par, double D_perp) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream);
         cudaFree(tmp);
-        if (e != cudaSuccess) rc = BBX_ERR_CUDA;
+        if (e != cudaSuccess) rc = fail_cuda(e);
         else if (err & kErrFibre) rc = BBX_ERR_FIBRE;
         if (rc != BBX_OK) {
             cudaFree(fib);
@@ -764,6 +958,7 @@ int bbx_set_fibres(bbx_grid* g, const float* f, double D_par, double D_perp) {
         g->Dpar = D_par;
         g->Dperp = D_perp;
     }
+    if (g->dt > 0.0 && !stable(g, g->dt)) g->dt = 0.0;  // the next step must choose a stable dt
     if (g->model) return prepare(g);
     return BBX_OK;
 }
@@ -777,6 +972,7 @@ int bbx_set_ionic_model(bbx_grid* g, int model, const double* params, int n_para
     for (int i = 0; i < n_params && i < nd; ++i) p[i] = params[i];
     for (int i = 0; i < nd; ++i)
         if (!std::isfinite(p[i])) return BBX_ERR_ARG;
+    cudaStreamSynchronize(g->stream);
     if (g->bound && S != g->S) {
         g->bound = false;  // the caller's buffers no longer fit: back to library buffers
         g->d_state[0] = g->d_state[1] = nullptr;
@@ -786,10 +982,15 @@ int bbx_set_ionic_model(bbx_grid* g, int model, const double* params, int n_para
         cudaFree(g->d_state[1]);
         g->d_state[0] = g->d_state[1] = nullptr;
         if (dmalloc(&g->d_state[0], sizeof(float) * S * g->vol) != cudaSuccess ||
-            dmalloc(&g->d_state[1], sizeof(float) * S * g->vol) != cudaSuccess)
+            dmalloc(&g->d_state[1], sizeof(float) * S * g->vol) != cudaSuccess) {
+            cudaGetLastError();
             return BBX_ERR_NOMEM;
+        }
     }
-    if (!g->d_act && dmalloc(&g->d_act, sizeof(int32_t) * g->vol) != cudaSuccess) return BBX_ERR_NOMEM;
+    if (!g->d_act && dmalloc(&g->d_act, sizeof(int32_t) * g->vol) != cudaSuccess) {
+        cudaGetLastError();
+        return BBX_ERR_NOMEM;
+    }
     g->model = model;
     g->S = S;
     for (int i = 0; i < 8; ++i) g->par[i] = p[i];
@@ -804,10 +1005,8 @@ int bbx_set_ionic_model(bbx_grid* g, int model, const double* params, int n_para
     k_fill_int<<<n_blocks_for(g->vol, 256), 256, 0, g->stream>>>(g->d_act, g->vol, BBX_ACT_NONE);
     BBX_CUDA(cudaGetLastError());
     BBX_CUDA(cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream));
+    BBX_CUDA(cudaMemsetAsync(g->d_dyn, 0, sizeof(TissueDyn), g->stream));
     BBX_CUDA(cudaStreamSynchronize(g->stream));
-    g->cur = 0;
-    g->t = 0.0;
-    g->n = 0;
     g->stepped = false;
     return prepare(g);
 }
@@ -818,8 +1017,8 @@ int bbx_bind_state(bbx_grid* g, void* a, void* b, size_t bytes) {
     if (!a || !b || a == b || (reinterpret_cast<uintptr_t>(a) & 15) || (reinterpret_cast<uintptr_t>(b) & 15) ||
         bytes < sizeof(float) * g->S * (size_t)g->vol)
         return BBX_ERR_ARG;
+    cudaStreamSynchronize(g->stream);
     if (!g->bound) {
-        cudaStreamSynchronize(g->stream);
         cudaFree(g->d_state[0]);
         cudaFree(g->d_state[1]);
     }
@@ -830,8 +1029,11 @@ int bbx_bind_state(bbx_grid* g, void* a, void* b, size_t bytes) {
         k_fill_state<<<n_blocks_for((long long)g->S * g->vol, 256), 256, 0, g->stream>>>(g->d_state[k], g->S,
                                                                                             g->vol, g->d_rest);
     BBX_CUDA(cudaGetLastError());
-    BBX_CUDA(cudaStreamSynchronize(g->stream));
-    g->cur = 0;
+    TissueDyn d;
+    int rc = read_dyn(g, &d);
+    if (rc) return rc;
+    d.cur = 0;
+    if ((rc = write_dyn(g, d))) return rc;
     return prepare(g);
 }
 
@@ -839,13 +1041,14 @@ int bbx_write_state(bbx_grid* g, int var, const float* host, size_t n) {
     if (!g) return BBX_ERR_ARG;
     if (!g->model) return BBX_ERR_STATE;
     if (var < 0 || var >= g->S || !host || n != (size_t)g->ncell) return BBX_ERR_ARG;
-    float* cur = g->d_state[g->cur] + (size_t)var * g->vol;
-    float* oth = g->d_state[1 - g->cur] + (size_t)var * g->vol;
-    int rc = copy_in(g, cur, host, sizeof(float));
+    // both ping-pong buffers get the values (void nodes are never rewritten
+    // by a step, so the buffers must agree there): one copy from the host,
+    // one on the device
+    float* b0 = g->d_state[0] + (size_t)var * g->vol;
+    float* b1 = g->d_state[1] + (size_t)var * g->vol;
+    int rc = copy_in(g, b0, host, sizeof(float));
     if (rc) return rc;
-    // the other ping-pong buffer gets the same values (void nodes are never
-    // rewritten by a step, so both buffers must agree there)
-    BBX_CUDA(cudaMemcpyAsync(oth, cur, sizeof(float) * (size_t)g->vol, cudaMemcpyDeviceToDevice, g->stream));
+    BBX_CUDA(cudaMemcpyAsync(b1, b0, sizeof(float) * (size_t)g->vol, cudaMemcpyDeviceToDevice, g->stream));
     BBX_CUDA(cudaStreamSynchronize(g->stream));
     return BBX_OK;
 }
@@ -853,13 +1056,17 @@ int bbx_write_state(bbx_grid* g, int var, const float* host, size_t n) {
 int bbx_set_stimulus(bbx_grid* g, const uint8_t* region, double amp, double t_on, double t_off) {
     if (!g || !std::isfinite(amp) || std::isnan(t_on) || std::isnan(t_off)) return BBX_ERR_ARG;
     if (!region) {
+        cudaStreamSynchronize(g->stream);
         cudaFree(g->d_stim);
         g->d_stim = nullptr;
         g->stim_amp = 0.0;
-        return BBX_OK;
+        return g->model ? refresh_targs(g) : BBX_OK;
     }
     if (!g->d_stim) {
-        if (dmalloc(&g->d_stim, (size_t)g->vol) != cudaSuccess) return BBX_ERR_NOMEM;
+        if (dmalloc(&g->d_stim, (size_t)g->vol) != cudaSuccess) {
+            cudaGetLastError();
+            return BBX_ERR_NOMEM;
+        }
         BBX_CUDA(cudaMemsetAsync(g->d_stim, 0, (size_t)g->vol, g->stream));
     }
     std::vector<uint8_t> r01(g->ncell);
@@ -870,13 +1077,19 @@ int bbx_set_stimulus(bbx_grid* g, const uint8_t* region, double amp, double t_on
     g->stim_amp = amp;
     g->t_on = t_on;
     g->t_off = t_off;
-    return BBX_OK;
+    return g->model ? refresh_targs(g) : BBX_OK;
 }
 
 int bbx_set_threshold(bbx_grid* g, double theta) {
     if (!g || !std::isfinite(theta)) return BBX_ERR_ARG;
     g->theta = theta;
-    return BBX_OK;
+    return g->model ? refresh_targs(g) : BBX_OK;
+}
+
+int bbx_set_timestep(bbx_grid* g, double dt) {
+    if (!g) return BBX_ERR_ARG;
+    if (!g->model) return BBX_ERR_STATE;
+    return set_dt(g, dt);
 }
 
 int bbx_debug_poison_first_load(bbx_grid* g, int on) {
@@ -896,73 +1109,29 @@ int bbx_step(bbx_grid* g, double dt, int n_steps) {
     if (!g) return BBX_ERR_ARG;
     if (!g->model) return BBX_ERR_STATE;
     if (!(dt > 0.0) || !std::isfinite(dt) || n_steps < 0) return BBX_ERR_ARG;
-    const double Dmax = g->aniso ? std::max(g->Dpar, g->Dperp) : g->Dpar;
-    const double trD = g->aniso ? (g->Dpar + 2.0 * g->Dperp) : 3.0 * g->Dpar;
-    const double dD = g->aniso ? std::fabs(g->Dpar - g->Dperp) : 0.0;
-    (void)Dmax;
-    // Gershgorin bound on the spectrum of the discrete operator:
-    // |lambda| <= (4 tr D + 2 |Dpar - Dperp|) / h^2; forward Euler needs dt |lambda| <= 2.
-    if (dt * (4.0 * trD + 2.0 * dD) > 2.0 * g->h * g->h) return BBX_ERR_UNSTABLE;
+    int rc = set_dt(g, dt);
+    if (rc) return rc;
     if (n_steps == 0) return BBX_OK;
-    if (!g->maps_ok) {
-        int rc = prepare(g);
-        if (rc) return rc;
-    }
-    if (g->n_bricks == 0 || g->n_planes == 0) {
+    if (!g->ready && (rc = prepare(g))) return rc;
+    if (g->lp.n_planes == 0) {
         // no tissue: nothing moves, only time advances
-        g->t += dt * n_steps;
-        g->n += n_steps;
-        double zero = 0.0;
-        BBX_CUDA(cudaMemcpyAsync(g->d_total, &zero, sizeof(double), cudaMemcpyHostToDevice, g->stream));
-        BBX_CUDA(cudaStreamSynchronize(g->stream));
+        TissueDyn d;
+        if ((rc = read_dyn(g, &d))) return rc;
+        for (int s = 0; s < n_steps; ++s) {
+            d.t += dt;
+            d.n += 1;
+        }
+        d.total = 0.0;
+        if ((rc = write_dyn(g, d))) return rc;
         g->stepped = true;
         return BBX_OK;
     }
-    StepArgs a;
-    memset(&a, 0, sizeof(a));
-    a.nx = g->nx;
-    a.ny = g->ny;
-    a.nz = g->nz;
-    a.px = g->px;
-    a.plane = g->plane;
-    a.vol = g->vol;
-    a.pieces = g->d_pieces;
-    a.cta_off = g->d_cta_off;
-    a.act = g->d_act;
-    a.theta = (float)g->theta;
-    a.stim = g->d_stim;
-    a.dt = (float)dt;
-    {
-        const double ih2 = 1.0 / (g->h * g->h);
-        const double cd = (g->Dpar - g->Dperp) * ih2;
-        a.c_perp = (float)(g->Dperp * ih2);
-        a.c_d = (float)cd;
-        a.c_dh = (float)(0.5 * cd);
-        a.c_s = (float)(0.25 * cd);
-        a.c_iso = (float)(g->Dpar * ih2);
-    }
-    model_kernel_params(g->model, g->par, a.mp);
-    a.partials = g->d_partials;
-    a.ticket = g->d_ticket;
-    a.total_out = g->d_total;
-    a.err = g->d_err;
-    a.poison_first_load = g->poison;
-    a.wait_limit = g->poison ? kPoisonWaitLimit : kWaitLimitCycles;
+    const LaunchArgs L = launch_args(g->lp, g->d_t, g->d_err, g->poison);
     for (int s = 0; s < n_steps; ++s) {
-        const int src = g->cur, dst = 1 - g->cur;
-        a.dst = g->d_state[dst];
-        a.step_next = (int)(g->n + 1);
-        const bool on = g->d_stim && g->stim_amp != 0.0 && g->t >= g->t_on && g->t < g->t_off;
-        a.stim_amp = on ? (float)g->stim_amp : 0.0f;
-        void* args[] = {(void*)&g->tm_u[src], (void*)&g->tm_s[src], (void*)&g->tm_f, (void*)&g->tm_m, (void*)&a};
-        cudaError_t e = cudaLaunchKernel(g->kern.fn, dim3(g->grid_ctas), dim3(g->kern.threads), args,
-                                         (size_t)g->kern.smem, g->stream);
-        if (e != cudaSuccess) return BBX_ERR_CUDA;
-        g->cur = dst;
-        g->t += dt;
-        g->n += 1;
-        g->stepped = true;
+        const cudaError_t e = launch(g->lp, L, g->stream);
+        if (e != cudaSuccess) return fail_cuda(e);
     }
+    g->stepped = true;
     return BBX_OK;
 }
 
@@ -970,7 +1139,10 @@ int bbx_read_state(bbx_grid* g, int var, float* host, size_t n) {
     if (!g) return BBX_ERR_ARG;
     if (!g->model) return BBX_ERR_STATE;
     if (var < 0 || var >= g->S || !host || n != (size_t)g->ncell) return BBX_ERR_ARG;
-    int rc = copy_out(g, host, g->d_state[g->cur] + (size_t)var * g->vol, sizeof(float));
+    TissueDyn d;
+    int rc = read_dyn(g, &d);
+    if (rc) return rc;
+    rc = copy_out(g, host, g->d_state[d.cur] + (size_t)var * g->vol, sizeof(float));
     if (rc) return rc;
     return check_sticky(g);
 }
@@ -998,9 +1170,12 @@ int bbx_total(bbx_grid* g, int var, double* out) {
     if (!g) return BBX_ERR_ARG;
     if (!g->model) return BBX_ERR_STATE;
     if (var < 0 || var >= g->S || !out) return BBX_ERR_ARG;
+    TissueDyn d;
+    int rc = read_dyn(g, &d);
+    if (rc) return rc;
     int blocks = g->num_sms * 4;
     if (blocks > kMaxPartials) blocks = kMaxPartials;
-    k_total<<<blocks, 256, 0, g->stream>>>(g->d_state[g->cur] + (size_t)var * g->vol, g->d_mask, g->nx, g->ny,
+    k_total<<<blocks, 256, 0, g->stream>>>(g->d_state[d.cur] + (size_t)var * g->vol, g->d_mask, g->nx, g->ny,
                                            g->nz, g->px, g->plane, g->d_partials, g->d_ticket, g->d_total2, g->d_err);
     BBX_CUDA(cudaGetLastError());
     BBX_CUDA(cudaMemcpyAsync(out, g->d_total2, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
@@ -1010,26 +1185,39 @@ int bbx_total(bbx_grid* g, int var, double* out) {
 int bbx_step_total(bbx_grid* g, double* out) {
     if (!g || !out) return BBX_ERR_ARG;
     if (!g->stepped) return BBX_ERR_STATE;
-    BBX_CUDA(cudaMemcpyAsync(out, g->d_total, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    TissueDyn d;
+    int rc = read_dyn(g, &d);
+    if (rc) return rc;
+    *out = d.total;
     return check_sticky(g);
 }
 
 int bbx_get_time(bbx_grid* g, double* t, long long* step) {
     if (!g) return BBX_ERR_ARG;
-    if (t) *t = g->t;
-    if (step) *step = g->n;
+    TissueDyn d;
+    int rc = read_dyn(g, &d);
+    if (rc) return rc;
+    if (t) *t = d.t;
+    if (step) *step = d.n;
     return BBX_OK;
 }
 
 int bbx_set_time(bbx_grid* g, double t, long long step) {
     if (!g || !std::isfinite(t) || step < 0 || step >= 0x7fffffffLL) return BBX_ERR_ARG;
-    g->t = t;
-    g->n = step;
-    return BBX_OK;
+    TissueDyn d;
+    int rc = read_dyn(g, &d);
+    if (rc) return rc;
+    d.t = t;
+    d.n = step;
+    return write_dyn(g, d);
 }
 
 int bbx_get_info(bbx_grid* g, bbx_info* o) {
     if (!g || !o) return BBX_ERR_ARG;
+    TissueDyn d;
+    memset(&d, 0, sizeof(d));
+    int rc = read_dyn(g, &d);
+    if (rc) return rc;
     o->nx = g->nx;
     o->ny = g->ny;
     o->nz = g->nz;
@@ -1043,8 +1231,8 @@ int bbx_get_info(bbx_grid* g, bbx_info* o) {
     o->tile_z = g->zb;
     o->n_bricks = g->n_bricks;
     o->n_tissue = g->n_tissue;
-    o->step = g->n;
-    o->t = g->t;
+    o->step = d.n;
+    o->t = d.t;
     return BBX_OK;
 }
 
@@ -1052,9 +1240,8 @@ int bbx_read_active_bricks(bbx_grid* g, int32_t* out, size_t cap, long long* cou
     if (!g || !count) return BBX_ERR_ARG;
     *count = g->n_bricks;
     if ((size_t)g->n_bricks > cap || (!out && g->n_bricks > 0)) return BBX_ERR_ARG;
-    if (g->d_bricks) {
-        BBX_CUDA(cudaMemcpyAsync(out, g->d_bricks, sizeof(int32_t) * g->n_bricks, cudaMemcpyDeviceToHost, g->stream));
-        BBX_CUDA(cudaStreamSynchronize(g->stream));
+    if (g->d_mask) {
+        for (long long i = 0; i < g->n_bricks; ++i) out[i] = g->h_bricks[(size_t)i];
     } else {
         for (long long i = 0; i < g->n_bricks; ++i) out[i] = (int32_t)i;
     }
@@ -1081,27 +1268,39 @@ int bbx_state_device_ptr(bbx_grid* g, int var, void** p) {
     if (!g || !p) return BBX_ERR_ARG;
     if (!g->model) return BBX_ERR_STATE;
     if (var < 0 || var >= g->S) return BBX_ERR_ARG;
-    *p = g->d_state[g->cur] + (size_t)var * g->vol;
+    TissueDyn d;
+    int rc = read_dyn(g, &d);
+    if (rc) return rc;
+    *p = g->d_state[d.cur] + (size_t)var * g->vol;
     return BBX_OK;
 }
 
 int bbx_autotune(bbx_grid* g, double dt, double* best_ms) {
     if (!g) return BBX_ERR_ARG;
     if (!g->model) return BBX_ERR_STATE;
+    int rc = set_dt(g, dt);
+    if (rc) return rc;
     // save the state so the trial steps leave no trace
     const size_t sbytes = sizeof(float) * g->S * (size_t)g->vol;
     float* save = nullptr;
     int32_t* save_act = nullptr;
-    if (dmalloc(&save, sbytes) != cudaSuccess) return BBX_ERR_NOMEM;
+    if (dmalloc(&save, sbytes) != cudaSuccess) {
+            cudaGetLastError();
+            return BBX_ERR_NOMEM;
+        }
     if (dmalloc(&save_act, sizeof(int32_t) * g->vol) != cudaSuccess) {
+        cudaGetLastError();
         cudaFree(save);
         return BBX_ERR_NOMEM;
     }
-    BBX_CUDA(cudaMemcpyAsync(save, g->d_state[g->cur], sbytes, cudaMemcpyDeviceToDevice, g->stream));
+    TissueDyn d0;
+    if ((rc = read_dyn(g, &d0))) {
+        cudaFree(save);
+        cudaFree(save_act);
+        return rc;
+    }
+    BBX_CUDA(cudaMemcpyAsync(save, g->d_state[d0.cur], sbytes, cudaMemcpyDeviceToDevice, g->stream));
     BBX_CUDA(cudaMemcpyAsync(save_act, g->d_act, sizeof(int32_t) * g->vol, cudaMemcpyDeviceToDevice, g->stream));
-    const int cur0 = g->cur;
-    const double t0 = g->t;
-    const long long n0 = g->n;
     const bool stepped0 = g->stepped;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -1117,11 +1316,14 @@ int bbx_autotune(bbx_grid* g, double dt, double* best_ms) {
     }
     double best = 1e30;
     int bty = g->ty, bzb = g->zb;
-    int rc = BBX_OK;
+    rc = BBX_OK;
     for (int ty : tys) {
         for (int zb : zbs) {
             if ((rc = bbx_set_tiling(g, ty, zb)) != BBX_OK) {
-                if (rc == BBX_ERR_UNSUPPORTED) { rc = BBX_OK; continue; }
+                if (rc == BBX_ERR_UNSUPPORTED) {
+                    rc = BBX_OK;
+                    continue;
+                }
                 break;
             }
             if ((rc = bbx_step(g, dt, 2)) != BBX_OK) break;
@@ -1142,20 +1344,338 @@ int bbx_autotune(bbx_grid* g, double dt, double* best_ms) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     int rc2 = bbx_set_tiling(g, bty, bzb);
-    g->cur = cur0;
-    cudaMemcpyAsync(g->d_state[g->cur], save, sbytes, cudaMemcpyDeviceToDevice, g->stream);
-    cudaMemcpyAsync(g->d_state[1 - g->cur], save, sbytes, cudaMemcpyDeviceToDevice, g->stream);
+    cudaMemcpyAsync(g->d_state[0], save, sbytes, cudaMemcpyDeviceToDevice, g->stream);
+    cudaMemcpyAsync(g->d_state[1], save, sbytes, cudaMemcpyDeviceToDevice, g->stream);
     cudaMemcpyAsync(g->d_act, save_act, sizeof(int32_t) * g->vol, cudaMemcpyDeviceToDevice, g->stream);
     cudaStreamSynchronize(g->stream);
     cudaFree(save);
     cudaFree(save_act);
-    g->t = t0;
-    g->n = n0;
+    d0.cur = 0;
+    int rc3 = write_dyn(g, d0);
     g->stepped = stepped0;
     if (best_ms) *best_ms = best;
     if (rc) return rc;
     if (rc2) return rc2;
+    if (rc3) return rc3;
     return check_sticky(g);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batches of independent grids
+// ---------------------------------------------------------------------------
+
+struct bbx_batch {
+    struct Group {
+        int model = 0;
+        bool masked = false, aniso = false;
+        int ty = 16;
+        std::vector<int> members;  // indices into grids
+        TissueArgs* d_t = nullptr;  // one TissueArgs per member (tensor maps for this group's ty)
+        LaunchPlan lp;
+        cudaStream_t s = nullptr;
+        cudaEvent_t done = nullptr;
+        long long work = 0;
+    };
+    std::vector<bbx_grid*> grids;
+    std::vector<unsigned long long> versions;
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    std::vector<Group> groups;
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_steps = 0;
+    int* d_err = nullptr;
+    bool built = false;
+};
+
+namespace {
+
+void batch_release_groups(bbx_batch* b) {
+    for (auto& gr : b->groups) {
+        cudaFree(gr.d_t);
+        gr.lp.release();
+        if (gr.s) cudaStreamDestroy(gr.s);
+        if (gr.done) cudaEventDestroy(gr.done);
+    }
+    b->groups.clear();
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->gexec = nullptr;
+    b->graph = nullptr;
+    b->graph_steps = 0;
+    b->built = false;
+}
+
+// Group the grids by kernel type; give each group a share of the GPU's
+// resident CTAs proportional to its column-planes, so that all groups of a
+// step run side by side and finish together.
+int batch_build(bbx_batch* b, const std::vector<int>* tys) {
+    cudaStreamSynchronize(b->stream);
+    std::vector<int> keep_ty;
+    for (auto& gr : b->groups) keep_ty.push_back(gr.ty);
+    batch_release_groups(b);
+    for (size_t i = 0; i < b->grids.size(); ++i) {
+        bbx_grid* g = b->grids[i];
+        size_t gi = 0;
+        for (; gi < b->groups.size(); ++gi) {
+            auto& gr = b->groups[gi];
+            if (gr.model == g->model && gr.masked == (g->d_mask != nullptr) && gr.aniso == g->aniso) break;
+        }
+        if (gi == b->groups.size()) {
+            bbx_batch::Group gr;
+            gr.model = g->model;
+            gr.masked = g->d_mask != nullptr;
+            gr.aniso = g->aniso;
+            b->groups.push_back(gr);
+        }
+        b->groups[gi].members.push_back((int)i);
+    }
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        auto& gr = b->groups[gi];
+        if (tys && gi < tys->size()) gr.ty = (*tys)[gi];
+        else if (gi < keep_ty.size()) gr.ty = keep_ty[gi];
+    }
+    long long total_work = 0;
+    std::vector<std::vector<Seg>> segs(b->groups.size());
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        auto& gr = b->groups[gi];
+        std::vector<TissueArgs> ta(gr.members.size());
+        for (size_t m = 0; m < gr.members.size(); ++m) {
+            bbx_grid* g = b->grids[(size_t)gr.members[m]];
+            // columns for this group's tile rows
+            const int ty0 = g->ty;
+            if (g->ty != gr.ty) {
+                g->ty = gr.ty;
+                int rc = build_bricks(g);
+                if (rc) { g->ty = ty0; build_bricks(g); return rc; }
+            }
+            grid_segments(g, (int)m, &segs[gi]);
+            int rc = encode_targs(g, gr.ty, &ta[m]);
+            if (g->ty != ty0) {
+                g->ty = ty0;
+                build_bricks(g);
+            }
+            if (rc) return rc;
+        }
+        for (const Seg& sg : segs[gi]) gr.work += (long long)(sg.z1 - sg.z0);
+        total_work += gr.work;
+        if (dmalloc(&gr.d_t, sizeof(TissueArgs) * ta.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return BBX_ERR_NOMEM;
+        }
+        BBX_CUDA(cudaMemcpy(gr.d_t, ta.data(), sizeof(TissueArgs) * ta.size(), cudaMemcpyHostToDevice));
+        BBX_CUDA(cudaStreamCreateWithFlags(&gr.s, cudaStreamNonBlocking));
+        BBX_CUDA(cudaEventCreateWithFlags(&gr.done, cudaEventDisableTiming));
+    }
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        auto& gr = b->groups[gi];
+        int ctas = 0;
+        int rc = select_kernel(gr.model, gr.masked, gr.aniso, gr.ty, b->device, b->num_sms, &gr.lp.k, &ctas);
+        if (rc) return rc;
+        long long share = total_work > 0 ? (long long)((double)ctas * gr.work / total_work + 0.5) : 1;
+        if (share < 1) share = 1;
+        if ((rc = build_plan(&gr.lp, segs[gi], (int)gr.members.size(), (int)share))) return rc;
+    }
+    b->versions.clear();
+    for (bbx_grid* g : b->grids) b->versions.push_back(g->version);
+    b->built = true;
+    return BBX_OK;
+}
+
+int batch_launch_step(bbx_batch* b) {
+    BBX_CUDA(cudaEventRecord(b->fork, b->stream));
+    for (auto& gr : b->groups) {
+        if (gr.lp.n_planes == 0) continue;
+        BBX_CUDA(cudaStreamWaitEvent(gr.s, b->fork, 0));
+        const LaunchArgs L = launch_args(gr.lp, gr.d_t, b->d_err, 0);
+        BBX_CUDA(launch(gr.lp, L, gr.s));
+        BBX_CUDA(cudaEventRecord(gr.done, gr.s));
+        BBX_CUDA(cudaStreamWaitEvent(b->stream, gr.done, 0));
+    }
+    return BBX_OK;
+}
+
+int batch_capture(bbx_batch* b, int steps) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->gexec = nullptr;
+    b->graph = nullptr;
+    b->graph_steps = 0;
+    BBX_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = BBX_OK;
+    for (int s = 0; s < steps && rc == BBX_OK; ++s) rc = batch_launch_step(b);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail_cuda(e);
+    b->graph = graph;
+    BBX_CUDA(cudaGraphInstantiate(&b->gexec, graph, 0));
+    b->graph_steps = steps;
+    return BBX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bbx_batch_create(bbx_batch** out, bbx_grid* const* grids, int n) {
+    if (!out || !grids || n <= 0) return BBX_ERR_ARG;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!grids[i]) return BBX_ERR_ARG;
+        if (!grids[i]->model || !(grids[i]->dt > 0.0)) return BBX_ERR_STATE;
+        if (grids[i]->stream != grids[0]->stream || grids[i]->device != grids[0]->device) return BBX_ERR_ARG;
+        for (int j = 0; j < i; ++j)
+            if (grids[j] == grids[i]) return BBX_ERR_ARG;
+    }
+    bbx_batch* b = new (std::nothrow) bbx_batch();
+    if (!b) return BBX_ERR_NOMEM;
+    b->grids.assign(grids, grids + n);
+    b->stream = grids[0]->stream;
+    b->device = grids[0]->device;
+    b->num_sms = grids[0]->num_sms;
+    int rc = BBX_OK;
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        dmalloc(&b->d_err, sizeof(int)) != cudaSuccess || cudaMemset(b->d_err, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        rc = BBX_ERR_CUDA;
+    }
+    if (rc == BBX_OK) rc = batch_build(b, nullptr);
+    if (rc) {
+        bbx_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return BBX_OK;
+}
+
+void bbx_batch_destroy(bbx_batch* b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    batch_release_groups(b);
+    if (b->fork) cudaEventDestroy(b->fork);
+    cudaFree(b->d_err);
+    cudaGetLastError();
+    delete b;
+}
+
+int bbx_batch_step(bbx_batch* b, int n_steps) {
+    if (!b || n_steps < 0) return BBX_ERR_ARG;
+    if (n_steps == 0) return BBX_OK;
+    for (size_t i = 0; i < b->grids.size(); ++i) {
+        bbx_grid* g = b->grids[i];
+        if (!g->model || !(g->dt > 0.0)) return BBX_ERR_STATE;
+        if (g->version != b->versions[i]) b->built = false;  // a member changed since the batch was built
+    }
+    int rc;
+    if (!b->built && (rc = batch_build(b, nullptr))) return rc;
+    const int chunk = n_steps < 16 ? n_steps : 16;
+    if (n_steps >= 2 && b->graph_steps != chunk && (rc = batch_capture(b, chunk))) return rc;
+    int done = 0;
+    if (n_steps >= 2) {
+        for (; done + chunk <= n_steps; done += chunk) BBX_CUDA(cudaGraphLaunch(b->gexec, b->stream));
+    }
+    for (; done < n_steps; ++done)
+        if ((rc = batch_launch_step(b))) return rc;
+    for (bbx_grid* g : b->grids) g->stepped = true;
+    return BBX_OK;
+}
+
+int bbx_batch_sync(bbx_batch* b) {
+    if (!b) return BBX_ERR_ARG;
+    return check_sticky_ptr(b->stream, b->d_err);
+}
+
+int bbx_batch_autotune(bbx_batch* b, double* best_ms) {
+    if (!b) return BBX_ERR_ARG;
+    int rc;
+    if (!b->built && (rc = batch_build(b, nullptr))) return rc;
+    // save every member so the trial steps leave no trace
+    struct Saved {
+        float* st;
+        int32_t* act;
+        TissueDyn dyn;
+    };
+    std::vector<Saved> saved;
+    for (bbx_grid* g : b->grids) {
+        Saved sv{nullptr, nullptr, {}};
+        const size_t sbytes = sizeof(float) * g->S * (size_t)g->vol;
+        if (read_dyn(g, &sv.dyn) || dmalloc(&sv.st, sbytes) != cudaSuccess ||
+            dmalloc(&sv.act, sizeof(int32_t) * g->vol) != cudaSuccess) {
+            cudaGetLastError();
+            for (auto& s2 : saved) { cudaFree(s2.st); cudaFree(s2.act); }
+            cudaFree(sv.st);
+            return BBX_ERR_NOMEM;
+        }
+        cudaMemcpyAsync(sv.st, g->d_state[sv.dyn.cur], sbytes, cudaMemcpyDeviceToDevice, b->stream);
+        cudaMemcpyAsync(sv.act, g->d_act, sizeof(int32_t) * g->vol, cudaMemcpyDeviceToDevice, b->stream);
+        saved.push_back(sv);
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<int> tys;
+    for (auto& gr : b->groups) tys.push_back(gr.ty);
+    double best_total = 0;
+    rc = BBX_OK;
+    // one group at a time, the others at their current shape
+    for (size_t gi = 0; gi < tys.size() && rc == BBX_OK; ++gi) {
+        double best = 1e30;
+        int bty = tys[gi];
+        for (int ty : {8, 16, 32}) {
+            std::vector<int> trial = tys;
+            trial[gi] = ty;
+            int r = batch_build(b, &trial);
+            if (r == BBX_ERR_UNSUPPORTED) continue;
+            if (r) { rc = r; break; }
+            for (int s = 0; s < 2 && rc == BBX_OK; ++s) rc = batch_launch_step(b);
+            cudaEventRecord(e0, b->stream);
+            for (int s = 0; s < 4 && rc == BBX_OK; ++s) rc = batch_launch_step(b);
+            cudaEventRecord(e1, b->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms / 4.0 < best) {
+                best = ms / 4.0;
+                bty = ty;
+            }
+        }
+        tys[gi] = bty;
+        best_total = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int rc2 = batch_build(b, &tys);
+    for (size_t i = 0; i < b->grids.size(); ++i) {
+        bbx_grid* g = b->grids[i];
+        const size_t sbytes = sizeof(float) * g->S * (size_t)g->vol;
+        cudaMemcpyAsync(g->d_state[0], saved[i].st, sbytes, cudaMemcpyDeviceToDevice, b->stream);
+        cudaMemcpyAsync(g->d_state[1], saved[i].st, sbytes, cudaMemcpyDeviceToDevice, b->stream);
+        cudaMemcpyAsync(g->d_act, saved[i].act, sizeof(int32_t) * g->vol, cudaMemcpyDeviceToDevice, b->stream);
+        TissueDyn d = saved[i].dyn;
+        d.cur = 0;
+        cudaMemcpyAsync(g->d_dyn, &d, sizeof(TissueDyn), cudaMemcpyHostToDevice, b->stream);
+        cudaStreamSynchronize(b->stream);
+        cudaFree(saved[i].st);
+        cudaFree(saved[i].act);
+    }
+    if (best_ms) *best_ms = best_total;
+    if (rc) return rc;
+    if (rc2) return rc2;
+    return check_sticky_ptr(b->stream, b->d_err);
+}
+
+int bbx_batch_info(bbx_batch* b, int* n_groups, int* tile_y, int cap) {
+    if (!b || !n_groups) return BBX_ERR_ARG;
+    *n_groups = (int)b->groups.size();
+    for (int i = 0; i < *n_groups && tile_y && i < cap; ++i) tile_y[i] = b->groups[(size_t)i].ty;
+    return BBX_OK;
 }
 
 }  // extern "C"
