@@ -176,7 +176,7 @@ int bbx_get_info(bbx_grid* g, bbx_info* out);
  * *count receives the number of bricks.  Synchronises. */
 int bbx_read_active_bricks(bbx_grid* g, int32_t* out, size_t cap, long long* count);
 
-/* Choose the brick shape of the step kernel: tile_y in {8, 16, 32} rows of 64
+/* Choose the brick shape of the step kernel: tile_y in {7, 14, 28} rows of 64
  * nodes, and tile_z >= 1 planes per brick (the z-granularity at which idle
  * bricks of a masked grid are elided).  Rebuilds the brick list. */
 int bbx_set_tiling(bbx_grid* g, int tile_y, int tile_z);
@@ -217,7 +217,7 @@ int bbx_batch_step(bbx_batch* b, int n_steps);
  * steps (BBX_ERR_NAN, BBX_ERR_TIMEOUT). */
 int bbx_batch_sync(bbx_batch* b);
 
-/* Time the tile rows {8, 16, 32} of each kernel type on a few steps (member
+/* Time the tile rows {7, 14, 28} of each kernel type on a few steps (member
  * states restored afterwards) and keep the fastest.  best_ms may be NULL. */
 int bbx_batch_autotune(bbx_batch* b, double* best_ms);
 

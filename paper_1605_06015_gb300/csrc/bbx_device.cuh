@@ -233,18 +233,25 @@ __device__ __forceinline__ void step_finalize(const LaunchArgs& L, double* scrat
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int ti = threadIdx.x; ti < L.n_tissues; ti += blockDim.x) {
+    // one warp per grid; its lanes stride over the grid's pieces in a fixed
+    // order and reduce by a fixed shuffle tree (deterministic)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
+    for (int ti = warp; ti < L.n_tissues; ti += nwarps) {
+        const int k0 = __ldcg(&L.tissue_off[ti]), k1 = __ldcg(&L.tissue_off[ti + 1]);
         double s = 0.0;
-        for (int k = __ldcg(&L.tissue_off[ti]); k < __ldcg(&L.tissue_off[ti + 1]); ++k)
-            s += __ldcg(&L.partials[__ldcg(&L.tissue_pieces[k])]);
-        const TissueArgs* T = L.tissues + ti;
-        TissueDyn* d = T->dyn;
-        if (!isfinite(s)) atomicOr(L.err, ERRBIT_NAN);
-        d->total = s;
-        d->t = d->t + T->dt_d;
-        d->n = d->n + 1;
-        d->cur = d->cur ^ 1;
+        for (int k = k0 + lane; k < k1; k += 32) s += __ldcg(&L.partials[__ldcg(&L.tissue_pieces[k])]);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            const TissueArgs* T = L.tissues + ti;
+            TissueDyn* d = T->dyn;
+            if (!isfinite(s)) atomicOr(L.err, ERRBIT_NAN);
+            d->total = s;
+            d->t = d->t + T->dt_d;
+            d->n = d->n + 1;
+            d->cur = d->cur ^ 1;
+        }
     }
+    __syncthreads();
     (void)scratch32;
     if (threadIdx.x == 0) *L.ticket = 0u;
 }
@@ -366,7 +373,7 @@ struct Model<BBX_BR> {
 // ---------------------------------------------------------------------------
 
 constexpr int kTileX = 64;  // nodes per brick along x: 32 threads x 2 nodes
-constexpr int kRowsOfThreads = 8;  // thread rows per CTA (256 threads)
+constexpr int kRowsOfThreads = 7;  // consumer warps per CTA (plus one producer warp: 256 threads)
 constexpr int align128(int b) { return (b + 127) & ~127; }
 
 // Tissue-mask byte on the device: bit 0 = tissue, bit 1 = tissue node whose
@@ -379,7 +386,7 @@ struct Plan {
     static constexpr int TX = kTileX;
     static constexpr int RY = kRowsOfThreads;
     static constexpr int CY = TY / RY;  // nodes per thread along y (each a pair in x)
-    static constexpr int THREADS = 32 * RY;
+    static constexpr int THREADS = 32 * RY + 32;  // consumer warps + producer warp
     static constexpr int UW = TX + 8;   // x from x0-4 to x0+TX+3 (16-byte aligned start)
     static constexpr int UH = TY + 2;   // y from y0-1 to y0+TY
     static constexpr int MW = TX + 32;  // mask bytes: x from x0-16 (16-byte aligned start)
@@ -394,9 +401,9 @@ struct Plan {
     static constexpr int STAGE = S_OFF + align128(S_RAW);
     static constexpr uint32_t TX_BYTES = U_RAW + F_RAW + M_RAW + S_RAW;  // plane computed in this piece
     static constexpr uint32_t TX_BYTES_HALO = U_RAW + F_RAW + M_RAW;     // z-halo plane: no other vars
-    static constexpr int NS_FIT = (110 * 1024) / STAGE;
+    static constexpr int NS_FIT = (112 * 1024) / STAGE;  // two CTAs per SM where the stage allows
     static constexpr int NS = NS_FIT > 8 ? 8 : (NS_FIT < 4 ? 4 : NS_FIT);
-    static constexpr int SMEM = 128 + NS * STAGE + NS * 8;
+    static constexpr int SMEM = 128 + NS * STAGE + 2 * NS * 8 + NS * 160;  // stages, full/empty rings, piece ring
     static_assert(TY % RY == 0 && CY >= 1, "tile rows must be a multiple of the thread rows");
 };
 
@@ -541,8 +548,11 @@ __device__ __forceinline__ float lap_general(const Coef& a, const Nb& n, const P
 // the fused step kernel
 // ---------------------------------------------------------------------------
 
-// Per-piece view of the grid being stepped (loaded from its TissueArgs).
-struct PieceCtx : Coef {
+// Per-piece context, written into a shared ring by the producer warp when it
+// issues the piece's first plane load, and read by the consumer warps once
+// that load has landed (the mbarrier orders the two).
+struct PieceSlot : Coef {
+    int x0, y0, z0, z1;
     int nx, ny, nz, px;
     long long plane, vol;
     float* dst;
@@ -550,330 +560,390 @@ struct PieceCtx : Coef {
     const uint8_t* stim;
     float stim_amp, dt, theta;
     int step_next;
+    float mp[8];
 };
 
+
+// Barrier over the consumer warps only (named barrier 1), returning the OR of
+// a per-thread predicate.
+__device__ __forceinline__ bool consumers_sync_or(bool p, int nthreads) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\t"
+        "setp.ne.u32 pi, %1, 0;\n\t"
+        "bar.red.or.pred po, 1, %2, pi;\n\t"
+        "selp.u32 %0, 1, 0, po;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)p), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void consumers_sync(int nthreads) {
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// Warp-specialised step kernel: warps 0..7 compute (2 x CY nodes per thread),
+// warp 8 is the producer.  Stage slots cycle through two mbarrier rings:
+// full[s] completes when the plane's bulk copies have landed, empty[s] when
+// all 8 consumer warps are done with the plane.  No CTA-wide barrier is taken
+// per plane.
 template <int MODEL, bool MASKED, bool ANISO, int TY>
-__global__ void __launch_bounds__(32 * kRowsOfThreads, (MASKED && ANISO) || TY == 32 ? 1 : 2)
+__global__ void __launch_bounds__(32 * kRowsOfThreads + 32, (MASKED && ANISO) || TY == 28 ? 1 : 2)
 step_kernel(const __grid_constant__ LaunchArgs L) {
     using P = Plan<MODEL, MASKED, ANISO, TY>;
     constexpr int S = P::S, TX = P::TX, UW = P::UW, MW = P::MW, NS = P::NS, CY = P::CY;
+    constexpr int NCW = kRowsOfThreads;  // consumer warps
+    constexpr int NCT = 32 * NCW;        // consumer threads
     static_assert(TX == 64, "pair mapping assumes 64-node rows");
     constexpr int FC = UW * P::UH;  // fibre component stride in a stage
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NS * P::STAGE);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * P::STAGE);
+    uint64_t* empty = full + NS;
+    PieceSlot* ring = reinterpret_cast<PieceSlot*>(empty + NS);
     __shared__ double red_scratch[32];
+    __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x;
-    const int tx = tid % 32, row0 = (tid / 32) * CY;  // node pair (x, x+1) = x0 + 2 tx
+    const int warp = tid / 32, lane = tid % 32;
 
     if (tid == 0) {
-        for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCW);
+        }
+        abort_flag = 0;
         mbar_init_fence();
     }
     __syncthreads();
 
-    // ---- producer state (thread 0 only) ----
     const int piece_begin = L.cta_off[blockIdx.x], piece_end = L.cta_off[blockIdx.x + 1];
-    int p_piece = piece_begin, p_off = 0, issued = 0;
-    auto issue_next = [&]() -> bool {
-        if (p_piece >= piece_end) return false;
-        const int4 pc = L.pieces[p_piece];
-        const TissueArgs* T = L.tissues + L.piece_tissue[p_piece];
-        const int src = T->dyn->cur;
-        const int nload = pc.w - pc.z + 2;
-        const int z = pc.z - 1 + p_off;
-        const bool halo = (p_off == 0) || (p_off == nload - 1);
-        const int slot = issued % NS;
-        uint64_t* bar = &bars[slot];
-        unsigned char* st = smem + slot * P::STAGE;
-        if (L.poison_first_load && blockIdx.x == 0 && issued == 0) {
-            mbar_arrive_expect_tx(bar, 16);  // fault injection: bytes no copy delivers
-        } else if (z < 0 || z >= T->nz) {
-            mbar_arrive(bar);  // plane outside the array: nothing to load
-        } else {
-            mbar_arrive_expect_tx(bar, (halo || S == 1) ? P::TX_BYTES_HALO : P::TX_BYTES);
-            tma_load_3d(st + P::U_OFF, &T->tm_u[src], pc.x - 4, pc.y - 1, z, bar);
-            if (ANISO) tma_load_4d(st + P::F_OFF, &T->tm_f, pc.x, pc.y - 1, z, 0, bar);  // fibre x offset 4
-            if (MASKED) tma_load_3d(st + P::M_OFF, &T->tm_m, pc.x - 16, pc.y - 1, z, bar);
-            if (S > 1 && !halo) tma_load_4d(st + P::S_OFF, &T->tm_s[src], pc.x, pc.y, z, 1, bar);
-        }
-        ++issued;
-        if (++p_off == nload) {
-            p_off = 0;
-            ++p_piece;
-        }
-        return true;
-    };
-    if (tid == 0) {
-        while (issued < NS && issue_next()) {
-        }
-    }
+    int issued = 0;  // producer lane 0: plane loads issued
 
-    // ---- consumer ----
-    F2 vsum = {0.0f, 0.0f};
-    bool timed_out = false, abort = false;
-    int jb = 0;  // load index of the first plane of the current piece
-
-    for (int pi = piece_begin; pi < piece_end; ++pi) {
-        const int4 pc = L.pieces[pi];
-        PieceCtx a;
-        float mp[8];
-        float theta;
-        {
-            const TissueArgs* T = L.tissues + L.piece_tissue[pi];
-            const TissueDyn* D = T->dyn;
-            const int src = D->cur;
-            const double tn = D->t;
-            a.nx = T->nx; a.ny = T->ny; a.nz = T->nz; a.px = T->px;
-            a.plane = T->plane; a.vol = T->vol;
-            a.dst = T->state[src ^ 1];
-            a.act = T->act;
-            a.stim = T->stim;
-            a.stim_amp = (T->stim && T->stim_amp != 0.0f && tn >= T->t_on && tn < T->t_off) ? T->stim_amp : 0.0f;
-            a.dt = T->dt;
-            a.theta = T->theta;
-            a.step_next = (int)(D->n + 1);
-            a.c_perp = T->c_perp; a.c_d = T->c_d; a.c_dh = T->c_dh; a.c_s = T->c_s; a.c_iso = T->c_iso;
+    if (warp == NCW) {
+        // ---------------- producer warp ----------------
+        if (lane == 0) {
+            bool stop = false;
+            int lp = 0;
+            for (int pi = piece_begin; pi < piece_end && !stop; ++pi, ++lp) {
+                const int4 pc = L.pieces[pi];
+                const TissueArgs* T = L.tissues + L.piece_tissue[pi];
+                const TissueDyn* D = T->dyn;
+                const int src = D->cur;
+                const int nz = T->nz;
+                const int nload = pc.w - pc.z + 2;
+                for (int off = 0; off < nload; ++off) {
+                    const int slot = issued % NS;
+                    if (L.poison_first_load && blockIdx.x == 0 && issued == 0) {
+                        // fault injection: wait for an empty-slot phase that no
+                        // consumer completes; the bounded wait runs out
+                        (void)mbar_wait_bounded(&empty[slot], 0, L.wait_limit);
+                        stop = true;
+                    } else if (issued >= NS &&
+                               !mbar_wait_bounded(&empty[slot], ((issued / NS) - 1) & 1, L.wait_limit)) {
+                        stop = true;
+                    }
+                    if (stop || abort_flag) {
+                        stop = true;
+                        break;
+                    }
+                    if (off == 0) {
+                        PieceSlot& r = ring[lp % NS];
+                        const double tn = D->t;
+                        r.x0 = pc.x; r.y0 = pc.y; r.z0 = pc.z; r.z1 = pc.w;
+                        r.nx = T->nx; r.ny = T->ny; r.nz = nz; r.px = T->px;
+                        r.plane = T->plane; r.vol = T->vol;
+                        r.dst = T->state[src ^ 1];
+                        r.act = T->act;
+                        r.stim = T->stim;
+                        r.stim_amp = (T->stim && T->stim_amp != 0.0f && tn >= T->t_on && tn < T->t_off) ? T->stim_amp
+                                                                                                       : 0.0f;
+                        r.dt = T->dt;
+                        r.theta = T->theta;
+                        r.step_next = (int)(D->n + 1);
+                        r.c_perp = T->c_perp; r.c_d = T->c_d; r.c_dh = T->c_dh; r.c_s = T->c_s; r.c_iso = T->c_iso;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) mp[i] = T->mp[i];
-            theta = a.theta;
-        }
-        const int x = pc.x + 2 * tx;  // first node of this thread's pair
-        const int yb = pc.y + row0;   // y of this thread's first row
-        const bool x_in = x < a.nx;
-        const int ncomp = pc.w - pc.z;
-
-        for (int w = 0; w < 2; ++w) {
-            const int j = jb + w;
-            if (!mbar_wait_bounded(&bars[j % NS], (j / NS) & 1, L.wait_limit)) timed_out = true;
-        }
-        for (int t = 0; t < ncomp; ++t) {
-            {
-                const int j = jb + t + 2;
-                if (!mbar_wait_bounded(&bars[j % NS], (j / NS) & 1, L.wait_limit)) timed_out = true;
-            }
-            const int k = pc.z + t;
-            const unsigned char* stp = smem + ((jb + t) % NS) * P::STAGE;
-            const unsigned char* stc = smem + ((jb + t + 1) % NS) * P::STAGE;
-            const unsigned char* stn = smem + ((jb + t + 2) % NS) * P::STAGE;
-            const float* Up = reinterpret_cast<const float*>(stp + P::U_OFF);
-            const float* Uc = reinterpret_cast<const float*>(stc + P::U_OFF);
-            const float* Un = reinterpret_cast<const float*>(stn + P::U_OFF);
-            const float* Fp = reinterpret_cast<const float*>(stp + P::F_OFF);
-            const float* Fc = reinterpret_cast<const float*>(stc + P::F_OFF);
-            const float* Fn = reinterpret_cast<const float*>(stn + P::F_OFF);
-            const unsigned char* Mp = stp + P::M_OFF;
-            const unsigned char* Mc = stc + P::M_OFF;
-            const unsigned char* Mn = stn + P::M_OFF;
-            const float* Sv = reinterpret_cast<const float*>(stc + P::S_OFF);
-            const bool zn_ok = k + 1 < a.nz, zp_ok = k > 0;
-            const int c0 = (row0 + 1) * UW + (2 * tx + 4);   // stage index of node (x, yb), even
-            const int m0 = (row0 + 1) * MW + (2 * tx + 16);  // mask index of node (x, yb)
-
-            if (x_in) {
-                auto ld2 = [&](const float* U, int o) { return *reinterpret_cast<const float2*>(U + o); };
-                const bool x1_in = x + 1 < a.nx;
-                // psi of the x neighbours of the two nodes (unmasked grids)
-                const float px0 = x1_in ? 1.0f : 0.0f, mx0 = (x > 0) ? 1.0f : 0.0f;
-                const float px1 = (x + 2 < a.nx) ? 1.0f : 0.0f, mx1 = 1.0f;
-
-                // phase 1: the stencil for the 2 x CY nodes of this thread.
-                // Sliding window down the rows: plane k at x-2..x+3 (three
-                // float2), own pair of planes k+-1, own pair of fibres.
-                float Lr[CY][2], u0r[CY][2];
-                bool live[CY][2];
-                float2 wA[3], wB[3], wC[3], wN[3], wP[3];
-                float2 wFx[3], wFy[3], wFz[3];
-#pragma unroll
-                for (int w = 0; w < 2; ++w) {
-                    const int o = c0 + (w - 1) * UW;
-                    wA[w] = ld2(Uc, o - 2); wB[w] = ld2(Uc, o); wC[w] = ld2(Uc, o + 2);
-                    wN[w] = ld2(Un, o); wP[w] = ld2(Up, o);
-                    if (ANISO) { wFx[w] = ld2(Fc, o); wFy[w] = ld2(Fc + FC, o); wFz[w] = ld2(Fc + 2 * FC, o); }
+                        for (int i = 0; i < 8; ++i) r.mp[i] = T->mp[i];
+                    }
+                    const int z = pc.z - 1 + off;
+                    const bool halo = (off == 0) || (off == nload - 1);
+                    uint64_t* bar = &full[slot];
+                    unsigned char* st = smem + slot * P::STAGE;
+                    if (z < 0 || z >= nz) {
+                        mbar_arrive(bar);  // plane outside the array: nothing to load
+                    } else {
+                        mbar_arrive_expect_tx(bar, (halo || S == 1) ? P::TX_BYTES_HALO : P::TX_BYTES);
+                        tma_load_3d(st + P::U_OFF, &T->tm_u[src], pc.x - 4, pc.y - 1, z, bar);
+                        if (ANISO) tma_load_4d(st + P::F_OFF, &T->tm_f, pc.x, pc.y - 1, z, 0, bar);  // fibre x offset 4
+                        if (MASKED) tma_load_3d(st + P::M_OFF, &T->tm_m, pc.x - 16, pc.y - 1, z, bar);
+                        if (S > 1 && !halo) tma_load_4d(st + P::S_OFF, &T->tm_s[src], pc.x, pc.y, z, 1, bar);
+                    }
+                    ++issued;
                 }
-#pragma unroll
-                for (int r = 0; r < CY; ++r) {
-                    const int y = yb + r;
-                    const int c = c0 + r * UW;
-                    const int m = m0 + r * MW;
-                    {
-                        const int o = c + UW;  // row r+1
-                        wA[2] = ld2(Uc, o - 2); wB[2] = ld2(Uc, o); wC[2] = ld2(Uc, o + 2);
-                        wN[2] = ld2(Un, o); wP[2] = ld2(Up, o);
-                        if (ANISO) { wFx[2] = ld2(Fc, o); wFy[2] = ld2(Fc + FC, o); wFz[2] = ld2(Fc + 2 * FC, o); }
+            }
+            if (stop) abort_flag = 1;
+        }
+        __syncwarp();
+    } else {
+        // ---------------- consumer warps ----------------
+        const int tx = tid % 32, row0 = (tid / 32) * CY;  // node pair (x, x+1) = x0 + 2 tx
+        F2 vsum = {0.0f, 0.0f};
+        bool timed_out = false;
+        int jb = 0, lp = 0;  // load index of the first plane of the piece, local piece index
+        auto wait_full = [&](int j) {
+            if (timed_out || abort_flag) {
+                timed_out = true;
+                return;
+            }
+            if (!mbar_wait_bounded(&full[j % NS], (j / NS) & 1, L.wait_limit)) {
+                timed_out = true;
+                abort_flag = 1;
+            }
+        };
+        for (int pi = piece_begin; pi < piece_end; ++pi, ++lp) {
+            wait_full(jb);  // the piece's first load carries its context
+            const PieceSlot& a = ring[lp % NS];  // read from shared memory where used
+            const float* mp = a.mp;
+            const float theta = a.theta;
+            int4 pc = make_int4(a.x0, a.y0, a.z0, a.z1);
+            if (timed_out) pc.w = pc.z = 0;  // context unreliable: compute nothing
+            const int x = pc.x + 2 * tx;  // first node of this thread's pair
+            const int yb = pc.y + row0;   // y of this thread's first row
+            const bool x_in = x < a.nx && !timed_out;
+            const int ncomp = pc.w - pc.z;
+            wait_full(jb + 1);
+            for (int t = 0; t < ncomp; ++t) {
+                wait_full(jb + t + 2);
+                const int k = pc.z + t;
+                const unsigned char* stp = smem + ((jb + t) % NS) * P::STAGE;
+                const unsigned char* stc = smem + ((jb + t + 1) % NS) * P::STAGE;
+                const unsigned char* stn = smem + ((jb + t + 2) % NS) * P::STAGE;
+                const float* Up = reinterpret_cast<const float*>(stp + P::U_OFF);
+                const float* Uc = reinterpret_cast<const float*>(stc + P::U_OFF);
+                const float* Un = reinterpret_cast<const float*>(stn + P::U_OFF);
+                const float* Fp = reinterpret_cast<const float*>(stp + P::F_OFF);
+                const float* Fc = reinterpret_cast<const float*>(stc + P::F_OFF);
+                const float* Fn = reinterpret_cast<const float*>(stn + P::F_OFF);
+                const unsigned char* Mp = stp + P::M_OFF;
+                const unsigned char* Mc = stc + P::M_OFF;
+                const unsigned char* Mn = stn + P::M_OFF;
+                const float* Sv = reinterpret_cast<const float*>(stc + P::S_OFF);
+                const bool zn_ok = k + 1 < a.nz, zp_ok = k > 0;
+                const int c0 = (row0 + 1) * UW + (2 * tx + 4);   // stage index of node (x, yb), even
+                const int m0 = (row0 + 1) * MW + (2 * tx + 16);  // mask index of node (x, yb)
+    
+                if (x_in) {
+                    auto ld2 = [&](const float* U, int o) { return *reinterpret_cast<const float2*>(U + o); };
+                    const bool x1_in = x + 1 < a.nx;
+                    // psi of the x neighbours of the two nodes (unmasked grids)
+                    const float px0 = x1_in ? 1.0f : 0.0f, mx0 = (x > 0) ? 1.0f : 0.0f;
+                    const float px1 = (x + 2 < a.nx) ? 1.0f : 0.0f, mx1 = 1.0f;
+    
+                    // phase 1: the stencil for the 2 x CY nodes of this thread.
+                    // Sliding window down the rows: plane k at x-2..x+3 (three
+                    // float2), own pair of planes k+-1, own pair of fibres.
+                    float Lr[CY][2], u0r[CY][2];
+                    bool live[CY][2];
+                    float2 wA[3], wB[3], wC[3], wN[3], wP[3];
+                    float2 wFx[3], wFy[3], wFz[3];
+    #pragma unroll
+                    for (int w = 0; w < 2; ++w) {
+                        const int o = c0 + (w - 1) * UW;
+                        wA[w] = ld2(Uc, o - 2); wB[w] = ld2(Uc, o); wC[w] = ld2(Uc, o + 2);
+                        wN[w] = ld2(Un, o); wP[w] = ld2(Up, o);
+                        if (ANISO) { wFx[w] = ld2(Fc, o); wFy[w] = ld2(Fc + FC, o); wFz[w] = ld2(Fc + 2 * FC, o); }
                     }
-                    bool tis[2] = {y < a.ny, y < a.ny && x1_in}, intr[2];
-                    if (MASKED) {
-                        const unsigned char mc0 = Mc[m], mc1 = Mc[m + 1];
-                        tis[0] = tis[0] && (mc0 & MASK_TISSUE);
-                        tis[1] = tis[1] && (mc1 & MASK_TISSUE);
-                        intr[0] = (mc0 & MASK_INTERIOR) != 0;
-                        intr[1] = (mc1 & MASK_INTERIOR) != 0;
-                    } else {
-                        intr[0] = intr[1] = (y > 0) && (y + 1 < a.ny) && zp_ok && zn_ok;  // warp-uniform
-                    }
-                    Nb n[2];
-                    F3 f[2], fxp[2], fxm[2], fyp[2], fym[2], fzp[2], fzm[2];
-                    n[0].u0 = wB[1].x; n[0].xp = wB[1].y; n[0].xm = wA[1].y;
-                    n[0].yp = wB[2].x; n[0].ym = wB[0].x; n[0].zp = wN[1].x; n[0].zm = wP[1].x;
-                    n[1].u0 = wB[1].y; n[1].xp = wC[1].x; n[1].xm = wB[1].x;
-                    n[1].yp = wB[2].y; n[1].ym = wB[0].y; n[1].zp = wN[1].y; n[1].zm = wP[1].y;
-                    if (ANISO) {
-                        const float2 nA = ld2(Un, c - 2), nC = ld2(Un, c + 2);
-                        const float2 pA = ld2(Up, c - 2), pC = ld2(Up, c + 2);
-                        n[0].pp = wB[2].y; n[0].mm = wA[0].y; n[0].pm = wB[0].y; n[0].mp = wA[2].y;
-                        n[0].xpzp = wN[1].y; n[0].xmzm = pA.y; n[0].xpzm = wP[1].y; n[0].xmzp = nA.y;
-                        n[0].ypzp = wN[2].x; n[0].ymzm = wP[0].x; n[0].ypzm = wP[2].x; n[0].ymzp = wN[0].x;
-                        n[1].pp = wC[2].x; n[1].mm = wB[0].x; n[1].pm = wC[0].x; n[1].mp = wB[2].x;
-                        n[1].xpzp = nC.x; n[1].xmzm = wP[1].x; n[1].xpzm = pC.x; n[1].xmzp = wN[1].x;
-                        n[1].ypzp = wN[2].y; n[1].ymzm = wP[0].y; n[1].ypzm = wP[2].y; n[1].ymzp = wN[0].y;
-                        const float2 fAx = ld2(Fc, c - 2), fAy = ld2(Fc + FC, c - 2), fAz = ld2(Fc + 2 * FC, c - 2);
-                        const float2 fCx = ld2(Fc, c + 2), fCy = ld2(Fc + FC, c + 2), fCz = ld2(Fc + 2 * FC, c + 2);
-                        const float2 fNx = ld2(Fn, c), fNy = ld2(Fn + FC, c), fNz = ld2(Fn + 2 * FC, c);
-                        const float2 fPx = ld2(Fp, c), fPy = ld2(Fp + FC, c), fPz = ld2(Fp + 2 * FC, c);
-                        f[0] = F3{wFx[1].x, wFy[1].x, wFz[1].x};
-                        f[1] = F3{wFx[1].y, wFy[1].y, wFz[1].y};
-                        fxp[0] = f[1];
-                        fxm[0] = F3{fAx.y, fAy.y, fAz.y};
-                        fxp[1] = F3{fCx.x, fCy.x, fCz.x};
-                        fxm[1] = f[0];
-                        fyp[0] = F3{wFx[2].x, wFy[2].x, wFz[2].x};
-                        fyp[1] = F3{wFx[2].y, wFy[2].y, wFz[2].y};
-                        fym[0] = F3{wFx[0].x, wFy[0].x, wFz[0].x};
-                        fym[1] = F3{wFx[0].y, wFy[0].y, wFz[0].y};
-                        fzp[0] = F3{fNx.x, fNy.x, fNz.x};
-                        fzp[1] = F3{fNx.y, fNy.y, fNz.y};
-                        fzm[0] = F3{fPx.x, fPy.x, fPz.x};
-                        fzm[1] = F3{fPx.y, fPy.y, fPz.y};
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            f[e] = F3{0.f, 0.f, 0.f};
-                            fxp[e] = fxm[e] = fyp[e] = fym[e] = fzp[e] = fzm[e] = f[e];
+    #pragma unroll
+                    for (int r = 0; r < CY; ++r) {
+                        const int y = yb + r;
+                        const int c = c0 + r * UW;
+                        const int m = m0 + r * MW;
+                        {
+                            const int o = c + UW;  // row r+1
+                            wA[2] = ld2(Uc, o - 2); wB[2] = ld2(Uc, o); wC[2] = ld2(Uc, o + 2);
+                            wN[2] = ld2(Un, o); wP[2] = ld2(Up, o);
+                            if (ANISO) { wFx[2] = ld2(Fc, o); wFy[2] = ld2(Fc + FC, o); wFz[2] = ld2(Fc + 2 * FC, o); }
                         }
-                    }
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        live[r][e] = tis[e];
-                        u0r[r][e] = n[e].u0;
-                        // fast formula for every node (values of void or
-                        // out-of-array nodes are finite and never stored) ...
-                        if (MASKED)
-                            Lr[r][e] = lap_interior<ANISO>(a, n[e], f[e], fxp[e], fxm[e], fyp[e], fym[e], fzp[e],
-                                                           fzm[e]);
-                        else
-                            Lr[r][e] = lap_xbound<ANISO>(a, n[e], e ? px1 : px0, e ? mx1 : mx0, f[e], fxp[e],
-                                                         fxm[e], fyp[e], fym[e], fzp[e], fzm[e]);
-                    }
-                    // ... and the general one where a y/z neighbour (or, in a
-                    // masked grid, any neighbour) may be void: rare, and
-                    // warp-uniform on unmasked grids
-                    if (!((intr[0] || !tis[0]) && (intr[1] || !tis[1]))) {
-#pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            if (!tis[e] || intr[e]) continue;
-                            const int xe = x + e, me = m + e;
-                            Psi q;
-                            if (MASKED) {
-                                q.xp = Mc[me + 1] != 0; q.xm = Mc[me - 1] != 0;
-                                q.yp = Mc[me + MW] != 0; q.ym = Mc[me - MW] != 0;
-                                q.zp = zn_ok && Mn[me] != 0; q.zm = zp_ok && Mp[me] != 0;
-                                q.pp = Mc[me + MW + 1] != 0; q.mm = Mc[me - MW - 1] != 0;
-                                q.pm = Mc[me - MW + 1] != 0; q.mp = Mc[me + MW - 1] != 0;
-                                q.xpzp = zn_ok && Mn[me + 1] != 0; q.xmzm = zp_ok && Mp[me - 1] != 0;
-                                q.xpzm = zp_ok && Mp[me + 1] != 0; q.xmzp = zn_ok && Mn[me - 1] != 0;
-                                q.ypzp = zn_ok && Mn[me + MW] != 0; q.ymzm = zp_ok && Mp[me - MW] != 0;
-                                q.ypzm = zp_ok && Mp[me + MW] != 0; q.ymzp = zn_ok && Mn[me - MW] != 0;
-                            } else {
-                                const bool xp = xe + 1 < a.nx, xm = xe > 0, yp = y + 1 < a.ny, ym = y > 0;
-                                q.xp = xp; q.xm = xm; q.yp = yp; q.ym = ym; q.zp = zn_ok; q.zm = zp_ok;
-                                q.pp = xp && yp; q.mm = xm && ym; q.pm = xp && ym; q.mp = xm && yp;
-                                q.xpzp = xp && zn_ok; q.xmzm = xm && zp_ok; q.xpzm = xp && zp_ok; q.xmzp = xm && zn_ok;
-                                q.ypzp = yp && zn_ok; q.ymzm = ym && zp_ok; q.ypzm = yp && zp_ok; q.ymzp = ym && zn_ok;
+                        bool tis[2] = {y < a.ny, y < a.ny && x1_in}, intr[2];
+                        if (MASKED) {
+                            const unsigned char mc0 = Mc[m], mc1 = Mc[m + 1];
+                            tis[0] = tis[0] && (mc0 & MASK_TISSUE);
+                            tis[1] = tis[1] && (mc1 & MASK_TISSUE);
+                            intr[0] = (mc0 & MASK_INTERIOR) != 0;
+                            intr[1] = (mc1 & MASK_INTERIOR) != 0;
+                        } else {
+                            intr[0] = intr[1] = (y > 0) && (y + 1 < a.ny) && zp_ok && zn_ok;  // warp-uniform
+                        }
+                        Nb n[2];
+                        F3 f[2], fxp[2], fxm[2], fyp[2], fym[2], fzp[2], fzm[2];
+                        n[0].u0 = wB[1].x; n[0].xp = wB[1].y; n[0].xm = wA[1].y;
+                        n[0].yp = wB[2].x; n[0].ym = wB[0].x; n[0].zp = wN[1].x; n[0].zm = wP[1].x;
+                        n[1].u0 = wB[1].y; n[1].xp = wC[1].x; n[1].xm = wB[1].x;
+                        n[1].yp = wB[2].y; n[1].ym = wB[0].y; n[1].zp = wN[1].y; n[1].zm = wP[1].y;
+                        if (ANISO) {
+                            const float2 nA = ld2(Un, c - 2), nC = ld2(Un, c + 2);
+                            const float2 pA = ld2(Up, c - 2), pC = ld2(Up, c + 2);
+                            n[0].pp = wB[2].y; n[0].mm = wA[0].y; n[0].pm = wB[0].y; n[0].mp = wA[2].y;
+                            n[0].xpzp = wN[1].y; n[0].xmzm = pA.y; n[0].xpzm = wP[1].y; n[0].xmzp = nA.y;
+                            n[0].ypzp = wN[2].x; n[0].ymzm = wP[0].x; n[0].ypzm = wP[2].x; n[0].ymzp = wN[0].x;
+                            n[1].pp = wC[2].x; n[1].mm = wB[0].x; n[1].pm = wC[0].x; n[1].mp = wB[2].x;
+                            n[1].xpzp = nC.x; n[1].xmzm = wP[1].x; n[1].xpzm = pC.x; n[1].xmzp = wN[1].x;
+                            n[1].ypzp = wN[2].y; n[1].ymzm = wP[0].y; n[1].ypzm = wP[2].y; n[1].ymzp = wN[0].y;
+                            const float2 fAx = ld2(Fc, c - 2), fAy = ld2(Fc + FC, c - 2), fAz = ld2(Fc + 2 * FC, c - 2);
+                            const float2 fCx = ld2(Fc, c + 2), fCy = ld2(Fc + FC, c + 2), fCz = ld2(Fc + 2 * FC, c + 2);
+                            const float2 fNx = ld2(Fn, c), fNy = ld2(Fn + FC, c), fNz = ld2(Fn + 2 * FC, c);
+                            const float2 fPx = ld2(Fp, c), fPy = ld2(Fp + FC, c), fPz = ld2(Fp + 2 * FC, c);
+                            f[0] = F3{wFx[1].x, wFy[1].x, wFz[1].x};
+                            f[1] = F3{wFx[1].y, wFy[1].y, wFz[1].y};
+                            fxp[0] = f[1];
+                            fxm[0] = F3{fAx.y, fAy.y, fAz.y};
+                            fxp[1] = F3{fCx.x, fCy.x, fCz.x};
+                            fxm[1] = f[0];
+                            fyp[0] = F3{wFx[2].x, wFy[2].x, wFz[2].x};
+                            fyp[1] = F3{wFx[2].y, wFy[2].y, wFz[2].y};
+                            fym[0] = F3{wFx[0].x, wFy[0].x, wFz[0].x};
+                            fym[1] = F3{wFx[0].y, wFy[0].y, wFz[0].y};
+                            fzp[0] = F3{fNx.x, fNy.x, fNz.x};
+                            fzp[1] = F3{fNx.y, fNy.y, fNz.y};
+                            fzm[0] = F3{fPx.x, fPy.x, fPz.x};
+                            fzm[1] = F3{fPx.y, fPy.y, fPz.y};
+                        } else {
+    #pragma unroll
+                            for (int e = 0; e < 2; ++e) {
+                                f[e] = F3{0.f, 0.f, 0.f};
+                                fxp[e] = fxm[e] = fyp[e] = fym[e] = fzp[e] = fzm[e] = f[e];
                             }
-                            Lr[r][e] = lap_general<ANISO>(a, n[e], q, f[e], fxp[e], fxm[e], fyp[e], fym[e], fzp[e],
-                                                          fzm[e]);
+                        }
+    #pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            live[r][e] = tis[e];
+                            u0r[r][e] = n[e].u0;
+                            // fast formula for every node (values of void or
+                            // out-of-array nodes are finite and never stored) ...
+                            if (MASKED)
+                                Lr[r][e] = lap_interior<ANISO>(a, n[e], f[e], fxp[e], fxm[e], fyp[e], fym[e], fzp[e],
+                                                               fzm[e]);
+                            else
+                                Lr[r][e] = lap_xbound<ANISO>(a, n[e], e ? px1 : px0, e ? mx1 : mx0, f[e], fxp[e],
+                                                             fxm[e], fyp[e], fym[e], fzp[e], fzm[e]);
+                        }
+                        // ... and the general one where a y/z neighbour (or, in a
+                        // masked grid, any neighbour) may be void: rare, and
+                        // warp-uniform on unmasked grids
+                        if (!((intr[0] || !tis[0]) && (intr[1] || !tis[1]))) {
+    #pragma unroll
+                            for (int e = 0; e < 2; ++e) {
+                                if (!tis[e] || intr[e]) continue;
+                                const int xe = x + e, me = m + e;
+                                Psi q;
+                                if (MASKED) {
+                                    q.xp = Mc[me + 1] != 0; q.xm = Mc[me - 1] != 0;
+                                    q.yp = Mc[me + MW] != 0; q.ym = Mc[me - MW] != 0;
+                                    q.zp = zn_ok && Mn[me] != 0; q.zm = zp_ok && Mp[me] != 0;
+                                    q.pp = Mc[me + MW + 1] != 0; q.mm = Mc[me - MW - 1] != 0;
+                                    q.pm = Mc[me - MW + 1] != 0; q.mp = Mc[me + MW - 1] != 0;
+                                    q.xpzp = zn_ok && Mn[me + 1] != 0; q.xmzm = zp_ok && Mp[me - 1] != 0;
+                                    q.xpzm = zp_ok && Mp[me + 1] != 0; q.xmzp = zn_ok && Mn[me - 1] != 0;
+                                    q.ypzp = zn_ok && Mn[me + MW] != 0; q.ymzm = zp_ok && Mp[me - MW] != 0;
+                                    q.ypzm = zp_ok && Mp[me + MW] != 0; q.ymzp = zn_ok && Mn[me - MW] != 0;
+                                } else {
+                                    const bool xp = xe + 1 < a.nx, xm = xe > 0, yp = y + 1 < a.ny, ym = y > 0;
+                                    q.xp = xp; q.xm = xm; q.yp = yp; q.ym = ym; q.zp = zn_ok; q.zm = zp_ok;
+                                    q.pp = xp && yp; q.mm = xm && ym; q.pm = xp && ym; q.mp = xm && yp;
+                                    q.xpzp = xp && zn_ok; q.xmzm = xm && zp_ok; q.xpzm = xp && zp_ok; q.xmzp = xm && zn_ok;
+                                    q.ypzp = yp && zn_ok; q.ymzm = ym && zp_ok; q.ypzm = yp && zp_ok; q.ymzp = ym && zn_ok;
+                                }
+                                Lr[r][e] = lap_general<ANISO>(a, n[e], q, f[e], fxp[e], fxm[e], fyp[e], fym[e], fzp[e],
+                                                              fzm[e]);
+                            }
+                        }
+                        // slide the window down one row
+                        wA[0] = wA[1]; wA[1] = wA[2]; wB[0] = wB[1]; wB[1] = wB[2]; wC[0] = wC[1]; wC[1] = wC[2];
+                        wN[0] = wN[1]; wN[1] = wN[2]; wP[0] = wP[1]; wP[1] = wP[2];
+                        if (ANISO) {
+                            wFx[0] = wFx[1]; wFx[1] = wFx[2]; wFy[0] = wFy[1]; wFy[1] = wFy[2];
+                            wFz[0] = wFz[1]; wFz[1] = wFz[2];
                         }
                     }
-                    // slide the window down one row
-                    wA[0] = wA[1]; wA[1] = wA[2]; wB[0] = wB[1]; wB[1] = wB[2]; wC[0] = wC[1]; wC[1] = wC[2];
-                    wN[0] = wN[1]; wN[1] = wN[2]; wP[0] = wP[1]; wP[1] = wP[2];
-                    if (ANISO) {
-                        wFx[0] = wFx[1]; wFx[1] = wFx[2]; wFy[0] = wFy[1]; wFy[1] = wFy[2];
-                        wFz[0] = wFz[1]; wFz[1] = wFz[2];
-                    }
-                }
-
-                // phase 2: reaction, stores, activation, tissue sum (predicated)
-                const bool stim_on = a.stim_amp != 0.0f;
-#pragma unroll
-                for (int r = 0; r < CY; ++r) {
-                    const int y = yb + r;
-                    const long long gi = (long long)k * a.plane + (long long)y * a.px + x;  // even
-                    float yv[2][S];
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) yv[e][0] = u0r[r][e];
-#pragma unroll
-                    for (int v = 1; v < S; ++v) {
-                        const float2 sv = *reinterpret_cast<const float2*>(Sv + (v - 1) * TX * TY + (row0 + r) * TX + 2 * tx);
-                        yv[0][v] = sv.x;
-                        yv[1][v] = sv.y;
-                    }
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        float Is = 0.0f;
-                        if (stim_on && live[r][e] && a.stim[gi + e]) Is = a.stim_amp;
-                        Model<MODEL>::update(mp, yv[e], Lr[r][e], Is, a.dt);
-                    }
-                    if (live[r][0] && live[r][1]) {
-#pragma unroll
-                        for (int v = 0; v < S; ++v)
-                            *reinterpret_cast<float2*>(a.dst + (long long)v * a.vol + gi) = make_float2(yv[0][v], yv[1][v]);
-                    } else if (live[r][0] || live[r][1]) {
-#pragma unroll
-                        for (int e = 0; e < 2; ++e)
-                            if (live[r][e])
-#pragma unroll
-                                for (int v = 0; v < S; ++v) a.dst[(long long)v * a.vol + gi + e] = yv[e][v];
-                    }
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        if (live[r][e] && u0r[r][e] < theta && theta <= yv[e][0]) {
-                            if (a.act[gi + e] == BBX_ACT_NONE) a.act[gi + e] = a.step_next;
+    
+                    // phase 2: reaction, stores, activation, tissue sum (predicated)
+                    const bool stim_on = a.stim_amp != 0.0f;
+    #pragma unroll
+                    for (int r = 0; r < CY; ++r) {
+                        const int y = yb + r;
+                        const long long gi = (long long)k * a.plane + (long long)y * a.px + x;  // even
+                        float yv[2][S];
+    #pragma unroll
+                        for (int e = 0; e < 2; ++e) yv[e][0] = u0r[r][e];
+    #pragma unroll
+                        for (int v = 1; v < S; ++v) {
+                            const float2 sv = *reinterpret_cast<const float2*>(Sv + (v - 1) * TX * TY + (row0 + r) * TX + 2 * tx);
+                            yv[0][v] = sv.x;
+                            yv[1][v] = sv.y;
                         }
-                        two_sum_add(vsum, live[r][e] ? yv[e][0] : 0.0f);
+    #pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            float Is = 0.0f;
+                            if (stim_on && live[r][e] && a.stim[gi + e]) Is = a.stim_amp;
+                            Model<MODEL>::update(mp, yv[e], Lr[r][e], Is, a.dt);
+                        }
+                        if (live[r][0] && live[r][1]) {
+    #pragma unroll
+                            for (int v = 0; v < S; ++v)
+                                *reinterpret_cast<float2*>(a.dst + (long long)v * a.vol + gi) = make_float2(yv[0][v], yv[1][v]);
+                        } else if (live[r][0] || live[r][1]) {
+    #pragma unroll
+                            for (int e = 0; e < 2; ++e)
+                                if (live[r][e])
+    #pragma unroll
+                                    for (int v = 0; v < S; ++v) a.dst[(long long)v * a.vol + gi + e] = yv[e][v];
+                        }
+    #pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            if (live[r][e] && u0r[r][e] < theta && theta <= yv[e][0]) {
+                                if (a.act[gi + e] == BBX_ACT_NONE) a.act[gi + e] = a.step_next;
+                            }
+                            two_sum_add(vsum, live[r][e] ? yv[e][0] : 0.0f);
+                        }
                     }
                 }
+    
+                    __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[(jb + t) % NS]);
             }
-
-            abort = __syncthreads_or(timed_out);
-            if (abort) break;
+            __syncwarp();
+            if (lane == 0) {
+                // release the piece's last two planes (or all of a piece cut short)
+                for (int j = jb + (ncomp > 0 ? ncomp : 0); j < jb + (ncomp > 0 ? ncomp + 2 : 2); ++j)
+                    mbar_arrive(&empty[j % NS]);
+            }
+            jb += (ncomp > 0 ? ncomp : 0) + 2;
+            // per-piece partial of the tissue sum, and a vote on timeouts
+            double v = (double)vsum.hi + (double)vsum.lo;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red_scratch[warp] = v;
+            const bool any_to = consumers_sync_or(timed_out, NCT);
             if (tid == 0) {
-                const int freed = (t < ncomp - 1) ? (jb + t + 1) : (jb + ncomp + 2);
-                while (issued < freed + NS && issue_next()) {
-                }
+                double s = 0.0;
+                for (int w = 0; w < NCW; ++w) s += red_scratch[w];
+                L.partials[pi] = s;
             }
-        }
-        if (abort) break;
-        jb += ncomp + 2;
-        {
-            const double bs = block_sum_double((double)vsum.hi + (double)vsum.lo, red_scratch);
-            if (tid == 0) L.partials[pi] = bs;
+            consumers_sync(NCT);
             vsum.hi = vsum.lo = 0.0f;
-            __syncthreads();  // red_scratch is reused by the next piece
+            if (any_to) break;
         }
+        if (timed_out) abort_flag = 1;
     }
+    __syncthreads();
 
-    if (abort && tid == 0) {
-        // Give loads still in flight a bounded chance to land before exit.
+    if (abort_flag && warp == NCW && lane == 0) {
+        // Give the loads that may still be in flight a bounded chance to land.
         atomicOr(L.err, ERRBIT_TIMEOUT);
-        for (int j = jb; j < issued; ++j) {
-            if (L.poison_first_load && blockIdx.x == 0 && j == 0) continue;
-            (void)mbar_wait_bounded(&bars[j % NS], (j / NS) & 1, L.wait_limit);
-        }
+        for (int j = issued > NS ? issued - NS : 0; j < issued; ++j)
+            (void)mbar_wait_bounded(&full[j % NS], (j / NS) & 1, L.wait_limit);
     }
     step_finalize(L, red_scratch);
 }

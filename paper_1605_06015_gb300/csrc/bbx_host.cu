@@ -830,7 +830,7 @@ int bbx_create_grid(bbx_grid** out, int nx, int ny, int nz, double h, const uint
     g->ncell = ncell;
     g->stream = static_cast<cudaStream_t>(cuda_stream);
     g->zb = (nz == 1) ? 1 : 16;
-    g->ty = 16;
+    g->ty = 14;
     int rc = BBX_OK;
     do {
         if (cudaGetDevice(&g->device) != cudaSuccess ||
@@ -1249,7 +1249,7 @@ int bbx_read_active_bricks(bbx_grid* g, int32_t* out, size_t cap, long long* cou
 }
 
 int bbx_set_tiling(bbx_grid* g, int tile_y, int tile_z) {
-    if (!g || (tile_y != 8 && tile_y != 16 && tile_y != 32) || tile_z < 1) return BBX_ERR_ARG;
+    if (!g || (tile_y != 7 && tile_y != 14 && tile_y != 28) || tile_z < 1) return BBX_ERR_ARG;
     const int old_ty = g->ty, old_zb = g->zb;
     g->ty = tile_y;
     g->zb = tile_z > g->nz ? g->nz : tile_z;
@@ -1305,7 +1305,7 @@ int bbx_autotune(bbx_grid* g, double dt, double* best_ms) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int tys[3] = {8, 16, 32};
+    const int tys[3] = {7, 14, 28};
     std::vector<int> zbs;
     if (g->nz == 1 || !g->d_mask) {
         zbs.push_back(g->zb);  // unmasked columns are marched whole; only the tile rows matter
@@ -1370,7 +1370,7 @@ struct bbx_batch {
     struct Group {
         int model = 0;
         bool masked = false, aniso = false;
-        int ty = 16;
+        int ty = 14;
         std::vector<int> members;  // indices into grids
         TissueArgs* d_t = nullptr;  // one TissueArgs per member (tensor maps for this group's ty)
         LaunchPlan lp;
@@ -1380,7 +1380,9 @@ struct bbx_batch {
     };
     std::vector<bbx_grid*> grids;
     std::vector<unsigned long long> versions;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;  // the members' stream (may be the legacy default stream)
+    cudaStream_t ps = nullptr;      // the batch's own stream: graph capture and launches
+    cudaEvent_t enter = nullptr, leave = nullptr;
     int device = 0, num_sms = 0;
     std::vector<Group> groups;
     cudaEvent_t fork = nullptr;
@@ -1414,6 +1416,7 @@ void batch_release_groups(bbx_batch* b) {
 // step run side by side and finish together.
 int batch_build(bbx_batch* b, const std::vector<int>* tys) {
     cudaStreamSynchronize(b->stream);
+    if (b->ps) cudaStreamSynchronize(b->ps);
     std::vector<int> keep_ty;
     for (auto& gr : b->groups) keep_ty.push_back(gr.ty);
     batch_release_groups(b);
@@ -1486,14 +1489,14 @@ int batch_build(bbx_batch* b, const std::vector<int>* tys) {
 }
 
 int batch_launch_step(bbx_batch* b) {
-    BBX_CUDA(cudaEventRecord(b->fork, b->stream));
+    BBX_CUDA(cudaEventRecord(b->fork, b->ps));
     for (auto& gr : b->groups) {
         if (gr.lp.n_planes == 0) continue;
         BBX_CUDA(cudaStreamWaitEvent(gr.s, b->fork, 0));
         const LaunchArgs L = launch_args(gr.lp, gr.d_t, b->d_err, 0);
         BBX_CUDA(launch(gr.lp, L, gr.s));
         BBX_CUDA(cudaEventRecord(gr.done, gr.s));
-        BBX_CUDA(cudaStreamWaitEvent(b->stream, gr.done, 0));
+        BBX_CUDA(cudaStreamWaitEvent(b->ps, gr.done, 0));
     }
     return BBX_OK;
 }
@@ -1504,11 +1507,11 @@ int batch_capture(bbx_batch* b, int steps) {
     b->gexec = nullptr;
     b->graph = nullptr;
     b->graph_steps = 0;
-    BBX_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    BBX_CUDA(cudaStreamBeginCapture(b->ps, cudaStreamCaptureModeThreadLocal));
     int rc = BBX_OK;
     for (int s = 0; s < steps && rc == BBX_OK; ++s) rc = batch_launch_step(b);
     cudaGraph_t graph = nullptr;
-    const cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+    const cudaError_t e = cudaStreamEndCapture(b->ps, &graph);
     if (rc) {
         if (graph) cudaGraphDestroy(graph);
         return rc;
@@ -1541,7 +1544,10 @@ int bbx_batch_create(bbx_batch** out, bbx_grid* const* grids, int n) {
     b->device = grids[0]->device;
     b->num_sms = grids[0]->num_sms;
     int rc = BBX_OK;
-    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+    if (cudaStreamCreateWithFlags(&b->ps, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->enter, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->leave, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
         dmalloc(&b->d_err, sizeof(int)) != cudaSuccess || cudaMemset(b->d_err, 0, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         rc = BBX_ERR_CUDA;
@@ -1558,8 +1564,12 @@ int bbx_batch_create(bbx_batch** out, bbx_grid* const* grids, int n) {
 void bbx_batch_destroy(bbx_batch* b) {
     if (!b) return;
     cudaStreamSynchronize(b->stream);
+    if (b->ps) cudaStreamSynchronize(b->ps);
     batch_release_groups(b);
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->enter) cudaEventDestroy(b->enter);
+    if (b->leave) cudaEventDestroy(b->leave);
+    if (b->ps) cudaStreamDestroy(b->ps);
     cudaFree(b->d_err);
     cudaGetLastError();
     delete b;
@@ -1577,18 +1587,24 @@ int bbx_batch_step(bbx_batch* b, int n_steps) {
     if (!b->built && (rc = batch_build(b, nullptr))) return rc;
     const int chunk = n_steps < 16 ? n_steps : 16;
     if (n_steps >= 2 && b->graph_steps != chunk && (rc = batch_capture(b, chunk))) return rc;
+    // order the batch's stream after the members' stream, and back
+    BBX_CUDA(cudaEventRecord(b->enter, b->stream));
+    BBX_CUDA(cudaStreamWaitEvent(b->ps, b->enter, 0));
     int done = 0;
     if (n_steps >= 2) {
-        for (; done + chunk <= n_steps; done += chunk) BBX_CUDA(cudaGraphLaunch(b->gexec, b->stream));
+        for (; done + chunk <= n_steps; done += chunk) BBX_CUDA(cudaGraphLaunch(b->gexec, b->ps));
     }
     for (; done < n_steps; ++done)
         if ((rc = batch_launch_step(b))) return rc;
+    BBX_CUDA(cudaEventRecord(b->leave, b->ps));
+    BBX_CUDA(cudaStreamWaitEvent(b->stream, b->leave, 0));
     for (bbx_grid* g : b->grids) g->stepped = true;
     return BBX_OK;
 }
 
 int bbx_batch_sync(bbx_batch* b) {
     if (!b) return BBX_ERR_ARG;
+    BBX_CUDA(cudaStreamSynchronize(b->ps));
     return check_sticky_ptr(b->stream, b->d_err);
 }
 
@@ -1628,16 +1644,17 @@ int bbx_batch_autotune(bbx_batch* b, double* best_ms) {
     for (size_t gi = 0; gi < tys.size() && rc == BBX_OK; ++gi) {
         double best = 1e30;
         int bty = tys[gi];
-        for (int ty : {8, 16, 32}) {
+        for (int ty : {7, 14, 28}) {
             std::vector<int> trial = tys;
             trial[gi] = ty;
             int r = batch_build(b, &trial);
             if (r == BBX_ERR_UNSUPPORTED) continue;
             if (r) { rc = r; break; }
+            cudaStreamSynchronize(b->stream);
             for (int s = 0; s < 2 && rc == BBX_OK; ++s) rc = batch_launch_step(b);
-            cudaEventRecord(e0, b->stream);
+            cudaEventRecord(e0, b->ps);
             for (int s = 0; s < 4 && rc == BBX_OK; ++s) rc = batch_launch_step(b);
-            cudaEventRecord(e1, b->stream);
+            cudaEventRecord(e1, b->ps);
             cudaEventSynchronize(e1);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
@@ -1651,6 +1668,7 @@ int bbx_batch_autotune(bbx_batch* b, double* best_ms) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaStreamSynchronize(b->ps);
     int rc2 = batch_build(b, &tys);
     for (size_t i = 0; i < b->grids.size(); ++i) {
         bbx_grid* g = b->grids[i];

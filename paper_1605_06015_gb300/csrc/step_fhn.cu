@@ -12,10 +12,10 @@ static StepKernel make_fhn() {
 StepKernel step_kernel_fhn(bool masked, bool aniso, int ty) {
 #define BBX_CASE(MA, AN, T) \
     if (masked == MA && aniso == AN && ty == T) return make_fhn<MA, AN, T>();
-    BBX_CASE(false, false, 8) BBX_CASE(false, false, 16) BBX_CASE(false, false, 32)
-    BBX_CASE(false, true, 8) BBX_CASE(false, true, 16) BBX_CASE(false, true, 32)
-    BBX_CASE(true, false, 8) BBX_CASE(true, false, 16) BBX_CASE(true, false, 32)
-    BBX_CASE(true, true, 8) BBX_CASE(true, true, 16) BBX_CASE(true, true, 32)
+    BBX_CASE(false, false, 7) BBX_CASE(false, false, 14) BBX_CASE(false, false, 28)
+    BBX_CASE(false, true, 7) BBX_CASE(false, true, 14) BBX_CASE(false, true, 28)
+    BBX_CASE(true, false, 7) BBX_CASE(true, false, 14) BBX_CASE(true, false, 28)
+    BBX_CASE(true, true, 7) BBX_CASE(true, true, 14) BBX_CASE(true, true, 28)
 #undef BBX_CASE
     return StepKernel{nullptr, 0, 0, 0};
 }

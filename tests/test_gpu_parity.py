@@ -95,8 +95,8 @@ def test_fhn2d_config1_activation_full_run(bbx):
     assert n_act > 1000  # the cross-field IC makes a wave that activates tissue
 
 
-@pytest.mark.parametrize("shape,ty,tz", [((96, 40, 24), 16, 16), ((67, 45, 13), 8, 5), ((130, 33, 9), 32, 4),
-                                         ((64, 16, 40), 16, 40)])
+@pytest.mark.parametrize("shape,ty,tz", [((96, 40, 24), 14, 16), ((67, 45, 13), 7, 5), ((130, 33, 9), 28, 4),
+                                         ((64, 16, 40), 14, 40)])
 def test_barkley3d_rotating_fibres_100_steps(bbx, shape, ty, tz):
     nx, ny, nz = shape
     w = wl.barkley_slab(nx, ny, nz)
@@ -107,17 +107,17 @@ def test_barkley3d_rotating_fibres_100_steps(bbx, shape, ty, tz):
 
 def test_br_slab_100_steps(bbx):
     w = wl.br_slab(72, 20, 10)
-    osim, G = _pair(bbx, w, 100, 16, 5)
+    osim, G = _pair(bbx, w, 100, 14, 5)
     _check_state(osim, G, w)
 
 
 def test_br_shell_masked_100_steps_and_bricks(bbx):
     w = wl.br_shell(64)
-    osim, G = _pair(bbx, w, 100, 16, 8)
+    osim, G = _pair(bbx, w, 100, 14, 8)
     _check_state(osim, G, w)
     _check_activation(osim, G, 100)
     og = osim.grid
-    for ty, tz in ((16, 8), (8, 3), (16, 64)):
+    for ty, tz in ((14, 8), (7, 3), (14, 64)):
         G.set_tiling(ty, tz)
         assert np.array_equal(G.read_active_bricks(), og.active_bricks(64, ty, min(tz, w.nz)))
 
@@ -130,16 +130,16 @@ def test_random_masks_and_fibres_zfk(bbx, seed, shape, aniso):
     rng = np.random.default_rng(seed + 50)
     w = wl.Workload("zfk_rand", nx, ny, nz, 0.5, 0.01, wl.ZFK, [0.13], 1.0, 0.3 if aniso else 1.0, mask=mask,
                     fibres=fib, ic_fields={0: rng.random((nz, ny, nx))}, theta=0.5)
-    osim, G = _pair(bbx, w, 60, 8, 4)
+    osim, G = _pair(bbx, w, 60, 7, 4)
     _check_state(osim, G, w)
-    for ty, tz in ((32, 2), (8, 5), (16, 64)):
+    for ty, tz in ((28, 2), (7, 5), (14, 64)):
         G.set_tiling(ty, tz)
         assert np.array_equal(G.read_active_bricks(), osim.grid.active_bricks(64, ty, min(tz, w.nz)))
 
 
 def test_isotropic_2d_fhn_ragged_sheet(bbx):
     w = wl.fhn_sheet(131, 77)
-    osim, G = _pair(bbx, w, 100, 32, 1)
+    osim, G = _pair(bbx, w, 100, 28, 1)
     _check_state(osim, G, w)
 
 
@@ -154,7 +154,7 @@ def test_stimulus_current(bbx):
 
 def test_totals_fused_and_standalone(bbx):
     w = wl.br_shell(48)
-    osim, G = _pair(bbx, w, 20, 16, 8)
+    osim, G = _pair(bbx, w, 20, 14, 8)
     g = osim.grid
     for v in range(osim.S):
         got = G.total(v)
@@ -229,7 +229,7 @@ def test_edge_cases(bbx):
     w = wl.Workload("sheet", 70, 20, 3, 0.4, 0.01, wl.ZFK, [0.13], 1.0, 0.3, mask=m,
                     fibres=wl.rotational_fibres(70, 20, 3),
                     ic_fields={0: np.random.default_rng(0).random((3, 20, 70))}, theta=0.5)
-    osim, G = _pair(bbx, w, 50, 8, 2)
+    osim, G = _pair(bbx, w, 50, 7, 2)
     _check_state(osim, G, w)
 
 
@@ -254,7 +254,7 @@ def test_errors_are_reported(bbx):
     H.set_fibres(np.ones((8, 64, 64, 3), np.float32), 0.1, 0.025)
     H.set_ionic_model(bbx.BBX_BR)
     with pytest.raises(bbx.BbxError) as e:
-        H.set_tiling(32, 8)
+        H.set_tiling(28, 8)
     assert e.value.code == bbx.BBX_ERR_UNSUPPORTED
     H.step(0.02, 2)
     assert np.isfinite(H.read_state(0)).all()
@@ -265,7 +265,7 @@ def test_bounded_wait_reports_timeout_and_recovers(bbx):
     # bytes no copy delivers; its bounded wait runs out and the step records
     # a timeout instead of hanging.  The context stays usable.
     w = wl.barkley_slab(64, 32, 16)
-    G = _gpu_grid(bbx, w, 16, 8)
+    G = _gpu_grid(bbx, w, 14, 8)
     G.debug_poison_first_load(1)
     G.step(w.dt, 1)
     with pytest.raises(bbx.BbxError) as e:
@@ -273,7 +273,7 @@ def test_bounded_wait_reports_timeout_and_recovers(bbx):
     assert e.value.code == bbx.BBX_ERR_TIMEOUT
     G.debug_poison_first_load(0)
     G.clear_device_error()
-    osim, G2 = _pair(bbx, w, 20, 16, 8)
+    osim, G2 = _pair(bbx, w, 20, 14, 8)
     _check_state(osim, G2, w)
 
 
@@ -281,12 +281,12 @@ def test_checkpoint_resume_is_bit_identical(bbx):
     w = wl.barkley_slab(80, 24, 12)
     rest = oracle.rest_state(w.model, w.params)
     st0 = w.initial_state(rest).astype(np.float32)
-    A = _gpu_grid(bbx, w, 16, 4)
+    A = _gpu_grid(bbx, w, 14, 4)
     A.write_all(st0)
     A.step(w.dt, 60)
     mid, act, (t, n) = A.read_all(), A.read_activation(), A.get_time()
     A.step(w.dt, 60)
-    B = _gpu_grid(bbx, w, 16, 4)
+    B = _gpu_grid(bbx, w, 14, 4)
     B.write_all(mid)
     B.write_activation(act)
     B.set_time(t, n)
@@ -298,7 +298,7 @@ def test_checkpoint_resume_is_bit_identical(bbx):
 def test_bound_torch_buffers(bbx):
     import torch
     w = wl.barkley_slab(64, 20, 6)
-    G = _gpu_grid(bbx, w, 16, 6)
+    G = _gpu_grid(bbx, w, 14, 6)
     info = G.get_info()
     n = info["nvars"] * info["nz"] * info["ny"] * info["px"]
     a = torch.zeros(n, dtype=torch.float32, device="cuda")
