@@ -242,6 +242,24 @@ int bbx_debug_poison_first_load(bbx_grid* g, int on);
  * BBX_ERR_TIMEOUT).  Synchronous. */
 int bbx_clear_device_error(bbx_grid* g);
 
+/* Tissue sum of one field, in double precision, for callers that cannot
+ * allocate device memory (a framework that owns all allocations through its
+ * own pool, a real-time loop that must never call cudaMalloc, a context with
+ * a memory budget fixed up front).  The paper has no counterpart; it is the
+ * reduction of bbx_total with its scratch held in a fixed device array that
+ * the library keeps on every GPU that loads it until the process exits.
+ * field_dev: nx*ny*nz floats on the current device in the pitched layout
+ * (rows of `pitch` >= nx elements, planes of pitch*ny); mask_dev: NULL (sum
+ * every node) or bytes in the same layout, nonzero = tissue; out_dev: one
+ * double on the device, written when the work enqueued on cuda_stream runs.
+ * No device memory is allocated or freed.  Limits: nx*ny*nz <= 2^28 nodes,
+ * else BBX_ERR_ARG.  The first call on a device looks up the scratch array's
+ * device address (make that first call before any stream capture).  All
+ * calls share the scratch, so calls that overlap on the GPU (concurrent
+ * streams) race; serialise them.  Errors: BBX_ERR_ARG, BBX_ERR_CUDA. */
+int bbx_total_noalloc(const float* field_dev, const uint8_t* mask_dev, int nx, int ny, int nz, int pitch,
+                      double* out_dev, void* cuda_stream);
+
 /* Release every resource of the grid (NULL is ignored). */
 void bbx_destroy_grid(bbx_grid* g);
 

@@ -80,6 +80,7 @@ def _load():
         "bbx_batch_sync": [P],
         "bbx_batch_autotune": [P, ctypes.POINTER(D)],
         "bbx_batch_info": [P, ctypes.POINTER(I), ctypes.POINTER(I), I],
+        "bbx_total_noalloc": [P, P, I, I, I, I, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -329,6 +330,13 @@ def bbx_batch_info(b):
 
 def bbx_batch_destroy(b):
     _lib.bbx_batch_destroy(b)
+
+
+def bbx_total_noalloc(field_dev, mask_dev, nx, ny, nz, pitch, out_dev, stream=None):
+    """Device pointers in, one double written to out_dev on the stream; the
+    library allocates nothing (see include/bbx.h)."""
+    _check(_lib.bbx_total_noalloc(field_dev, mask_dev, int(nx), int(ny), int(nz), int(pitch), out_dev,
+                                  _stream_handle(stream)), "bbx_total_noalloc")
 
 
 class Batch:
