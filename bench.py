@@ -213,6 +213,67 @@ def run_e2e(G, w, st0, S, args, dist, dev, ws, n_tissue):
     return {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": bytes_io,
             "d2h_bytes_per_step": bytes_io, "steps": e2e_steps}
 
+def initial_state(G, w):
+    """The workload's initial condition on top of the library's own rest
+    state (every node holds it right after bbx_set_ionic_model)."""
+    import numpy as np
+    rest = [float(G.read_state(v).reshape(-1)[0]) for v in range(G.get_info()["nvars"])]
+    return w.initial_state(rest).astype(np.float32)
+
+
+def run_batched(args, dev, stream):
+    """The batch of 256 independent tissues (192 FHN sheets with sides in
+    64..512, 64 Barkley blocks with sides in 64..128, parameters swept by
+    +-20%): cell-updates/s of batched, graph-replayed steps against the same
+    grids stepped one launch per grid."""
+    import numpy as np
+    import torch
+    from paper_1605_06015_gb300 import bbx
+    from paper_1605_06015_gb300 import workloads as wl
+    ws = wl.tissue_batch(n2d=args.batch_2d, n3d=args.batch_3d)
+    grids = []
+    for w in ws:
+        G = bbx.Grid(w.nx, w.ny, w.nz, w.h, w.mask, stream=stream)
+        G.set_fibres(None, w.D_par, w.D_par)
+        G.set_ionic_model(w.model, w.params)
+        G.set_threshold(w.theta)
+        G.set_timestep(w.dt)
+        G.write_all(initial_state(G, w))
+        grids.append(G)
+    cells = sum(w.n_cells for w in ws)
+    B = bbx.Batch(grids)
+    B.autotune()
+    K = args.batch_steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    B.step(16)  # warm-up and graph capture
+    torch.cuda.synchronize()
+    e0.record(stream)
+    B.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    B.sync()
+    t_batch = e0.elapsed_time(e1) * 1e-3
+    for G, w in zip(grids, ws):
+        G.step(w.dt, 2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(K):
+        for G, w in zip(grids, ws):
+            G.step(w.dt, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_solo = e0.elapsed_time(e1) * 1e-3
+    info = B.info()
+    B.close()
+    for G in grids:
+        G.close()
+    return {"workload": "%d 2D FHN sheets (sides 64..512) + %d 3D Barkley blocks (sides 64..128), D and model "
+                        "parameters swept +-20%%, isotropic" % (args.batch_2d, args.batch_3d),
+            "cells": cells, "steps": K, "value": cells * K / t_batch, "unit": "cell-updates/s",
+            "one_launch_per_grid_value": cells * K / t_solo, "speedup_vs_one_launch_per_grid": t_solo / t_batch,
+            "groups": info["n_groups"], "tile_y": info["tile_y"], "graph_steps_per_replay": 16}
+
+
 def run_bbx(args):
     import numpy as np
     import torch
@@ -221,18 +282,16 @@ def run_bbx(args):
         raise SystemExit("bench.py needs a CUDA GPU")
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    import oracle
     from paper_1605_06015_gb300 import bbx
     from paper_1605_06015_gb300 import workloads as wl
 
     w = wl.barkley_slab()
-    rest = oracle.rest_state(w.model, w.params)  # only to build the IC host-side
-    st0 = w.initial_state(rest).astype(np.float32)
     stream = torch.cuda.current_stream()
     G = bbx.Grid(w.nx, w.ny, w.nz, w.h, w.mask, stream=stream)
     G.set_fibres(w.fibres, w.D_par, w.D_perp)
     G.set_ionic_model(w.model, w.params)
     G.set_threshold(w.theta)
+    st0 = initial_state(G, w)
     G.write_all(st0)
     if args.tile:
         ty, tz = (int(v) for v in args.tile.split(","))
@@ -292,6 +351,9 @@ def run_bbx(args):
     e2e = None if args.no_e2e else run_e2e(G, w, st0, S, args, dist, dev, ws, n_tissue)
 
 
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(args, dev, stream)
     peak, peak_kind = load_peaks()
     achieved = B_alg * n_tissue / (ms_step * 1e-3) / 1e9
     cpu = None
@@ -312,6 +374,7 @@ def run_bbx(args):
                      "bytes_per_cell": B_alg},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "batched": batched,
         "gpu_launches": args.steps,
         "clocks": clk,
         "tissue_total_V": total_v,
@@ -335,6 +398,10 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-2d", type=int, default=192)
+    ap.add_argument("--batch-3d", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=48)
     ap.add_argument("--tile", default=None, help="TY,TZ brick shape instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
