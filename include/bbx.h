@@ -227,6 +227,52 @@ int bbx_batch_info(bbx_batch* b, int* n_groups, int* tile_y, int cap);
 /* Release the batch (the grids are not touched).  NULL is ignored. */
 void bbx_batch_destroy(bbx_batch* b);
 
+/* ---- reaction surrogate ------------------------------------------------- */
+/* A small perceptron, 8 -> 64 -> 64 -> 8 with ReLU hidden layers, that learns
+ * the Beeler-Reuter reaction increment s' - s of one step from (normalised)
+ * states s, trained on samples of the plain method's trajectories, and used
+ * in the step kernel in place of the exact update wherever the state lies in
+ * the training envelope and V is below the upstroke threshold (elsewhere the
+ * exact model runs).  Not part of the paper.
+ * Parameters are packed as W1[64][8] b1[64] W2[64][64] b2[64] W3[8][64]
+ * b3[8] (5256 floats).  Normalisation (48 floats): mu_in[8] sd_in[8]
+ * mu_out[8] sd_out[8] lo[8] hi[8]; the network sees (s - mu_in)/sd_in and
+ * predicts ((s' - s) - mu_out)/sd_out; [lo, hi] bounds the raw inputs. */
+typedef struct bbx_mlp bbx_mlp;
+
+/* Create a network with seeded uniform(+-1/sqrt(fan_in)) weights on the
+ * given stream.  Errors: BBX_ERR_ARG, BBX_ERR_NOMEM, BBX_ERR_CUDA. */
+int bbx_mlp_create(bbx_mlp** out, unsigned long long seed, void* cuda_stream);
+void bbx_mlp_destroy(bbx_mlp* m);
+int bbx_mlp_set_params(bbx_mlp* m, const float* params_host, size_t n);  /* resets Adam */
+int bbx_mlp_get_params(bbx_mlp* m, float* params_host, size_t n);
+int bbx_mlp_set_normalization(bbx_mlp* m, const float* norm_host, size_t n);
+int bbx_mlp_get_normalization(bbx_mlp* m, float* norm_host, size_t n);
+
+/* Fit the normalisation and the envelope to n training pairs (device arrays
+ * x[n][8] raw states, t[n][8] raw increments), accumulating in double. */
+int bbx_mlp_fit_normalization(bbx_mlp* m, const float* x_dev, const float* t_dev, long long n);
+
+/* Gradient of the mean squared error over the first `batch` pairs (no
+ * update): grad_host[5256], loss (may be NULL).  Synchronises. */
+int bbx_mlp_gradients(bbx_mlp* m, const float* x_dev, const float* t_dev, int batch, float* grad_host, size_t n,
+                      double* loss);
+
+/* `steps` Adam steps (beta 0.9/0.999, eps 1e-8) on minibatches of `batch`
+ * pairs drawn with replacement from the n pairs by a counter-based hash of
+ * (seed != 0, step, index); loss of the last minibatch into final_loss (may
+ * be NULL; synchronises if not). */
+int bbx_mlp_train(bbx_mlp* m, const float* x_dev, const float* t_dev, long long n, int batch, int steps, double lr,
+                  unsigned long long seed, double* final_loss);
+
+/* Training pairs from a running Beeler-Reuter grid (asynchronous): n tissue
+ * nodes drawn by a counter-based hash of (seed, i); x_dev[i][8] = their
+ * current state, t_dev[i][8] = the exact reaction increment of one step of
+ * the grid's time step (no diffusion, no stimulus).  Call between steps to
+ * sample a trajectory.  Errors: BBX_ERR_UNSUPPORTED (model is not BBX_BR),
+ * BBX_ERR_STATE (no model or time step), BBX_ERR_ARG. */
+int bbx_sample_reaction_pairs(bbx_grid* g, long long n, unsigned long long seed, float* x_dev, float* t_dev);
+
 /* Device pointer of the current buffer of one state variable (pitched
  * layout), for callers that keep data on the GPU. */
 int bbx_state_device_ptr(bbx_grid* g, int var, void** dev_ptr);

@@ -81,6 +81,15 @@ def _load():
         "bbx_batch_autotune": [P, ctypes.POINTER(D)],
         "bbx_batch_info": [P, ctypes.POINTER(I), ctypes.POINTER(I), I],
         "bbx_total_noalloc": [P, P, I, I, I, I, P, P],
+        "bbx_mlp_create": [ctypes.POINTER(P), ctypes.c_ulonglong, P],
+        "bbx_mlp_set_params": [P, P, Z],
+        "bbx_mlp_get_params": [P, P, Z],
+        "bbx_mlp_set_normalization": [P, P, Z],
+        "bbx_mlp_get_normalization": [P, P, Z],
+        "bbx_mlp_fit_normalization": [P, P, P, LL],
+        "bbx_mlp_gradients": [P, P, P, I, P, Z, ctypes.POINTER(D)],
+        "bbx_mlp_train": [P, P, P, LL, I, I, D, ctypes.c_ulonglong, ctypes.POINTER(D)],
+        "bbx_sample_reaction_pairs": [P, LL, ctypes.c_ulonglong, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -90,6 +99,8 @@ def _load():
     L.bbx_destroy_grid.restype = None
     L.bbx_batch_destroy.argtypes = [P]
     L.bbx_batch_destroy.restype = None
+    L.bbx_mlp_destroy.argtypes = [P]
+    L.bbx_mlp_destroy.restype = None
     L.bbx_status_string.argtypes = [I]
     L.bbx_status_string.restype = ctypes.c_char_p
     return L
@@ -337,6 +348,70 @@ def bbx_total_noalloc(field_dev, mask_dev, nx, ny, nz, pitch, out_dev, stream=No
     library allocates nothing (see include/bbx.h)."""
     _check(_lib.bbx_total_noalloc(field_dev, mask_dev, int(nx), int(ny), int(nz), int(pitch), out_dev,
                                   _stream_handle(stream)), "bbx_total_noalloc")
+
+
+MLP_PARAMS = 8 * 64 + 64 + 64 * 64 + 64 + 64 * 8 + 8
+MLP_NORM = 48
+
+
+def _devptr(t):
+    return t.data_ptr() if hasattr(t, "data_ptr") else t
+
+
+def bbx_mlp_create(seed=1, stream=None):
+    m = ctypes.c_void_p()
+    _check(_lib.bbx_mlp_create(ctypes.byref(m), int(seed), _stream_handle(stream)), "bbx_mlp_create")
+    return m
+
+
+def bbx_mlp_destroy(m):
+    _lib.bbx_mlp_destroy(m)
+
+
+def bbx_mlp_set_params(m, params):
+    p = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+    _check(_lib.bbx_mlp_set_params(m, p.ctypes.data, p.size), "bbx_mlp_set_params")
+
+
+def bbx_mlp_get_params(m):
+    p = np.empty(MLP_PARAMS, dtype=np.float32)
+    _check(_lib.bbx_mlp_get_params(m, p.ctypes.data, p.size), "bbx_mlp_get_params")
+    return p
+
+
+def bbx_mlp_set_normalization(m, norm):
+    p = np.ascontiguousarray(norm, dtype=np.float32).reshape(-1)
+    _check(_lib.bbx_mlp_set_normalization(m, p.ctypes.data, p.size), "bbx_mlp_set_normalization")
+
+
+def bbx_mlp_get_normalization(m):
+    p = np.empty(MLP_NORM, dtype=np.float32)
+    _check(_lib.bbx_mlp_get_normalization(m, p.ctypes.data, p.size), "bbx_mlp_get_normalization")
+    return p
+
+
+def bbx_mlp_fit_normalization(m, x_dev, t_dev, n):
+    _check(_lib.bbx_mlp_fit_normalization(m, _devptr(x_dev), _devptr(t_dev), int(n)), "bbx_mlp_fit_normalization")
+
+
+def bbx_mlp_gradients(m, x_dev, t_dev, batch):
+    g = np.empty(MLP_PARAMS, dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(_lib.bbx_mlp_gradients(m, _devptr(x_dev), _devptr(t_dev), int(batch), g.ctypes.data, g.size,
+                                  ctypes.byref(loss)), "bbx_mlp_gradients")
+    return g, loss.value
+
+
+def bbx_mlp_train(m, x_dev, t_dev, n, batch, steps, lr, seed=1):
+    loss = ctypes.c_double()
+    _check(_lib.bbx_mlp_train(m, _devptr(x_dev), _devptr(t_dev), int(n), int(batch), int(steps), float(lr),
+                              int(seed), ctypes.byref(loss)), "bbx_mlp_train")
+    return loss.value
+
+
+def bbx_sample_reaction_pairs(g, n, seed, x_dev, t_dev):
+    _check(_lib.bbx_sample_reaction_pairs(g, int(n), int(seed), _devptr(x_dev), _devptr(t_dev)),
+           "bbx_sample_reaction_pairs")
 
 
 class Batch:

@@ -316,23 +316,20 @@ template <>
 struct Model<BBX_BR> {
     static constexpr int S = 8;
 
-    // One Rush-Larsen gate step, Eq. (RL) read as y' = A y + B, in the
-    // algebraically equal form y' = y + (1 - A)(y_inf - y), with 1 - A taken
-    // by expm1f (no cancellation when (alpha+beta) dt is small).
-    __device__ static __forceinline__ float rl(float y, float al, float be, float dt) {
-        const float s = al + be;
-        const float one_minus_A = -expm1f(-s * dt);
-        return y + one_minus_A * (__fdividef(al, s) - y);
-    }
 
-    __device__ static __forceinline__ void update(const float* mp, float* y, float L, float Is, float dt) {
+    // The change of every variable over one step (the update is y + d): the
+    // Euler increments of V and Ca, and the Rush-Larsen increments of the
+    // gates, Eq. (RL) read as y' = A y + B, i.e. d = (1 - A)(y_inf - y) with
+    // 1 - A by expm1f (no cancellation when (alpha+beta) dt is small).
+    __device__ static __forceinline__ void increment(const float* mp, const float* y, float L, float Is, float dt,
+                                                     float* d) {
         const float V = y[0], Ca = y[1];
-        const float x1 = y[2], m = y[3], h = y[4], j = y[5], d = y[6], f = y[7];
+        const float x1 = y[2], m = y[3], h = y[4], j = y[5], dd = y[6], f = y[7];
 
         // membrane currents
         const float INa = (mp[0] * m * m * m * h * j + mp[1]) * (V - mp[2]);
         const float Es = -82.3f - 13.0287f * __logf(Ca);
-        const float Is_ = mp[3] * d * f * (V - Es);
+        const float Is_ = mp[3] * dd * f * (V - Es);
         const float Ix1 = x1 * 0.8f * (__expf(0.04f * (V + 77.0f)) - 1.0f) * __expf(-0.04f * (V + 35.0f));
         const float w = V + 23.0f;
         const float lin = (w == 0.0f) ? 5.0f : br_ratio(0.2f * w, -expm1f(-0.04f * w));
@@ -357,14 +354,27 @@ struct Model<BBX_BR> {
         const float a_f = br_ratio(0.012f * __expf(-0.008f * (V + 28.0f)), __expf(0.15f * (V + 28.0f)) + 1.0f);
         const float b_f = br_ratio(0.0065f * __expf(-0.02f * (V + 30.0f)), __expf(-0.2f * (V + 30.0f)) + 1.0f);
 
-        y[0] = V + dt * (-(Iion - Is) + L);  // Cm = 1
-        y[1] = Ca + dt * dCa;
-        y[2] = rl(x1, a_x1, b_x1, dt);
-        y[3] = rl(m, a_m, b_m, dt);
-        y[4] = rl(h, a_h, b_h, dt);
-        y[5] = rl(j, a_j, b_j, dt);
-        y[6] = rl(d, a_d, b_d, dt);
-        y[7] = rl(f, a_f, b_f, dt);
+        d[0] = dt * (-(Iion - Is) + L);  // Cm = 1
+        d[1] = dt * dCa;
+        d[2] = rl_inc(x1, a_x1, b_x1, dt);
+        d[3] = rl_inc(m, a_m, b_m, dt);
+        d[4] = rl_inc(h, a_h, b_h, dt);
+        d[5] = rl_inc(j, a_j, b_j, dt);
+        d[6] = rl_inc(dd, a_d, b_d, dt);
+        d[7] = rl_inc(f, a_f, b_f, dt);
+    }
+
+    __device__ static __forceinline__ float rl_inc(float y, float al, float be, float dt) {
+        const float s = al + be;
+        const float one_minus_A = -expm1f(-s * dt);
+        return one_minus_A * (__fdividef(al, s) - y);
+    }
+
+    __device__ static __forceinline__ void update(const float* mp, float* y, float L, float Is, float dt) {
+        float d[8];
+        increment(mp, y, L, Is, dt, d);
+#pragma unroll
+        for (int v = 0; v < 8; ++v) y[v] = y[v] + d[v];
     }
 };
 

@@ -291,6 +291,46 @@ __global__ void k_total(const float* __restrict__ u, const uint8_t* __restrict__
     grid_total_finalize(bs, partials, ticket, out, err, false, scratch);
 }
 
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Training pairs for the reaction surrogate: n tissue nodes drawn by a
+// counter-based hash, their current Beeler-Reuter state s and the exact
+// reaction increment of one step (no diffusion, no stimulus) s' - s.
+__global__ void k_sample_pairs_br(const TissueArgs* __restrict__ T, const uint8_t* __restrict__ mask, long long n,
+                                  unsigned long long seed, float* __restrict__ X, float* __restrict__ Y) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long cells = (long long)T->nx * T->ny * T->nz;
+    long long node = 0, gi = 0;
+    for (int attempt = 0; attempt < 256; ++attempt) {
+        node = (long long)(mix64(seed ^ mix64((unsigned long long)i * 256ull + attempt)) % (unsigned long long)cells);
+        const int x = int(node % T->nx);
+        const long long r = node / T->nx;
+        const int y = int(r % T->ny);
+        const int z = int(r / T->ny);
+        gi = z * T->plane + (long long)y * T->px + x;
+        if (!mask || mask[gi]) break;
+    }
+    const float* st = T->state[T->dyn->cur];
+    float s[8], d[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) s[v] = st[(long long)v * T->vol + gi];
+    float mp[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) mp[k] = T->mp[k];
+    Model<BBX_BR>::increment(mp, s, 0.0f, 0.0f, T->dt, d);
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        X[i * 8 + v] = s[v];
+        Y[i * 8 + v] = d[v];
+    }
+}
+
 template <typename T>
 cudaError_t dmalloc(T** p, size_t bytes) {
     return cudaMalloc(reinterpret_cast<void**>(p), bytes);
@@ -1361,6 +1401,22 @@ int bbx_autotune(bbx_grid* g, double dt, double* best_ms) {
 }
 
 }  // extern "C"
+
+extern "C" int bbx_sample_reaction_pairs(bbx_grid* g, long long n, unsigned long long seed, float* x_dev,
+                                         float* t_dev) {
+    if (!g || n <= 0 || !x_dev || !t_dev) return BBX_ERR_ARG;
+    if (!g->model) return BBX_ERR_STATE;
+    if (g->model != BBX_BR) return BBX_ERR_UNSUPPORTED;
+    if (!(g->dt > 0.0)) return BBX_ERR_STATE;
+    if (g->n_tissue == 0) return BBX_ERR_ARG;
+    if (!g->ready) {
+        int rc = prepare(g);
+        if (rc) return rc;
+    }
+    k_sample_pairs_br<<<(unsigned)((n + 255) / 256), 256, 0, g->stream>>>(g->d_t, g->d_mask, n, seed, x_dev, t_dev);
+    BBX_CUDA(cudaGetLastError());
+    return BBX_OK;
+}
 
 // ---------------------------------------------------------------------------
 // batches of independent grids
