@@ -265,6 +265,17 @@ int bbx_mlp_gradients(bbx_mlp* m, const float* x_dev, const float* t_dev, int ba
 int bbx_mlp_train(bbx_mlp* m, const float* x_dev, const float* t_dev, long long n, int batch, int steps, double lr,
                   unsigned long long seed, double* final_loss);
 
+/* Use a trained network for the reaction of a Beeler-Reuter grid: its BF16
+ * copy (weights rounded to bfloat16, biases and normalisation in float) is
+ * made now, so later changes to m do not affect the grid.  Every step then
+ * advances each tissue node whose state lies inside the network's envelope
+ * and whose V is below v_upstroke (mV) by the network's increment (plus the
+ * exact diffusion and stimulus terms), and every other node by the exact
+ * model.  m NULL switches back to the exact model everywhere.  Errors:
+ * BBX_ERR_STATE (no model), BBX_ERR_UNSUPPORTED (model is not BBX_BR, or the
+ * tile shape with the surrogate's buffers does not fit shared memory). */
+int bbx_set_surrogate(bbx_grid* g, const bbx_mlp* m, double v_upstroke);
+
 /* Training pairs from a running Beeler-Reuter grid (asynchronous): n tissue
  * nodes drawn by a counter-based hash of (seed, i); x_dev[i][8] = their
  * current state, t_dev[i][8] = the exact reaction increment of one step of

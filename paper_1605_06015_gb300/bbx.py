@@ -90,6 +90,7 @@ def _load():
         "bbx_mlp_gradients": [P, P, P, I, P, Z, ctypes.POINTER(D)],
         "bbx_mlp_train": [P, P, P, LL, I, I, D, ctypes.c_ulonglong, ctypes.POINTER(D)],
         "bbx_sample_reaction_pairs": [P, LL, ctypes.c_ulonglong, P, P],
+        "bbx_set_surrogate": [P, P, D],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -407,6 +408,10 @@ def bbx_mlp_train(m, x_dev, t_dev, n, batch, steps, lr, seed=1):
     _check(_lib.bbx_mlp_train(m, _devptr(x_dev), _devptr(t_dev), int(n), int(batch), int(steps), float(lr),
                               int(seed), ctypes.byref(loss)), "bbx_mlp_train")
     return loss.value
+
+
+def bbx_set_surrogate(g, m, v_upstroke=-60.0):
+    _check(_lib.bbx_set_surrogate(g, m, float(v_upstroke)), "bbx_set_surrogate")
 
 
 def bbx_sample_reaction_pairs(g, n, seed, x_dev, t_dev):

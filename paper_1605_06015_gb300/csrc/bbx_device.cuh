@@ -23,6 +23,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 #include "../../include/bbx.h"
@@ -65,6 +66,7 @@ struct TissueArgs {  // (CUtensorMap members impose its alignment)
     // weights), c_s = c_d/4 (Wtilde); isotropic D gives c_iso = D/h^2.
     float c_perp, c_d, c_dh, c_s, c_iso;
     float mp[8];  // model parameters in kernel form
+    const struct SurrogateData* surr;  // reaction surrogate (Beeler-Reuter), or nullptr
 };
 
 // One launch: a balanced schedule of pieces over the grids of one kernel type.
@@ -390,7 +392,7 @@ constexpr int align128(int b) { return (b + 127) & ~127; }
 // 18 stencil neighbours are all tissue inside the array ("interior").
 enum : uint8_t { MASK_TISSUE = 1, MASK_INTERIOR = 2 };
 
-template <int MODEL, bool MASKED, bool ANISO, int TY>
+template <int MODEL, bool MASKED, bool ANISO, int TY, bool SURR = false>
 struct Plan {
     static constexpr int S = Model<MODEL>::S;
     static constexpr int TX = kTileX;
@@ -413,7 +415,8 @@ struct Plan {
     static constexpr uint32_t TX_BYTES_HALO = U_RAW + F_RAW + M_RAW;     // z-halo plane: no other vars
     static constexpr int NS_FIT = (112 * 1024) / STAGE;  // two CTAs per SM where the stage allows
     static constexpr int NS = NS_FIT > 8 ? 8 : (NS_FIT < 4 ? 4 : NS_FIT);
-    static constexpr int SMEM = 128 + NS * STAGE + 2 * NS * 8 + NS * 160;  // stages, full/empty rings, piece ring
+    static constexpr int WBUF = SURR ? RY * 2048 : 0;  // per consumer warp: 64 rows of 32 bytes
+    static constexpr int SMEM = 128 + NS * STAGE + WBUF + 2 * NS * 8 + NS * 176;  // stages, warp buffers, rings
     static_assert(TY % RY == 0 && CY >= 1, "tile rows must be a multiple of the thread rows");
 };
 
@@ -558,6 +561,102 @@ __device__ __forceinline__ float lap_general(const Coef& a, const Nb& n, const P
 // the fused step kernel
 // ---------------------------------------------------------------------------
 
+// The reaction surrogate as the step kernel uses it (built on the device from
+// a trained network, bbx_set_surrogate): BF16 weights laid out row-major
+// [out][in] as 32-bit pairs (W1 padded to 16 inputs), FP32 biases, the
+// normalisation and envelope, and the upstroke threshold.
+struct SurrogateData {
+    uint32_t W1[64 * 8];   // [64][16] bf16
+    uint32_t W2[64 * 32];  // [64][64] bf16
+    uint32_t W3[8 * 32];   // [8][64] bf16
+    float b1[64], b2[64], b3[8];
+    float norm[48];        // mu_in, sd_in, mu_out, sd_out, lo, hi (8 each)
+    float v_up;            // the exact model runs where V >= v_up
+};
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// The network on the 64 nodes of one warp row (2 per lane) with tensor-core
+// MMAs (m16n8k16, BF16 inputs, FP32 accumulation), four m-tiles of 16 nodes.
+// Hidden activations stay in registers: the accumulators of two adjacent
+// 8-column tiles are the A fragment of the next layer's 16-wide k-tile.
+// wbuf: this warp's 2 KB of shared memory (64 rows of 32 bytes), first the
+// BF16 inputs of a row, then, row by row, its 8 FP32 outputs.  All 32 lanes
+// must call it.  s: the two nodes' raw states; d: their raw increments.
+__device__ __forceinline__ void surrogate_warp64(const SurrogateData* __restrict__ W, unsigned char* wbuf,
+                                                 const float (*s)[8], float (*d)[8]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const float* nrm = W->norm;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        uint32_t* row = reinterpret_cast<uint32_t*>(wbuf + (lane * 2 + e) * 32);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            row[k] = pack_bf16((s[e][2 * k] - nrm[2 * k]) / nrm[8 + 2 * k],
+                               (s[e][2 * k + 1] - nrm[2 * k + 1]) / nrm[8 + 2 * k + 1]);
+#pragma unroll
+        for (int k = 4; k < 8; ++k) row[k] = 0u;
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+        uint32_t* X = reinterpret_cast<uint32_t*>(wbuf + q * 16 * 32);
+        uint32_t a[4] = {X[g * 8 + t], X[(g + 8) * 8 + t], X[g * 8 + t + 4], X[(g + 8) * 8 + t + 4]};
+        __syncwarp();  // every lane holds its fragment before the rows are overwritten
+        uint32_t h[4][4];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+            mma_bf16(c, a, W->W1[(8 * j + g) * 8 + t], W->W1[(8 * j + g) * 8 + t + 4]);
+            const float bl = W->b1[8 * j + 2 * t], bh = W->b1[8 * j + 2 * t + 1];
+            const uint32_t lo = pack_bf16(fmaxf(c[0] + bl, 0.f), fmaxf(c[1] + bh, 0.f));
+            const uint32_t hi = pack_bf16(fmaxf(c[2] + bl, 0.f), fmaxf(c[3] + bh, 0.f));
+            if (j & 1) { h[j >> 1][2] = lo; h[j >> 1][3] = hi; }
+            else { h[j >> 1][0] = lo; h[j >> 1][1] = hi; }
+        }
+        uint32_t h2[4][4];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                mma_bf16(c, h[kk], W->W2[(8 * j + g) * 32 + 8 * kk + t], W->W2[(8 * j + g) * 32 + 8 * kk + t + 4]);
+            const float bl = W->b2[8 * j + 2 * t], bh = W->b2[8 * j + 2 * t + 1];
+            const uint32_t lo = pack_bf16(fmaxf(c[0] + bl, 0.f), fmaxf(c[1] + bh, 0.f));
+            const uint32_t hi = pack_bf16(fmaxf(c[2] + bl, 0.f), fmaxf(c[3] + bh, 0.f));
+            if (j & 1) { h2[j >> 1][2] = lo; h2[j >> 1][3] = hi; }
+            else { h2[j >> 1][0] = lo; h2[j >> 1][1] = hi; }
+        }
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) mma_bf16(c, h2[kk], W->W3[g * 32 + 8 * kk + t], W->W3[g * 32 + 8 * kk + t + 4]);
+        float* Y = reinterpret_cast<float*>(X);
+        Y[g * 8 + 2 * t] = c[0] + W->b3[2 * t];
+        Y[g * 8 + 2 * t + 1] = c[1] + W->b3[2 * t + 1];
+        Y[(g + 8) * 8 + 2 * t] = c[2] + W->b3[2 * t];
+        Y[(g + 8) * 8 + 2 * t + 1] = c[3] + W->b3[2 * t + 1];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float* y = reinterpret_cast<const float*>(wbuf + (lane * 2 + e) * 32);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) d[e][k] = fmaf(y[k], nrm[24 + k], nrm[16 + k]);
+    }
+    __syncwarp();  // the buffer is reused by the next row
+}
+
 // Per-piece context, written into a shared ring by the producer warp when it
 // issues the piece's first plane load, and read by the consumer warps once
 // that load has landed (the mbarrier orders the two).
@@ -570,8 +669,10 @@ struct PieceSlot : Coef {
     const uint8_t* stim;
     float stim_amp, dt, theta;
     int step_next;
+    const SurrogateData* surr;  // nullptr: exact reaction everywhere
     float mp[8];
 };
+static_assert(sizeof(PieceSlot) <= 176, "piece ring slot size");
 
 
 // Barrier over the consumer warps only (named barrier 1), returning the OR of
@@ -598,10 +699,10 @@ __device__ __forceinline__ void consumers_sync(int nthreads) {
 // full[s] completes when the plane's bulk copies have landed, empty[s] when
 // all 8 consumer warps are done with the plane.  No CTA-wide barrier is taken
 // per plane.
-template <int MODEL, bool MASKED, bool ANISO, int TY>
-__global__ void __launch_bounds__(32 * kRowsOfThreads + 32, (MASKED && ANISO) || TY == 28 ? 1 : 2)
+template <int MODEL, bool MASKED, bool ANISO, int TY, bool SURR = false>
+__global__ void __launch_bounds__(32 * kRowsOfThreads + 32, (MASKED && ANISO) || TY == 28 || SURR ? 1 : 2)
 step_kernel(const __grid_constant__ LaunchArgs L) {
-    using P = Plan<MODEL, MASKED, ANISO, TY>;
+    using P = Plan<MODEL, MASKED, ANISO, TY, SURR>;
     constexpr int S = P::S, TX = P::TX, UW = P::UW, MW = P::MW, NS = P::NS, CY = P::CY;
     constexpr int NCW = kRowsOfThreads;  // consumer warps
     constexpr int NCT = 32 * NCW;        // consumer threads
@@ -611,7 +712,8 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * P::STAGE);
+    unsigned char* wbufs = smem + NS * P::STAGE;  // surrogate buffers (SURR only)
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * P::STAGE + P::WBUF);
     uint64_t* empty = full + NS;
     PieceSlot* ring = reinterpret_cast<PieceSlot*>(empty + NS);
     __shared__ double red_scratch[32];
@@ -675,6 +777,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                         r.theta = T->theta;
                         r.step_next = (int)(D->n + 1);
                         r.c_perp = T->c_perp; r.c_d = T->c_d; r.c_dh = T->c_dh; r.c_s = T->c_s; r.c_iso = T->c_iso;
+                        r.surr = T->surr;
 #pragma unroll
                         for (int i = 0; i < 8; ++i) r.mp[i] = T->mp[i];
                     }
@@ -722,7 +825,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
             if (timed_out) pc.w = pc.z = 0;  // context unreliable: compute nothing
             const int x = pc.x + 2 * tx;  // first node of this thread's pair
             const int yb = pc.y + row0;   // y of this thread's first row
-            const bool x_in = x < a.nx && !timed_out;
+            const bool x_in = x < a.nx && !timed_out;  // (folded into the per-node flags)
             const int ncomp = pc.w - pc.z;
             wait_full(jb + 1);
             for (int t = 0; t < ncomp; ++t) {
@@ -745,7 +848,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                 const int c0 = (row0 + 1) * UW + (2 * tx + 4);   // stage index of node (x, yb), even
                 const int m0 = (row0 + 1) * MW + (2 * tx + 16);  // mask index of node (x, yb)
     
-                if (x_in) {
+                {
                     auto ld2 = [&](const float* U, int o) { return *reinterpret_cast<const float2*>(U + o); };
                     const bool x1_in = x + 1 < a.nx;
                     // psi of the x neighbours of the two nodes (unmasked grids)
@@ -777,7 +880,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                             wN[2] = ld2(Un, o); wP[2] = ld2(Up, o);
                             if (ANISO) { wFx[2] = ld2(Fc, o); wFy[2] = ld2(Fc + FC, o); wFz[2] = ld2(Fc + 2 * FC, o); }
                         }
-                        bool tis[2] = {y < a.ny, y < a.ny && x1_in}, intr[2];
+                        bool tis[2] = {x_in && y < a.ny, x_in && y < a.ny && x1_in}, intr[2];
                         if (MASKED) {
                             const unsigned char mc0 = Mc[m], mc1 = Mc[m + 1];
                             tis[0] = tis[0] && (mc0 & MASK_TISSUE);
@@ -894,11 +997,48 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                             yv[0][v] = sv.x;
                             yv[1][v] = sv.y;
                         }
-    #pragma unroll
+                            float Isr[2];
+#pragma unroll
                         for (int e = 0; e < 2; ++e) {
-                            float Is = 0.0f;
-                            if (stim_on && live[r][e] && a.stim[gi + e]) Is = a.stim_amp;
-                            Model<MODEL>::update(mp, yv[e], Lr[r][e], Is, a.dt);
+                            Isr[e] = 0.0f;
+                            if (stim_on && live[r][e] && a.stim[gi + e]) Isr[e] = a.stim_amp;
+                        }
+                        if constexpr (SURR && MODEL == BBX_BR) {
+                            // the surrogate where the state is inside the training
+                            // envelope and V below the upstroke threshold; the
+                            // exact model elsewhere
+                            const SurrogateData* W = a.surr;
+                            bool want[2] = {false, false};
+                            if (W) {
+#pragma unroll
+                                for (int e = 0; e < 2; ++e) {
+                                    bool in = live[r][e] && yv[e][0] < W->v_up;
+#pragma unroll
+                                    for (int v = 0; v < S; ++v)
+                                        in = in && yv[e][v] >= W->norm[32 + v] && yv[e][v] <= W->norm[40 + v];
+                                    want[e] = in;
+                                }
+                            }
+                            if (__any_sync(0xffffffffu, want[0] || want[1])) {
+                                float dsur[2][8];
+                                surrogate_warp64(W, wbufs + (tid >> 5) * 2048, yv, dsur);
+#pragma unroll
+                                for (int e = 0; e < 2; ++e) {
+                                    if (want[e]) {
+#pragma unroll
+                                        for (int v = 0; v < S; ++v) yv[e][v] += dsur[e][v];
+                                        yv[e][0] += a.dt * (Lr[r][e] + Isr[e]);
+                                    } else {
+                                        Model<MODEL>::update(mp, yv[e], Lr[r][e], Isr[e], a.dt);
+                                    }
+                                }
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < 2; ++e) Model<MODEL>::update(mp, yv[e], Lr[r][e], Isr[e], a.dt);
+                            }
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 2; ++e) Model<MODEL>::update(mp, yv[e], Lr[r][e], Isr[e], a.dt);
                         }
                         if (live[r][0] && live[r][1]) {
     #pragma unroll

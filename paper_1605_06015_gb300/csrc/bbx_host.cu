@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "bbx_device.cuh"
+#include "bbx_mlp.cuh"
 
 namespace bbx {
 StepKernel step_kernel_fhn(bool masked, bool aniso, int ty);
@@ -18,6 +19,7 @@ StepKernel step_kernel_barkley(bool masked, bool aniso, int ty);
 StepKernel step_kernel_br(bool masked, bool aniso, int ty);
 StepKernel step_kernel_zfk(bool masked, bool aniso, int ty);
 StepKernel step_kernel_diffusion(bool masked, bool aniso, int ty);
+StepKernel step_kernel_br_surrogate(bool masked, bool aniso, int ty);
 }  // namespace bbx
 
 using namespace bbx;
@@ -72,7 +74,8 @@ void model_kernel_params(int model, const double* p, float* mp) {
     }
 }
 
-StepKernel lookup_kernel(int model, bool masked, bool aniso, int ty) {
+StepKernel lookup_kernel(int model, bool masked, bool aniso, int ty, bool surrogate = false) {
+    if (surrogate) return model == BBX_BR ? step_kernel_br_surrogate(masked, aniso, ty) : StepKernel{nullptr, 0, 0, 0};
     switch (model) {
         case BBX_FHN: return step_kernel_fhn(masked, aniso, ty);
         case BBX_BARKLEY: return step_kernel_barkley(masked, aniso, ty);
@@ -331,6 +334,36 @@ __global__ void k_sample_pairs_br(const TissueArgs* __restrict__ T, const uint8_
     }
 }
 
+// The step kernel's copy of a trained network: BF16 weights in row-major
+// 32-bit pairs (W1 padded from 8 to 16 inputs), FP32 biases, normalisation.
+__global__ void k_build_surrogate(const float* __restrict__ P, const float* __restrict__ norm, float v_up,
+                                  SurrogateData* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    auto pair = [](float lo, float hi) {
+        __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<uint32_t*>(&v);
+    };
+    if (i < 64 * 8) {  // W1 [64][16]: word i = row i/8, columns 2(i%8), 2(i%8)+1
+        const int n = i / 8, c = 2 * (i % 8);
+        out->W1[i] = pair(c < 8 ? P[kOffW1 + n * 8 + c] : 0.0f, c + 1 < 8 ? P[kOffW1 + n * 8 + c + 1] : 0.0f);
+    }
+    if (i < 64 * 32) {
+        const int n = i / 32, c = 2 * (i % 32);
+        out->W2[i] = pair(P[kOffW2 + n * 64 + c], P[kOffW2 + n * 64 + c + 1]);
+    }
+    if (i < 8 * 32) {
+        const int n = i / 32, c = 2 * (i % 32);
+        out->W3[i] = pair(P[kOffW3 + n * 64 + c], P[kOffW3 + n * 64 + c + 1]);
+    }
+    if (i < 64) {
+        out->b1[i] = P[kOffB1 + i];
+        out->b2[i] = P[kOffB2 + i];
+    }
+    if (i < 8) out->b3[i] = P[kOffB3 + i];
+    if (i < kNormSize) out->norm[i] = norm[i];
+    if (i == 0) out->v_up = v_up;
+}
+
 template <typename T>
 cudaError_t dmalloc(T** p, size_t bytes) {
     return cudaMalloc(reinterpret_cast<void**>(p), bytes);
@@ -483,8 +516,8 @@ cudaError_t launch(const LaunchPlan& lp, const LaunchArgs& L, cudaStream_t s) {
 // Select the kernel for a configuration, check it fits, and return the CTA
 // budget (resident CTAs on the whole GPU).
 int select_kernel(int model, bool masked, bool aniso, int ty, int device, int num_sms, StepKernel* out,
-                  int* ctas) {
-    StepKernel k = lookup_kernel(model, masked, aniso, ty);
+                  int* ctas, bool surrogate = false) {
+    StepKernel k = lookup_kernel(model, masked, aniso, ty, surrogate);
     if (!k.fn) return BBX_ERR_UNSUPPORTED;
     int smem_optin = 0;
     if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
@@ -554,6 +587,9 @@ struct bbx_grid {
     LaunchPlan lp;                 // single-grid launch
     bool ready = false;            // h_t, d_t and lp match the current settings
     unsigned long long version = 1;  // bumped whenever the kernel's view changes
+
+    SurrogateData* d_surr = nullptr;  // reaction surrogate (Beeler-Reuter), owned
+    bool surr_on = false;
 
     double* d_partials = nullptr;  // bbx_total scratch
     unsigned int* d_ticket = nullptr;
@@ -709,6 +745,7 @@ int encode_targs(const bbx_grid* g, int ty, TissueArgs* t) {
     t->c_s = (float)(0.25 * cd);
     t->c_iso = (float)(g->Dpar * ih2);
     model_kernel_params(g->model, g->par, t->mp);
+    t->surr = (g->surr_on && g->model == BBX_BR) ? g->d_surr : nullptr;
     return BBX_OK;
 }
 
@@ -719,7 +756,8 @@ int prepare(bbx_grid* g) {
     if (!g->model || !g->d_state[0]) return BBX_ERR_STATE;
     StepKernel k;
     int ctas = 0;
-    int rc = select_kernel(g->model, g->d_mask != nullptr, g->aniso, g->ty, g->device, g->num_sms, &k, &ctas);
+    int rc = select_kernel(g->model, g->d_mask != nullptr, g->aniso, g->ty, g->device, g->num_sms, &k, &ctas,
+                           g->surr_on && g->model == BBX_BR);
     if (rc) return rc;
     if ((rc = encode_targs(g, g->ty, &g->h_t))) return rc;
     BBX_CUDA(cudaMemcpyAsync(g->d_t, &g->h_t, sizeof(TissueArgs), cudaMemcpyHostToDevice, g->stream));
@@ -842,6 +880,7 @@ void bbx_destroy_grid(bbx_grid* g) {
     cudaFree(g->d_bricks);
     cudaFree(g->d_t);
     cudaFree(g->d_dyn);
+    cudaFree(g->d_surr);
     g->lp.release();
     cudaFree(g->d_partials);
     cudaFree(g->d_ticket);
@@ -1031,6 +1070,7 @@ int bbx_set_ionic_model(bbx_grid* g, int model, const double* params, int n_para
         cudaGetLastError();
         return BBX_ERR_NOMEM;
     }
+    if (model != BBX_BR) g->surr_on = false;
     g->model = model;
     g->S = S;
     for (int i = 0; i < 8; ++i) g->par[i] = p[i];
@@ -1402,6 +1442,32 @@ int bbx_autotune(bbx_grid* g, double dt, double* best_ms) {
 
 }  // extern "C"
 
+extern "C" int bbx_set_surrogate(bbx_grid* g, const bbx_mlp* m, double v_upstroke) {
+    if (!g || !std::isfinite(v_upstroke)) return BBX_ERR_ARG;
+    if (!m) {
+        g->surr_on = false;
+        return g->model ? prepare(g) : BBX_OK;
+    }
+    if (!g->model) return BBX_ERR_STATE;
+    if (g->model != BBX_BR) return BBX_ERR_UNSUPPORTED;
+    if (!g->d_surr && dmalloc(&g->d_surr, sizeof(SurrogateData)) != cudaSuccess) {
+        cudaGetLastError();
+        return BBX_ERR_NOMEM;
+    }
+    k_build_surrogate<<<(64 * 32 + 255) / 256, 256, 0, g->stream>>>(bbx_mlp_device_params(m), bbx_mlp_device_norm(m),
+                                                                    (float)v_upstroke, g->d_surr);
+    BBX_CUDA(cudaGetLastError());
+    BBX_CUDA(cudaStreamSynchronize(g->stream));
+    const bool was = g->surr_on;
+    g->surr_on = true;
+    int rc = prepare(g);
+    if (rc) {
+        g->surr_on = was;
+        prepare(g);
+    }
+    return rc;
+}
+
 extern "C" int bbx_sample_reaction_pairs(bbx_grid* g, long long n, unsigned long long seed, float* x_dev,
                                          float* t_dev) {
     if (!g || n <= 0 || !x_dev || !t_dev) return BBX_ERR_ARG;
@@ -1425,7 +1491,7 @@ extern "C" int bbx_sample_reaction_pairs(bbx_grid* g, long long n, unsigned long
 struct bbx_batch {
     struct Group {
         int model = 0;
-        bool masked = false, aniso = false;
+        bool masked = false, aniso = false, surr = false;
         int ty = 14;
         std::vector<int> members;  // indices into grids
         TissueArgs* d_t = nullptr;  // one TissueArgs per member (tensor maps for this group's ty)
@@ -1481,13 +1547,16 @@ int batch_build(bbx_batch* b, const std::vector<int>* tys) {
         size_t gi = 0;
         for (; gi < b->groups.size(); ++gi) {
             auto& gr = b->groups[gi];
-            if (gr.model == g->model && gr.masked == (g->d_mask != nullptr) && gr.aniso == g->aniso) break;
+            if (gr.model == g->model && gr.masked == (g->d_mask != nullptr) && gr.aniso == g->aniso &&
+                gr.surr == (g->surr_on && g->model == BBX_BR))
+                break;
         }
         if (gi == b->groups.size()) {
             bbx_batch::Group gr;
             gr.model = g->model;
             gr.masked = g->d_mask != nullptr;
             gr.aniso = g->aniso;
+            gr.surr = g->surr_on && g->model == BBX_BR;
             b->groups.push_back(gr);
         }
         b->groups[gi].members.push_back((int)i);
@@ -1532,7 +1601,7 @@ int batch_build(bbx_batch* b, const std::vector<int>* tys) {
     for (size_t gi = 0; gi < b->groups.size(); ++gi) {
         auto& gr = b->groups[gi];
         int ctas = 0;
-        int rc = select_kernel(gr.model, gr.masked, gr.aniso, gr.ty, b->device, b->num_sms, &gr.lp.k, &ctas);
+        int rc = select_kernel(gr.model, gr.masked, gr.aniso, gr.ty, b->device, b->num_sms, &gr.lp.k, &ctas, gr.surr);
         if (rc) return rc;
         long long share = total_work > 0 ? (long long)((double)ctas * gr.work / total_work + 0.5) : 1;
         if (share < 1) share = 1;
