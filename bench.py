@@ -153,6 +153,22 @@ def dist_setup():
     return rank, ws, local, dist
 
 
+def max_over_ranks(x, dist, dev=None):
+    """The largest of the ranks' values of x (x itself on one rank): timings
+    are combined by taking the slowest rank."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, steps, ws, seconds):
+    """Units all ranks processed per second of the slowest rank."""
+    return units_per_rank * steps * ws / seconds
+
+
 def run_reference(args):
     rank, ws, local, dist = dist_setup()
     if rank != 0:
@@ -204,11 +220,8 @@ def run_e2e(G, w, st0, S, args, dist, dev, ws, n_tissue):
             G.read_state(v, out=pin_out[v])
     torch.cuda.synchronize()
     e_wall = time.perf_counter() - e0
-    if dist:
-        t = torch.tensor([e_wall], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_wall = float(t.item())
-    e2e_value = n_tissue * e2e_steps * ws / e_wall
+    e_wall = max_over_ranks(e_wall, dist, dev)
+    e2e_value = whole_job_rate(n_tissue, e2e_steps, ws, e_wall)
     bytes_io = S * w.n_cells * 4
     return {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": bytes_io,
             "d2h_bytes_per_step": bytes_io, "steps": e2e_steps}
@@ -221,7 +234,7 @@ def initial_state(G, w):
     return w.initial_state(rest).astype(np.float32)
 
 
-def run_batched(args, dev, stream):
+def run_batched(args, dev, stream, dist=None, n_ranks=1):
     """The batch of 256 independent tissues (192 FHN sheets with sides in
     64..512, 64 Barkley blocks with sides in 64..128, parameters swept by
     +-20%): cell-updates/s of batched, graph-replayed steps against the same
@@ -252,7 +265,7 @@ def run_batched(args, dev, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     B.sync()
-    t_batch = e0.elapsed_time(e1) * 1e-3
+    t_batch = max_over_ranks(e0.elapsed_time(e1) * 1e-3, dist, dev)
     for G, w in zip(grids, ws):
         G.step(w.dt, 2)
     torch.cuda.synchronize()
@@ -262,15 +275,16 @@ def run_batched(args, dev, stream):
             G.step(w.dt, 1)
     e1.record(stream)
     torch.cuda.synchronize()
-    t_solo = e0.elapsed_time(e1) * 1e-3
+    t_solo = max_over_ranks(e0.elapsed_time(e1) * 1e-3, dist, dev)
     info = B.info()
     B.close()
     for G in grids:
         G.close()
     return {"workload": "%d 2D FHN sheets (sides 64..512) + %d 3D Barkley blocks (sides 64..128), D and model "
                         "parameters swept +-20%%, isotropic" % (args.batch_2d, args.batch_3d),
-            "cells": cells, "steps": K, "value": cells * K / t_batch, "unit": "cell-updates/s",
-            "one_launch_per_grid_value": cells * K / t_solo, "speedup_vs_one_launch_per_grid": t_solo / t_batch,
+            "cells": cells, "steps": K, "value": whole_job_rate(cells, K, n_ranks, t_batch), "unit": "cell-updates/s",
+            "one_launch_per_grid_value": whole_job_rate(cells, K, n_ranks, t_solo),
+            "speedup_vs_one_launch_per_grid": t_solo / t_batch,
             "groups": info["n_groups"], "tile_y": info["tile_y"], "graph_steps_per_replay": 16}
 
 
@@ -341,19 +355,16 @@ def run_bbx(args):
     clk = clocks.stop()
     dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     total_v = G.step_total()
-    if dist:
-        t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms = float(t.item())
+    dev_ms = max_over_ranks(dev_ms, dist, dev)
     ms_step = dev_ms / args.steps
-    value = n_tissue * args.steps * ws / (dev_ms * 1e-3)
+    value = whole_job_rate(n_tissue, args.steps, ws, dev_ms * 1e-3)
 
     e2e = None if args.no_e2e else run_e2e(G, w, st0, S, args, dist, dev, ws, n_tissue)
 
 
     batched = None
     if not args.no_batched:
-        batched = run_batched(args, dev, stream)
+        batched = run_batched(args, dev, stream, dist, ws)
     peak, peak_kind = load_peaks()
     achieved = B_alg * n_tissue / (ms_step * 1e-3) / 1e9
     cpu = None
