@@ -70,18 +70,28 @@ struct TissueArgs {  // (CUtensorMap members impose its alignment)
 };
 
 // One launch: a balanced schedule of pieces over the grids of one kernel type.
-// CTA c marches through pieces[cta_off[c] .. cta_off[c+1]); a piece
-// (x0, y0, z0, z1) is one 64 x TY column of grid piece_tissue[i] over the
-// z-range [z0, z1).
+// CTA c marches through the slots c*cta_stride .. c*cta_stride + cta_count[c]
+// of pieces[]; a piece (x0, y0, z0, z1) is one 64 x TY column of grid
+// piece_tissue[i] over the z-range [z0, z1).  A fixed stride lets a CTA find
+// its first piece with one load.
+//
+// A launch over one grid (`single`) carries that grid's TissueArgs in the
+// kernel parameters (t0): its tensor maps, constants and the pointer to its
+// TissueDyn are then read from parameter space instead of through a chain of
+// dependent global loads at the start of every CTA.
 struct LaunchArgs {
+    TissueArgs t0;             // the grid of a single-grid launch
     const TissueArgs* tissues;
-    const int4* pieces;
-    const int* piece_tissue;
-    const int* cta_off;
-    const int* tissue_off;     // grid t owns pieces tissue_pieces[tissue_off[t] .. tissue_off[t+1])
+    const int4* pieces;        // ctas x cta_stride slots
+    const int* piece_tissue;   // per slot
+    const int* cta_count;      // pieces of each CTA
+    const int* tissue_off;     // grid t owns slots tissue_pieces[tissue_off[t] .. tissue_off[t+1])
     const int* tissue_pieces;  // (for the per-grid sums, in a fixed order)
     int n_tissues;
-    double* partials;          // one per piece
+    int single;                // one grid: t0 is valid and slots are summed in index order
+    int cta_stride;
+    int n_slots;               // ctas x cta_stride; unused slots keep a zero partial
+    double* partials;          // one per slot
     unsigned int* ticket;      // zero between launches
     int* err;                  // sticky error bits
     long long wait_limit;      // clock64 cycles a wait may spin before giving up
@@ -224,7 +234,7 @@ __device__ __forceinline__ void grid_total_finalize(double block_partial, double
 // End of a step, in the last CTA to finish: per-grid totals from the
 // per-piece partials (fixed order), then t += dt, n += 1 and the buffer
 // parity flip of every grid of the launch.
-__device__ __forceinline__ void step_finalize(const LaunchArgs& L, double* scratch32) {
+__device__ __forceinline__ void step_finalize(const LaunchArgs& L, double* scratch32, const TissueDyn* dyn0) {
     __shared__ bool last;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -235,26 +245,68 @@ __device__ __forceinline__ void step_finalize(const LaunchArgs& L, double* scrat
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // one warp per grid; its lanes stride over the grid's pieces in a fixed
-    // order and reduce by a fixed shuffle tree (deterministic)
+    // Fixed-order sums (deterministic).  One grid: every thread of the CTA
+    // strides over its pieces, then a shuffle tree per warp and the warps in
+    // order.  Several grids: one warp per grid, lanes striding its pieces.
+    // The partials are loaded several at a time so their L2 latencies overlap.
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
-    for (int ti = warp; ti < L.n_tissues; ti += nwarps) {
-        const int k0 = __ldcg(&L.tissue_off[ti]), k1 = __ldcg(&L.tissue_off[ti + 1]);
+    auto finish = [&](int ti, double s) {
+        const TissueArgs* T = L.tissues + ti;
+        TissueDyn* d = T->dyn;
+        if (!isfinite(s)) atomicOr(L.err, ERRBIT_NAN);
+        d->total = s;
+        d->t = d->t + T->dt_d;
+        d->n = d->n + 1;
+        d->cur = d->cur ^ 1;
+    };
+    // direct: slots k0..k1 of partials; otherwise through tissue_pieces
+    auto strided_sum = [&](int k0, int k1, int first, int stride, bool direct) {
         double s = 0.0;
-        for (int k = k0 + lane; k < k1; k += 32) s += __ldcg(&L.partials[__ldcg(&L.tissue_pieces[k])]);
+        for (int k = k0 + first; k < k1; k += 4 * stride) {
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int kk = k + u * stride;
+                v[u] = kk < k1 ? __ldcg(&L.partials[direct ? kk : __ldcg(&L.tissue_pieces[kk])]) : 0.0;
+            }
+            s += (v[0] + v[1]) + (v[2] + v[3]);
+        }
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) {
-            const TissueArgs* T = L.tissues + ti;
-            TissueDyn* d = T->dyn;
-            if (!isfinite(s)) atomicOr(L.err, ERRBIT_NAN);
-            d->total = s;
-            d->t = d->t + T->dt_d;
-            d->n = d->n + 1;
-            d->cur = d->cur ^ 1;
+        return s;
+    };
+    if (L.single) {
+        // every slot (unused ones hold 0) in index order; t, n and the buffer
+        // parity as the producer warps read them at the start of the launch
+        const double s = strided_sum(0, L.n_slots, threadIdx.x, blockDim.x, true);
+        if (lane == 0) scratch32[warp] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < nwarps; ++w) t += scratch32[w];
+            TissueDyn* d = L.t0.dyn;
+            if (!isfinite(t)) atomicOr(L.err, ERRBIT_NAN);
+            d->total = t;
+            d->t = dyn0->t + L.t0.dt_d;
+            d->n = dyn0->n + 1;
+            d->cur = dyn0->cur ^ 1;
+        }
+    } else if (L.n_tissues == 1) {
+        const double s = strided_sum(__ldcg(&L.tissue_off[0]), __ldcg(&L.tissue_off[1]), threadIdx.x, blockDim.x,
+                                     false);
+        if (lane == 0) scratch32[warp] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < nwarps; ++w) t += scratch32[w];
+            finish(0, t);
+        }
+    } else {
+        for (int ti = warp; ti < L.n_tissues; ti += nwarps) {
+            const double s = strided_sum(__ldcg(&L.tissue_off[ti]), __ldcg(&L.tissue_off[ti + 1]), lane, 32, false);
+            if (lane == 0) finish(ti, s);
         }
     }
     __syncthreads();
-    (void)scratch32;
     if (threadIdx.x == 0) *L.ticket = 0u;
 }
 
@@ -717,6 +769,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
     uint64_t* empty = full + NS;
     PieceSlot* ring = reinterpret_cast<PieceSlot*>(empty + NS);
     __shared__ double red_scratch[32];
+    __shared__ TissueDyn dyn0;  // single-grid launch: the grid's t, n, parity at launch
     __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x;
@@ -732,7 +785,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
     }
     __syncthreads();
 
-    const int piece_begin = L.cta_off[blockIdx.x], piece_end = L.cta_off[blockIdx.x + 1];
+    const int piece_begin = blockIdx.x * L.cta_stride, piece_end = piece_begin + L.cta_count[blockIdx.x];
     int issued = 0;  // producer lane 0: plane loads issued
 
     if (warp == NCW) {
@@ -742,10 +795,15 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
             int lp = 0;
             for (int pi = piece_begin; pi < piece_end && !stop; ++pi, ++lp) {
                 const int4 pc = L.pieces[pi];
-                const TissueArgs* T = L.tissues + L.piece_tissue[pi];
+                const TissueArgs* T = L.single ? &L.t0 : L.tissues + L.piece_tissue[pi];
                 const TissueDyn* D = T->dyn;
                 const int src = D->cur;
                 const int nz = T->nz;
+                if (L.single && pi == piece_begin) {
+                    dyn0.t = D->t;
+                    dyn0.n = D->n;
+                    dyn0.cur = src;
+                }
                 const int nload = pc.w - pc.z + 2;
                 for (int off = 0; off < nload; ++off) {
                     const int slot = issued % NS;
@@ -1095,7 +1153,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
         for (int j = issued > NS ? issued - NS : 0; j < issued; ++j)
             (void)mbar_wait_bounded(&full[j % NS], (j / NS) & 1, L.wait_limit);
     }
-    step_finalize(L, red_scratch);
+    step_finalize(L, red_scratch, &dyn0);
 }
 
 // host-visible description of one compiled step kernel

@@ -388,17 +388,18 @@ struct LaunchPlan {
     long long n_planes = 0;
     int4* d_pieces = nullptr;
     int* d_piece_tissue = nullptr;
-    int* d_cta_off = nullptr;
+    int* d_cta_count = nullptr;
     int* d_tissue_off = nullptr;
     int* d_tissue_pieces = nullptr;
     double* d_partials = nullptr;
     unsigned int* d_ticket = nullptr;
-    size_t cap_pieces = 0, cap_cta = 0, cap_tis = 0;
+    size_t cap_pieces = 0, cap_cta = 0, cap_tis = 0, cap_tlist = 0;
+    int cta_stride = 1, n_slots = 0;
 
     void release() {
         cudaFree(d_pieces);
         cudaFree(d_piece_tissue);
-        cudaFree(d_cta_off);
+        cudaFree(d_cta_count);
         cudaFree(d_tissue_off);
         cudaFree(d_tissue_pieces);
         cudaFree(d_partials);
@@ -436,20 +437,20 @@ int build_plan(LaunchPlan* lp, const std::vector<Seg>& segs, int n_tissues, int 
     lp->n_planes = T;
     lp->n_tissues = n_tissues;
     if (ctas > T) ctas = (int)std::max<long long>(T, 1);
-    std::vector<int4> pieces;
-    std::vector<int> ptis, off((size_t)ctas + 1, 0);
+    std::vector<std::vector<int4>> per((size_t)ctas);
+    std::vector<std::vector<int>> per_t((size_t)ctas);
     size_t si = 0;
     long long consumed = 0;
+    int stride = 1;
     for (int c = 0; c < ctas; ++c) {
-        off[c] = (int)pieces.size();
         long long need = (long long)(c + 1) * T / ctas - (long long)c * T / ctas;
         while (need > 0 && si < segs.size()) {
             const Seg& sg = segs[si];
             const long long avail = (sg.z1 - sg.z0) - consumed;
             const long long take = std::min(avail, need);
             const int z0 = sg.z0 + (int)consumed;
-            pieces.push_back(make_int4(sg.x0, sg.y0, z0, z0 + (int)take));
-            ptis.push_back(sg.tissue);
+            per[(size_t)c].push_back(make_int4(sg.x0, sg.y0, z0, z0 + (int)take));
+            per_t[(size_t)c].push_back(sg.tissue);
             need -= take;
             consumed += take;
             if (consumed == sg.z1 - sg.z0) {
@@ -457,24 +458,42 @@ int build_plan(LaunchPlan* lp, const std::vector<Seg>& segs, int n_tissues, int 
                 consumed = 0;
             }
         }
+        stride = std::max(stride, (int)per[(size_t)c].size());
     }
-    off[ctas] = (int)pieces.size();
-    std::vector<int> toff((size_t)n_tissues + 1, 0), tlist(pieces.size());
-    for (int t : ptis) toff[(size_t)t + 1]++;
+    // slot c*stride + i holds piece i of CTA c; unused slots stay zero
+    const size_t nslot = (size_t)ctas * (size_t)stride;
+    std::vector<int4> pieces(nslot, make_int4(0, 0, 0, 0));
+    std::vector<int> ptis(nslot, 0), cnt((size_t)ctas, 0);
+    std::vector<int> toff((size_t)n_tissues + 1, 0);
+    for (int c = 0; c < ctas; ++c) {
+        cnt[(size_t)c] = (int)per[(size_t)c].size();
+        for (size_t i = 0; i < per[(size_t)c].size(); ++i) {
+            pieces[(size_t)c * stride + i] = per[(size_t)c][i];
+            ptis[(size_t)c * stride + i] = per_t[(size_t)c][i];
+            toff[(size_t)per_t[(size_t)c][i] + 1]++;
+        }
+    }
     for (int t = 0; t < n_tissues; ++t) toff[(size_t)t + 1] += toff[t];
+    std::vector<int> tlist((size_t)toff[(size_t)n_tissues]);
     {
         std::vector<int> fill(toff.begin(), toff.end() - 1);
-        for (size_t i = 0; i < ptis.size(); ++i) tlist[(size_t)fill[(size_t)ptis[i]]++] = (int)i;
+        for (int c = 0; c < ctas; ++c)
+            for (int i = 0; i < cnt[(size_t)c]; ++i) {
+                const size_t k = (size_t)c * stride + i;
+                tlist[(size_t)fill[(size_t)ptis[k]]++] = (int)k;
+            }
     }
     int rc;
-    size_t cap_pt = lp->cap_pieces, cap_tl = lp->cap_pieces, cap_part = lp->cap_pieces;
+    size_t cap_pt = lp->cap_pieces, cap_part = lp->cap_pieces;
     if ((rc = upload(&lp->d_pieces, &lp->cap_pieces, pieces))) return rc;
     if ((rc = upload(&lp->d_piece_tissue, &cap_pt, ptis))) return rc;
-    if ((rc = upload(&lp->d_tissue_pieces, &cap_tl, tlist))) return rc;
-    if ((rc = upload(&lp->d_cta_off, &lp->cap_cta, off))) return rc;
+    if ((rc = upload(&lp->d_tissue_pieces, &lp->cap_tlist, tlist))) return rc;
+    if ((rc = upload(&lp->d_cta_count, &lp->cap_cta, cnt))) return rc;
     if ((rc = upload(&lp->d_tissue_off, &lp->cap_tis, toff))) return rc;
-    std::vector<double> zeros(pieces.size(), 0.0);
+    std::vector<double> zeros(nslot, 0.0);
     if ((rc = upload(&lp->d_partials, &cap_part, zeros))) return rc;
+    lp->cta_stride = stride;
+    lp->n_slots = (int)nslot;
     if (!lp->d_ticket) {
         if (dmalloc(&lp->d_ticket, sizeof(unsigned int)) != cudaSuccess) {
             cudaGetLastError();
@@ -489,13 +508,22 @@ int build_plan(LaunchPlan* lp, const std::vector<Seg>& segs, int n_tissues, int 
     return BBX_OK;
 }
 
-LaunchArgs launch_args(const LaunchPlan& lp, const TissueArgs* d_tissues, int* d_err, int poison) {
+// h_single: the host copy of the TissueArgs of a single-grid launch (carried in
+// the kernel parameters), or nullptr.
+LaunchArgs launch_args(const LaunchPlan& lp, const TissueArgs* d_tissues, int* d_err, int poison,
+                       const TissueArgs* h_single = nullptr) {
     LaunchArgs L;
-    memset(&L, 0, sizeof(L));
+    memset((void*)&L, 0, sizeof(L));
+    if (h_single && lp.n_tissues == 1) {
+        L.t0 = *h_single;
+        L.single = 1;
+    }
     L.tissues = d_tissues;
     L.pieces = lp.d_pieces;
     L.piece_tissue = lp.d_piece_tissue;
-    L.cta_off = lp.d_cta_off;
+    L.cta_count = lp.d_cta_count;
+    L.cta_stride = lp.cta_stride;
+    L.n_slots = lp.n_slots;
     L.tissue_off = lp.d_tissue_off;
     L.tissue_pieces = lp.d_tissue_pieces;
     L.n_tissues = lp.n_tissues;
@@ -1206,7 +1234,7 @@ int bbx_step(bbx_grid* g, double dt, int n_steps) {
         g->stepped = true;
         return BBX_OK;
     }
-    const LaunchArgs L = launch_args(g->lp, g->d_t, g->d_err, g->poison);
+    const LaunchArgs L = launch_args(g->lp, g->d_t, g->d_err, g->poison, &g->h_t);
     for (int s = 0; s < n_steps; ++s) {
         const cudaError_t e = launch(g->lp, L, g->stream);
         if (e != cudaSuccess) return fail_cuda(e);
