@@ -288,6 +288,87 @@ def run_batched(args, dev, stream, dist=None, n_ranks=1):
             "groups": info["n_groups"], "tile_y": info["tile_y"], "graph_steps_per_replay": 16}
 
 
+def run_surrogate(args, dev, stream, dist=None, n_ranks=1):
+    """The 256x256x64 rotating-fibre slab with Beeler-Reuter physics and the
+    reaction surrogate: 10^7 (state, one-step reaction increment) pairs sampled
+    from a plain run, the network trained on the GPU, then the same number of
+    steps from the same initial state with the exact model and with the
+    surrogate (exact model in the upstroke and outside the envelope):
+    cell-updates/s of each and the difference of their activation maps.  The
+    state (8 variables, two buffers, 268 MB) is larger than L2."""
+    import numpy as np
+    import torch
+    from paper_1605_06015_gb300 import bbx
+    from paper_1605_06015_gb300 import workloads as wl
+    w = wl.br_slab(256, 256, 64)
+
+    st0 = []
+
+    def grid():
+        G = bbx.Grid(w.nx, w.ny, w.nz, w.h, w.mask, stream=stream)
+        G.set_fibres(w.fibres, w.D_par, w.D_perp)
+        G.set_ionic_model(w.model, w.params)
+        G.set_threshold(w.theta)
+        G.set_timestep(w.dt)
+        if not st0:
+            st0.append(initial_state(G, w))  # on the rest state the grid starts from
+        G.write_all(st0[0])
+        return G
+
+    n_pairs, chunks, traj = args.surrogate_pairs, 50, args.surrogate_traj_steps
+    per = n_pairs // chunks
+    X = torch.empty((per * chunks, 8), dtype=torch.float32, device=dev)
+    T = torch.empty_like(X)
+    G = grid()
+    for k in range(chunks):
+        bbx.bbx_sample_reaction_pairs(G.g, per, 5000 + k, X[k * per:(k + 1) * per], T[k * per:(k + 1) * per])
+        G.step(w.dt, traj // chunks)
+    G.close()
+    m = bbx.bbx_mlp_create(11, stream=stream)
+    bbx.bbx_mlp_fit_normalization(m, X, T, X.shape[0])
+    l0 = bbx.bbx_mlp_train(m, X, T, X.shape[0], 4096, 1, 1e-3, seed=12)
+    t0 = time.perf_counter()
+    l1 = bbx.bbx_mlp_train(m, X, T, X.shape[0], 4096, args.surrogate_train_steps, 1e-3, seed=13)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del X, T
+    K = args.surrogate_steps
+    res = {}
+    acts = {}
+    for name in ("exact", "surrogate"):
+        G = grid()
+        if name == "surrogate":
+            bbx.bbx_set_surrogate(G.g, m, args.v_upstroke)
+        G.autotune(w.dt)
+        G.write_all(st0[0])
+        G.write_activation(np.full(w.shape, bbx.BBX_ACT_NONE, dtype=np.int32))
+        G.set_time(0.0, 0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        G.step(w.dt, K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        secs = max_over_ranks(e0.elapsed_time(e1) * 1e-3, dist, dev)
+        res[name] = whole_job_rate(w.n_cells, K, n_ranks, secs)
+        acts[name] = G.read_activation().astype(np.int64)
+        G.close()
+    bbx.bbx_mlp_destroy(m)
+    a, b = acts["exact"], acts["surrogate"]
+    both = (a != bbx.BBX_ACT_NONE) & (b != bbx.BBX_ACT_NONE)
+    diff = np.abs(a - b)[both]
+    return {"workload": "BR slab 256x256x64 (rotating fibres, D_par=0.1 D_perp=0.025, h=0.2, dt=0.02), "
+                        "MLP 8-64-64-8 BF16/FP32, exact model where V >= %g mV or outside the envelope" % args.v_upstroke,
+            "training_pairs": per * chunks, "trajectory_steps": traj, "train_steps": args.surrogate_train_steps,
+            "train_batch": 4096, "loss_first": l0, "loss_last": l1, "train_s": t_train, "steps": K,
+            "exact_value": res["exact"], "surrogate_value": res["surrogate"], "unit": "cell-updates/s",
+            "surrogate_over_exact": res["surrogate"] / res["exact"],
+            "activated_exact": int((a != bbx.BBX_ACT_NONE).sum()),
+            "activated_surrogate": int((b != bbx.BBX_ACT_NONE).sum()),
+            "activation_max_abs_diff_steps": int(diff.max()) if diff.size else None,
+            "activation_frac_within_1_step": float((diff <= 1).mean()) if diff.size else None}
+
+
 def run_bbx(args):
     import numpy as np
     import torch
@@ -365,6 +446,9 @@ def run_bbx(args):
     batched = None
     if not args.no_batched:
         batched = run_batched(args, dev, stream, dist, ws)
+    surrogate = None
+    if not args.no_surrogate:
+        surrogate = run_surrogate(args, dev, stream, dist, ws)
     peak, peak_kind = load_peaks()
     achieved = B_alg * n_tissue / (ms_step * 1e-3) / 1e9
     cpu = None
@@ -386,6 +470,7 @@ def run_bbx(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "batched": batched,
+        "surrogate": surrogate,
         "gpu_launches": args.steps,
         "clocks": clk,
         "tissue_total_V": total_v,
@@ -414,6 +499,12 @@ def main():
     ap.add_argument("--batch-3d", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=48)
     ap.add_argument("--tile", default=None, help="TY,TZ brick shape instead of autotuning")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--surrogate-pairs", type=int, default=10_000_000)
+    ap.add_argument("--surrogate-traj-steps", type=int, default=6000)
+    ap.add_argument("--surrogate-train-steps", type=int, default=4000)
+    ap.add_argument("--surrogate-steps", type=int, default=3000)
+    ap.add_argument("--v-upstroke", type=float, default=-60.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

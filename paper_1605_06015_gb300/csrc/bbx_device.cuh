@@ -437,7 +437,16 @@ struct Model<BBX_BR> {
 // ---------------------------------------------------------------------------
 
 constexpr int kTileX = 64;  // nodes per brick along x: 32 threads x 2 nodes
-constexpr int kRowsOfThreads = 7;  // consumer warps per CTA (plus one producer warp: 256 threads)
+// Consumer warps per CTA (plus one producer warp) for a tile of TY rows: 7
+// warps of 1 or 2 rows each for TY = 7, 14 (two CTAs per SM), 14 warps of 2
+// rows for TY = 28 (one CTA of 480 threads per SM, whose warps share one
+// ring of planes and so finish together).
+__host__ __device__ constexpr int rows_of_threads(int ty) { return ty == 28 ? 14 : 7; }
+
+// Resident CTAs per SM a kernel variant is built for.
+__host__ __device__ constexpr int ctas_per_sm(bool masked, bool aniso, int ty, bool surr) {
+    return (masked && aniso) || ty == 28 || surr ? 1 : 2;
+}
 constexpr int align128(int b) { return (b + 127) & ~127; }
 
 // Tissue-mask byte on the device: bit 0 = tissue, bit 1 = tissue node whose
@@ -448,7 +457,8 @@ template <int MODEL, bool MASKED, bool ANISO, int TY, bool SURR = false>
 struct Plan {
     static constexpr int S = Model<MODEL>::S;
     static constexpr int TX = kTileX;
-    static constexpr int RY = kRowsOfThreads;
+    static constexpr int RY = rows_of_threads(TY);
+    static constexpr int CTAS = ctas_per_sm(MASKED, ANISO, TY, SURR);
     static constexpr int CY = TY / RY;  // nodes per thread along y (each a pair in x)
     static constexpr int THREADS = 32 * RY + 32;  // consumer warps + producer warp
     static constexpr int UW = TX + 8;   // x from x0-4 to x0+TX+3 (16-byte aligned start)
@@ -465,7 +475,7 @@ struct Plan {
     static constexpr int STAGE = S_OFF + align128(S_RAW);
     static constexpr uint32_t TX_BYTES = U_RAW + F_RAW + M_RAW + S_RAW;  // plane computed in this piece
     static constexpr uint32_t TX_BYTES_HALO = U_RAW + F_RAW + M_RAW;     // z-halo plane: no other vars
-    static constexpr int NS_FIT = (112 * 1024) / STAGE;  // two CTAs per SM where the stage allows
+    static constexpr int NS_FIT = ((CTAS == 1 ? 200 : 112) * 1024) / STAGE;  // stages that fit CTAS per SM
     static constexpr int NS = NS_FIT > 8 ? 8 : (NS_FIT < 4 ? 4 : NS_FIT);
     static constexpr int WBUF = SURR ? RY * 2048 : 0;  // per consumer warp: 64 rows of 32 bytes
     static constexpr int SMEM = 128 + NS * STAGE + WBUF + 2 * NS * 8 + NS * 176;  // stages, warp buffers, rings
@@ -746,17 +756,17 @@ __device__ __forceinline__ void consumers_sync(int nthreads) {
     asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
-// Warp-specialised step kernel: warps 0..7 compute (2 x CY nodes per thread),
-// warp 8 is the producer.  Stage slots cycle through two mbarrier rings:
-// full[s] completes when the plane's bulk copies have landed, empty[s] when
-// all 8 consumer warps are done with the plane.  No CTA-wide barrier is taken
-// per plane.
+// Warp-specialised step kernel: warps 0..RY-1 compute (2 x CY nodes per
+// thread), warp RY is the producer.  Stage slots cycle through two mbarrier
+// rings: full[s] completes when the plane's bulk copies have landed, empty[s]
+// when all RY consumer warps are done with the plane.  No CTA-wide barrier is
+// taken per plane.
 template <int MODEL, bool MASKED, bool ANISO, int TY, bool SURR = false>
-__global__ void __launch_bounds__(32 * kRowsOfThreads + 32, (MASKED && ANISO) || TY == 28 || SURR ? 1 : 2)
+__global__ void __launch_bounds__(32 * rows_of_threads(TY) + 32, ctas_per_sm(MASKED, ANISO, TY, SURR))
 step_kernel(const __grid_constant__ LaunchArgs L) {
     using P = Plan<MODEL, MASKED, ANISO, TY, SURR>;
     constexpr int S = P::S, TX = P::TX, UW = P::UW, MW = P::MW, NS = P::NS, CY = P::CY;
-    constexpr int NCW = kRowsOfThreads;  // consumer warps
+    constexpr int NCW = P::RY;  // consumer warps
     constexpr int NCT = 32 * NCW;        // consumer threads
     static_assert(TX == 64, "pair mapping assumes 64-node rows");
     constexpr int FC = UW * P::UH;  // fibre component stride in a stage
@@ -793,17 +803,24 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
         if (lane == 0) {
             bool stop = false;
             int lp = 0;
+            // the loads the first plane waits for, issued together: the first
+            // piece (its slot always exists) and, for one grid, its t, n, parity
+            int4 pc_next = L.pieces[piece_begin];
+            TissueDyn d0;
+            if (L.single) {
+                const TissueDyn* D = L.t0.dyn;
+                d0.t = D->t;
+                d0.n = D->n;
+                d0.cur = D->cur;
+                dyn0 = d0;
+            }
             for (int pi = piece_begin; pi < piece_end && !stop; ++pi, ++lp) {
-                const int4 pc = L.pieces[pi];
+                const int4 pc = pc_next;
+                if (pi + 1 < piece_end) pc_next = L.pieces[pi + 1];
                 const TissueArgs* T = L.single ? &L.t0 : L.tissues + L.piece_tissue[pi];
                 const TissueDyn* D = T->dyn;
-                const int src = D->cur;
+                const int src = L.single ? d0.cur : D->cur;
                 const int nz = T->nz;
-                if (L.single && pi == piece_begin) {
-                    dyn0.t = D->t;
-                    dyn0.n = D->n;
-                    dyn0.cur = src;
-                }
                 const int nload = pc.w - pc.z + 2;
                 for (int off = 0; off < nload; ++off) {
                     const int slot = issued % NS;
@@ -822,7 +839,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                     }
                     if (off == 0) {
                         PieceSlot& r = ring[lp % NS];
-                        const double tn = D->t;
+                        const double tn = L.single ? d0.t : D->t;
                         r.x0 = pc.x; r.y0 = pc.y; r.z0 = pc.z; r.z1 = pc.w;
                         r.nx = T->nx; r.ny = T->ny; r.nz = nz; r.px = T->px;
                         r.plane = T->plane; r.vol = T->vol;
@@ -833,7 +850,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                                                                                                        : 0.0f;
                         r.dt = T->dt;
                         r.theta = T->theta;
-                        r.step_next = (int)(D->n + 1);
+                        r.step_next = (int)((L.single ? d0.n : D->n) + 1);
                         r.c_perp = T->c_perp; r.c_d = T->c_d; r.c_dh = T->c_dh; r.c_s = T->c_s; r.c_iso = T->c_iso;
                         r.surr = T->surr;
 #pragma unroll
