@@ -335,10 +335,11 @@ def run_surrogate(args, dev, stream, dist=None, n_ranks=1):
     K = args.surrogate_steps
     res = {}
     acts = {}
-    for name in ("exact", "surrogate"):
+    v_ups = [float(v) for v in args.v_upstroke.split(",")]
+    for name in ["exact"] + ["surrogate@%g" % v for v in v_ups]:
         G = grid()
-        if name == "surrogate":
-            bbx.bbx_set_surrogate(G.g, m, args.v_upstroke)
+        if name != "exact":
+            bbx.bbx_set_surrogate(G.g, m, float(name.split("@")[1]))
         G.autotune(w.dt)
         G.write_all(st0[0])
         G.write_activation(np.full(w.shape, bbx.BBX_ACT_NONE, dtype=np.int32))
@@ -354,19 +355,84 @@ def run_surrogate(args, dev, stream, dist=None, n_ranks=1):
         acts[name] = G.read_activation().astype(np.int64)
         G.close()
     bbx.bbx_mlp_destroy(m)
-    a, b = acts["exact"], acts["surrogate"]
-    both = (a != bbx.BBX_ACT_NONE) & (b != bbx.BBX_ACT_NONE)
-    diff = np.abs(a - b)[both]
+    a = acts["exact"]
+    runs = []
+    for v in v_ups:
+        name = "surrogate@%g" % v
+        b = acts[name]
+        both = (a != bbx.BBX_ACT_NONE) & (b != bbx.BBX_ACT_NONE)
+        diff = np.abs(a - b)[both]
+        runs.append({"v_upstroke_mV": v, "value": res[name], "over_exact": res[name] / res["exact"],
+                     "activated": int((b != bbx.BBX_ACT_NONE).sum()),
+                     "activation_max_abs_diff_steps": int(diff.max()) if diff.size else None,
+                     "activation_frac_within_1_step": float((diff <= 1).mean()) if diff.size else None})
     return {"workload": "BR slab 256x256x64 (rotating fibres, D_par=0.1 D_perp=0.025, h=0.2, dt=0.02), "
-                        "MLP 8-64-64-8 BF16/FP32, exact model where V >= %g mV or outside the envelope" % args.v_upstroke,
+                        "MLP 8-64-64-8 BF16/FP32, exact model where V >= v_upstroke or outside the envelope",
             "training_pairs": per * chunks, "trajectory_steps": traj, "train_steps": args.surrogate_train_steps,
             "train_batch": 4096, "loss_first": l0, "loss_last": l1, "train_s": t_train, "steps": K,
-            "exact_value": res["exact"], "surrogate_value": res["surrogate"], "unit": "cell-updates/s",
-            "surrogate_over_exact": res["surrogate"] / res["exact"],
-            "activated_exact": int((a != bbx.BBX_ACT_NONE).sum()),
-            "activated_surrogate": int((b != bbx.BBX_ACT_NONE).sum()),
-            "activation_max_abs_diff_steps": int(diff.max()) if diff.size else None,
-            "activation_frac_within_1_step": float((diff <= 1).mean()) if diff.size else None}
+            "exact_value": res["exact"], "unit": "cell-updates/s",
+            "activated_exact": int((a != bbx.BBX_ACT_NONE).sum()), "surrogate_runs": runs}
+
+
+def run_configs(args, dev, stream, dist=None, n_ranks=1):
+    """The other workload shapes, each timed by differencing two back-to-back
+    runs of N1 and N2 steps (fixed launch costs cancel): cell-updates/s and
+    the fraction of the measured HBM bandwidth the algorithmic bytes imply.
+    The 200x200 sheet is L2-resident (latency-bound); the 16384^2 sheet, the
+    512x512x256 slab and the 512^3 shell are larger than L2."""
+    import numpy as np
+    import torch
+    from paper_1605_06015_gb300 import bbx
+    from paper_1605_06015_gb300 import workloads as wl
+    peak, _ = load_peaks()
+    makers = {
+        "fhn_200": (lambda: wl.fhn_sheet(200, 200), (100, 1100),
+                    "2D FitzHugh-Nagumo 200x200, h=0.5, dt=0.01, D=1, 5-point, cross-field IC"),
+        "fhn_16384": (lambda: wl.fhn_sheet(16384, 16384), (2, 12),
+                      "2D FitzHugh-Nagumo 16384x16384, same physics (roofline figure)"),
+        "barkley_512x512x256": (lambda: wl.barkley_slab(512, 512, 256), (2, 22),
+                                "3D Barkley slab 512x512x256, rotating fibres, 19-point"),
+        "br_shell_512": (lambda: wl.br_shell(512), (2, 22),
+                         "Beeler-Reuter ellipsoidal shell in 512^3 (14 % tissue), helical fibres, masked 19-point"),
+    }
+    out = {}
+    for name in args.configs.split(","):
+        if not name:
+            continue
+        make, (n1, n2), desc = makers[name]
+        w = make()
+        G = bbx.Grid(w.nx, w.ny, w.nz, w.h, w.mask, stream=stream)
+        G.set_fibres(w.fibres, w.D_par, w.D_perp)
+        G.set_ionic_model(w.model, w.params)
+        G.set_threshold(w.theta)
+        G.set_timestep(w.dt)
+        st = initial_state(G, w)
+        G.autotune(w.dt)
+        G.write_all(st)
+        del st
+        info = G.get_info()
+        cells = info["n_tissue"]
+        S = info["nvars"]
+        b_alg = 2 * S * 4 + (12 if info["anisotropic"] else 0) + (1 if info["masked"] else 0)
+        G.step(w.dt, 2)
+        secs = []
+        for n in (n1, n2):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            G.step(w.dt, n)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            secs.append(max_over_ranks(e0.elapsed_time(e1) * 1e-3, dist, dev))
+        G.step_total()  # synchronising call: reports any device error of the runs
+        rate = whole_job_rate(cells, n2 - n1, n_ranks, secs[1] - secs[0])
+        out[name] = {"workload": desc, "active_cells": cells, "steps": [n1, n2], "value": rate,
+                     "unit": "cell-updates/s", "ms_per_step": 1e3 * (secs[1] - secs[0]) / (n2 - n1),
+                     "bytes_per_cell": b_alg, "roofline_frac": rate * b_alg / (peak * 1e9),
+                     "tile": [info["tile_x"], info["tile_y"], info["tile_z"]]}
+        G.close()
+        del w
+    return out
 
 
 def run_bbx(args):
@@ -446,6 +512,9 @@ def run_bbx(args):
     batched = None
     if not args.no_batched:
         batched = run_batched(args, dev, stream, dist, ws)
+    configs = None
+    if args.configs:
+        configs = run_configs(args, dev, stream, dist, ws)
     surrogate = None
     if not args.no_surrogate:
         surrogate = run_surrogate(args, dev, stream, dist, ws)
@@ -471,6 +540,7 @@ def run_bbx(args):
         "e2e": e2e,
         "batched": batched,
         "surrogate": surrogate,
+        "configs": configs,
         "gpu_launches": args.steps,
         "clocks": clk,
         "tissue_total_V": total_v,
@@ -500,11 +570,13 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=48)
     ap.add_argument("--tile", default=None, help="TY,TZ brick shape instead of autotuning")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--configs", default="fhn_200,fhn_16384,barkley_512x512x256,br_shell_512",
+                    help="comma-separated other workloads to time by differencing ('' for none)")
     ap.add_argument("--surrogate-pairs", type=int, default=10_000_000)
     ap.add_argument("--surrogate-traj-steps", type=int, default=6000)
     ap.add_argument("--surrogate-train-steps", type=int, default=4000)
     ap.add_argument("--surrogate-steps", type=int, default=3000)
-    ap.add_argument("--v-upstroke", type=float, default=-60.0)
+    ap.add_argument("--v-upstroke", default="-60,-75", help="comma-separated upstroke thresholds (mV)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -757,11 +757,19 @@ __device__ __forceinline__ void consumers_sync(int nthreads) {
 }
 
 // Warp-specialised step kernel: warps 0..RY-1 compute (2 x CY nodes per
-// thread), warp RY is the producer.  Stage slots cycle through two mbarrier
+// thread), warp RY is the producer.
+//
+// PLANAR (grids with nz = 1): a piece is a run of tiles down one column of
+// the sheet, pieces[i] = (x0, -, first tile, end tile); each stage holds one
+// tile with its one-row halo and the consumers march along y.  The z
+// neighbours of a plane are the plane itself (the previous and next stage
+// pointers alias the current one): every z term of the stencil is then zero
+// (faces and edges exactly, the W-tilde divergence up to rounding), which is
+// the 5-point (isotropic) or 9-point (anisotropic) sheet operator.  Stage slots cycle through two mbarrier
 // rings: full[s] completes when the plane's bulk copies have landed, empty[s]
 // when all RY consumer warps are done with the plane.  No CTA-wide barrier is
 // taken per plane.
-template <int MODEL, bool MASKED, bool ANISO, int TY, bool SURR = false>
+template <int MODEL, bool MASKED, bool ANISO, int TY, bool SURR = false, bool PLANAR = false>
 __global__ void __launch_bounds__(32 * rows_of_threads(TY) + 32, ctas_per_sm(MASKED, ANISO, TY, SURR))
 step_kernel(const __grid_constant__ LaunchArgs L) {
     using P = Plan<MODEL, MASKED, ANISO, TY, SURR>;
@@ -821,7 +829,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                 const TissueDyn* D = T->dyn;
                 const int src = L.single ? d0.cur : D->cur;
                 const int nz = T->nz;
-                const int nload = pc.w - pc.z + 2;
+                const int nload = PLANAR ? pc.w - pc.z : pc.w - pc.z + 2;
                 for (int off = 0; off < nload; ++off) {
                     const int slot = issued % NS;
                     if (L.poison_first_load && blockIdx.x == 0 && issued == 0) {
@@ -856,18 +864,19 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
 #pragma unroll
                         for (int i = 0; i < 8; ++i) r.mp[i] = T->mp[i];
                     }
-                    const int z = pc.z - 1 + off;
-                    const bool halo = (off == 0) || (off == nload - 1);
+                    const int z = PLANAR ? 0 : pc.z - 1 + off;
+                    const int y0 = PLANAR ? (pc.z + off) * TY : pc.y;  // first row of the tile
+                    const bool halo = !PLANAR && ((off == 0) || (off == nload - 1));
                     uint64_t* bar = &full[slot];
                     unsigned char* st = smem + slot * P::STAGE;
                     if (z < 0 || z >= nz) {
                         mbar_arrive(bar);  // plane outside the array: nothing to load
                     } else {
                         mbar_arrive_expect_tx(bar, (halo || S == 1) ? P::TX_BYTES_HALO : P::TX_BYTES);
-                        tma_load_3d(st + P::U_OFF, &T->tm_u[src], pc.x - 4, pc.y - 1, z, bar);
-                        if (ANISO) tma_load_4d(st + P::F_OFF, &T->tm_f, pc.x, pc.y - 1, z, 0, bar);  // fibre x offset 4
-                        if (MASKED) tma_load_3d(st + P::M_OFF, &T->tm_m, pc.x - 16, pc.y - 1, z, bar);
-                        if (S > 1 && !halo) tma_load_4d(st + P::S_OFF, &T->tm_s[src], pc.x, pc.y, z, 1, bar);
+                        tma_load_3d(st + P::U_OFF, &T->tm_u[src], pc.x - 4, y0 - 1, z, bar);
+                        if (ANISO) tma_load_4d(st + P::F_OFF, &T->tm_f, pc.x, y0 - 1, z, 0, bar);  // fibre x offset 4
+                        if (MASKED) tma_load_3d(st + P::M_OFF, &T->tm_m, pc.x - 16, y0 - 1, z, bar);
+                        if (S > 1 && !halo) tma_load_4d(st + P::S_OFF, &T->tm_s[src], pc.x, y0, z, 1, bar);
                     }
                     ++issued;
                 }
@@ -899,16 +908,20 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
             int4 pc = make_int4(a.x0, a.y0, a.z0, a.z1);
             if (timed_out) pc.w = pc.z = 0;  // context unreliable: compute nothing
             const int x = pc.x + 2 * tx;  // first node of this thread's pair
-            const int yb = pc.y + row0;   // y of this thread's first row
             const bool x_in = x < a.nx && !timed_out;  // (folded into the per-node flags)
             const int ncomp = pc.w - pc.z;
-            wait_full(jb + 1);
+            if (!PLANAR) wait_full(jb + 1);
             for (int t = 0; t < ncomp; ++t) {
-                wait_full(jb + t + 2);
-                const int k = pc.z + t;
-                const unsigned char* stp = smem + ((jb + t) % NS) * P::STAGE;
-                const unsigned char* stc = smem + ((jb + t + 1) % NS) * P::STAGE;
-                const unsigned char* stn = smem + ((jb + t + 2) % NS) * P::STAGE;
+                if (PLANAR) {
+                    if (t > 0) wait_full(jb + t);
+                } else {
+                    wait_full(jb + t + 2);
+                }
+                const int k = PLANAR ? 0 : pc.z + t;
+                const int yb = (PLANAR ? (pc.z + t) * TY : pc.y) + row0;  // y of this thread's first row
+                const unsigned char* stc = smem + ((PLANAR ? jb + t : jb + t + 1) % NS) * P::STAGE;
+                const unsigned char* stp = PLANAR ? stc : smem + ((jb + t) % NS) * P::STAGE;
+                const unsigned char* stn = PLANAR ? stc : smem + ((jb + t + 2) % NS) * P::STAGE;
                 const float* Up = reinterpret_cast<const float*>(stp + P::U_OFF);
                 const float* Uc = reinterpret_cast<const float*>(stc + P::U_OFF);
                 const float* Un = reinterpret_cast<const float*>(stn + P::U_OFF);
@@ -963,7 +976,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                             intr[0] = (mc0 & MASK_INTERIOR) != 0;
                             intr[1] = (mc1 & MASK_INTERIOR) != 0;
                         } else {
-                            intr[0] = intr[1] = (y > 0) && (y + 1 < a.ny) && zp_ok && zn_ok;  // warp-uniform
+                            intr[0] = intr[1] = (y > 0) && (y + 1 < a.ny) && (PLANAR || (zp_ok && zn_ok));  // warp-uniform
                         }
                         Nb n[2];
                         F3 f[2], fxp[2], fxm[2], fyp[2], fym[2], fzp[2], fzm[2];
@@ -1140,12 +1153,12 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                 if (lane == 0) mbar_arrive(&empty[(jb + t) % NS]);
             }
             __syncwarp();
-            if (lane == 0) {
+            if (!PLANAR && lane == 0) {
                 // release the piece's last two planes (or all of a piece cut short)
                 for (int j = jb + (ncomp > 0 ? ncomp : 0); j < jb + (ncomp > 0 ? ncomp + 2 : 2); ++j)
                     mbar_arrive(&empty[j % NS]);
             }
-            jb += (ncomp > 0 ? ncomp : 0) + 2;
+            jb += (ncomp > 0 ? ncomp : 0) + (PLANAR ? 0 : 2);
             // per-piece partial of the tissue sum, and a vote on timeouts
             double v = (double)vsum.hi + (double)vsum.lo;
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

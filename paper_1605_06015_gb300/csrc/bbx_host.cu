@@ -14,11 +14,11 @@
 #include "bbx_mlp.cuh"
 
 namespace bbx {
-StepKernel step_kernel_fhn(bool masked, bool aniso, int ty);
-StepKernel step_kernel_barkley(bool masked, bool aniso, int ty);
-StepKernel step_kernel_br(bool masked, bool aniso, int ty);
-StepKernel step_kernel_zfk(bool masked, bool aniso, int ty);
-StepKernel step_kernel_diffusion(bool masked, bool aniso, int ty);
+StepKernel step_kernel_fhn(bool masked, bool aniso, int ty, bool planar);
+StepKernel step_kernel_barkley(bool masked, bool aniso, int ty, bool planar);
+StepKernel step_kernel_br(bool masked, bool aniso, int ty, bool planar);
+StepKernel step_kernel_zfk(bool masked, bool aniso, int ty, bool planar);
+StepKernel step_kernel_diffusion(bool masked, bool aniso, int ty, bool planar);
 StepKernel step_kernel_br_surrogate(bool masked, bool aniso, int ty);
 }  // namespace bbx
 
@@ -74,14 +74,17 @@ void model_kernel_params(int model, const double* p, float* mp) {
     }
 }
 
-StepKernel lookup_kernel(int model, bool masked, bool aniso, int ty, bool surrogate = false) {
-    if (surrogate) return model == BBX_BR ? step_kernel_br_surrogate(masked, aniso, ty) : StepKernel{nullptr, 0, 0, 0};
+// planar: a grid with nz = 1 (sheet kernels, tiles marched along y).  The
+// surrogate kernels exist for 3D grids only.
+StepKernel lookup_kernel(int model, bool masked, bool aniso, int ty, bool surrogate, bool planar) {
+    if (surrogate)
+        return model == BBX_BR && !planar ? step_kernel_br_surrogate(masked, aniso, ty) : StepKernel{nullptr, 0, 0, 0};
     switch (model) {
-        case BBX_FHN: return step_kernel_fhn(masked, aniso, ty);
-        case BBX_BARKLEY: return step_kernel_barkley(masked, aniso, ty);
-        case BBX_BR: return step_kernel_br(masked, aniso, ty);
-        case BBX_ZFK: return step_kernel_zfk(masked, aniso, ty);
-        case BBX_DIFFUSION: return step_kernel_diffusion(masked, aniso, ty);
+        case BBX_FHN: return step_kernel_fhn(masked, aniso, ty, planar);
+        case BBX_BARKLEY: return step_kernel_barkley(masked, aniso, ty, planar);
+        case BBX_BR: return step_kernel_br(masked, aniso, ty, planar);
+        case BBX_ZFK: return step_kernel_zfk(masked, aniso, ty, planar);
+        case BBX_DIFFUSION: return step_kernel_diffusion(masked, aniso, ty, planar);
     }
     return StepKernel{nullptr, 0, 0, 0};
 }
@@ -172,6 +175,7 @@ __global__ void k_mask_interior(const uint8_t* __restrict__ in, uint8_t* __restr
                     for (int dx = -1; dx <= 1 && all; ++dx) {
                         const int nnz = (dx != 0) + (dy != 0) + (dz != 0);
                         if (nnz == 0 || nnz == 3) continue;
+                        if (nz == 1 && dz != 0) continue;  // a sheet has no z neighbours
                         const int X = x + dx, Y = y + dy, Z = z + dz;
                         if (X < 0 || Y < 0 || Z < 0 || X >= nx || Y >= ny || Z >= nz) all = false;
                         else if (!in[Z * plane + (long long)Y * px + X]) all = false;
@@ -544,8 +548,8 @@ cudaError_t launch(const LaunchPlan& lp, const LaunchArgs& L, cudaStream_t s) {
 // Select the kernel for a configuration, check it fits, and return the CTA
 // budget (resident CTAs on the whole GPU).
 int select_kernel(int model, bool masked, bool aniso, int ty, int device, int num_sms, StepKernel* out,
-                  int* ctas, bool surrogate = false) {
-    StepKernel k = lookup_kernel(model, masked, aniso, ty, surrogate);
+                  int* ctas, bool surrogate, bool planar) {
+    StepKernel k = lookup_kernel(model, masked, aniso, ty, surrogate, planar);
     if (!k.fn) return BBX_ERR_UNSUPPORTED;
     int smem_optin = 0;
     if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
@@ -692,6 +696,26 @@ int build_bricks(bbx_grid* g) {
 // Active columns (64 x ty nodes) of a grid with their active z-runs, for the
 // given tile rows (the brick list must have been built for g->ty).
 void grid_segments(const bbx_grid* g, int tissue, std::vector<Seg>* segs) {
+    if (g->nz == 1) {
+        // a sheet: runs of tiles down each column, (z0, z1) = tile range
+        if (!g->d_mask) {
+            for (int bx = 0; bx < g->nbx; ++bx) segs->push_back({tissue, bx * kTileX, 0, 0, g->nby});
+            return;
+        }
+        std::vector<std::vector<int>> col((size_t)g->nbx);
+        for (int id : g->h_bricks) col[(size_t)(id % g->nbx)].push_back(id / g->nbx);  // (nz = 1: by = id / nbx)
+        for (int bx = 0; bx < g->nbx; ++bx) {
+            const std::vector<int>& ys = col[(size_t)bx];
+            size_t i = 0;
+            while (i < ys.size()) {
+                size_t j = i;
+                while (j + 1 < ys.size() && ys[j + 1] == ys[j] + 1) ++j;
+                segs->push_back({tissue, bx * kTileX, 0, ys[i], ys[j] + 1});
+                i = j + 1;
+            }
+        }
+        return;
+    }
     if (!g->d_mask) {
         for (int by = 0; by < g->nby; ++by)
             for (int bx = 0; bx < g->nbx; ++bx) segs->push_back({tissue, bx * kTileX, by * g->ty, 0, g->nz});
@@ -785,7 +809,7 @@ int prepare(bbx_grid* g) {
     StepKernel k;
     int ctas = 0;
     int rc = select_kernel(g->model, g->d_mask != nullptr, g->aniso, g->ty, g->device, g->num_sms, &k, &ctas,
-                           g->surr_on && g->model == BBX_BR);
+                           g->surr_on && g->model == BBX_BR, g->nz == 1);
     if (rc) return rc;
     if ((rc = encode_targs(g, g->ty, &g->h_t))) return rc;
     BBX_CUDA(cudaMemcpyAsync(g->d_t, &g->h_t, sizeof(TissueArgs), cudaMemcpyHostToDevice, g->stream));
@@ -1519,7 +1543,7 @@ extern "C" int bbx_sample_reaction_pairs(bbx_grid* g, long long n, unsigned long
 struct bbx_batch {
     struct Group {
         int model = 0;
-        bool masked = false, aniso = false, surr = false;
+        bool masked = false, aniso = false, surr = false, planar = false;
         int ty = 14;
         std::vector<int> members;  // indices into grids
         TissueArgs* d_t = nullptr;  // one TissueArgs per member (tensor maps for this group's ty)
@@ -1576,7 +1600,7 @@ int batch_build(bbx_batch* b, const std::vector<int>* tys) {
         for (; gi < b->groups.size(); ++gi) {
             auto& gr = b->groups[gi];
             if (gr.model == g->model && gr.masked == (g->d_mask != nullptr) && gr.aniso == g->aniso &&
-                gr.surr == (g->surr_on && g->model == BBX_BR))
+                gr.surr == (g->surr_on && g->model == BBX_BR) && gr.planar == (g->nz == 1))
                 break;
         }
         if (gi == b->groups.size()) {
@@ -1585,6 +1609,7 @@ int batch_build(bbx_batch* b, const std::vector<int>* tys) {
             gr.masked = g->d_mask != nullptr;
             gr.aniso = g->aniso;
             gr.surr = g->surr_on && g->model == BBX_BR;
+            gr.planar = g->nz == 1;
             b->groups.push_back(gr);
         }
         b->groups[gi].members.push_back((int)i);
@@ -1629,7 +1654,8 @@ int batch_build(bbx_batch* b, const std::vector<int>* tys) {
     for (size_t gi = 0; gi < b->groups.size(); ++gi) {
         auto& gr = b->groups[gi];
         int ctas = 0;
-        int rc = select_kernel(gr.model, gr.masked, gr.aniso, gr.ty, b->device, b->num_sms, &gr.lp.k, &ctas, gr.surr);
+        int rc = select_kernel(gr.model, gr.masked, gr.aniso, gr.ty, b->device, b->num_sms, &gr.lp.k, &ctas, gr.surr,
+                               gr.planar);
         if (rc) return rc;
         long long share = total_work > 0 ? (long long)((double)ctas * gr.work / total_work + 0.5) : 1;
         if (share < 1) share = 1;

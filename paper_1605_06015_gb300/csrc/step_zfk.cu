@@ -3,15 +3,18 @@
 
 namespace bbx {
 
-template <bool MA, bool AN, int TY>
+template <bool MA, bool AN, int TY, bool PL>
 static StepKernel make_zfk() {
     using P = Plan<BBX_ZFK, MA, AN, TY>;
-    return StepKernel{reinterpret_cast<const void*>(&step_kernel<BBX_ZFK, MA, AN, TY>), P::SMEM, P::THREADS, TY};
+    return StepKernel{reinterpret_cast<const void*>(&step_kernel<BBX_ZFK, MA, AN, TY, false, PL>), P::SMEM, P::THREADS,
+                      TY};
 }
 
-StepKernel step_kernel_zfk(bool masked, bool aniso, int ty) {
+// planar: grids with nz = 1 (tiles marched along y)
+StepKernel step_kernel_zfk(bool masked, bool aniso, int ty, bool planar) {
 #define BBX_CASE(MA, AN, T) \
-    if (masked == MA && aniso == AN && ty == T) return make_zfk<MA, AN, T>();
+    if (masked == MA && aniso == AN && ty == T) \
+        return planar ? make_zfk<MA, AN, T, true>() : make_zfk<MA, AN, T, false>();
     BBX_CASE(false, false, 7) BBX_CASE(false, false, 14) BBX_CASE(false, false, 28)
     BBX_CASE(false, true, 7) BBX_CASE(false, true, 14) BBX_CASE(false, true, 28)
     BBX_CASE(true, false, 7) BBX_CASE(true, false, 14) BBX_CASE(true, false, 28)
