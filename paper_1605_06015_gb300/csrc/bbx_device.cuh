@@ -151,6 +151,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return true;
 }
 
+// Stores of the new state: st.global states the address space, so the
+// compiler need not assume they overwrite the shared-memory piece context
+// (which it would otherwise reload after every store).
+__device__ __forceinline__ void st_global(float* p, float2 v) {
+    asm volatile("st.global.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y));
+}
+__device__ __forceinline__ void st_global(float* p, float v) { asm volatile("st.global.f32 [%0], %1;" ::"l"(p), "f"(v)); }
+
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
                                             uint64_t* bar) {
     asm volatile(
@@ -443,9 +451,11 @@ constexpr int kTileX = 64;  // nodes per brick along x: 32 threads x 2 nodes
 // ring of planes and so finish together).
 __host__ __device__ constexpr int rows_of_threads(int ty) { return ty == 28 ? 14 : 7; }
 
-// Resident CTAs per SM a kernel variant is built for.
+// Resident CTAs per SM a kernel variant is built for (the register budget:
+// two CTAs of 256 threads allow 128 registers a thread; the masked
+// anisotropic stencil with 2 rows a thread and the surrogate need more).
 __host__ __device__ constexpr int ctas_per_sm(bool masked, bool aniso, int ty, bool surr) {
-    return (masked && aniso) || ty == 28 || surr ? 1 : 2;
+    return (masked && aniso && ty != 7) || ty == 28 || (surr && ty != 7) ? 1 : 2;
 }
 constexpr int align128(int b) { return (b + 127) & ~127; }
 
@@ -890,16 +900,17 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
         F2 vsum = {0.0f, 0.0f};
         bool timed_out = false;
         int jb = 0, lp = 0;  // load index of the first plane of the piece, local piece index
-        auto wait_full = [&](int j) {
+        auto wait_slot = [&](int slot, int parity) {
             if (timed_out || abort_flag) {
                 timed_out = true;
                 return;
             }
-            if (!mbar_wait_bounded(&full[j % NS], (j / NS) & 1, L.wait_limit)) {
+            if (!mbar_wait_bounded(&full[slot], parity, L.wait_limit)) {
                 timed_out = true;
                 abort_flag = 1;
             }
         };
+        auto wait_full = [&](int j) { wait_slot(j % NS, (j / NS) & 1); };
         for (int pi = piece_begin; pi < piece_end; ++pi, ++lp) {
             wait_full(jb);  // the piece's first load carries its context
             const PieceSlot& a = ring[lp % NS];  // read from shared memory where used
@@ -911,17 +922,27 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
             const bool x_in = x < a.nx && !timed_out;  // (folded into the per-node flags)
             const int ncomp = pc.w - pc.z;
             if (!PLANAR) wait_full(jb + 1);
+            // stage slots of loads jb + t (sp), jb + t + 1 (sc), jb + t + 2 (sn)
+            // and the slot and phase parity of the next load to wait for,
+            // advanced per plane without divisions
+            int sp = jb % NS;
+            int sc = sp + 1 == NS ? 0 : sp + 1;
+            int sn = sc + 1 == NS ? 0 : sc + 1;
+            const int jw = jb + (PLANAR ? 1 : 2);
+            int sw = jw % NS, pw = (jw / NS) & 1;
             for (int t = 0; t < ncomp; ++t) {
-                if (PLANAR) {
-                    if (t > 0) wait_full(jb + t);
-                } else {
-                    wait_full(jb + t + 2);
+                if (!PLANAR || t > 0) {
+                    wait_slot(sw, pw);
+                    if (++sw == NS) {
+                        sw = 0;
+                        pw ^= 1;
+                    }
                 }
                 const int k = PLANAR ? 0 : pc.z + t;
                 const int yb = (PLANAR ? (pc.z + t) * TY : pc.y) + row0;  // y of this thread's first row
-                const unsigned char* stc = smem + ((PLANAR ? jb + t : jb + t + 1) % NS) * P::STAGE;
-                const unsigned char* stp = PLANAR ? stc : smem + ((jb + t) % NS) * P::STAGE;
-                const unsigned char* stn = PLANAR ? stc : smem + ((jb + t + 2) % NS) * P::STAGE;
+                const unsigned char* stc = smem + (PLANAR ? sp : sc) * P::STAGE;
+                const unsigned char* stp = PLANAR ? stc : smem + sp * P::STAGE;
+                const unsigned char* stn = PLANAR ? stc : smem + sn * P::STAGE;
                 const float* Up = reinterpret_cast<const float*>(stp + P::U_OFF);
                 const float* Uc = reinterpret_cast<const float*>(stc + P::U_OFF);
                 const float* Un = reinterpret_cast<const float*>(stn + P::U_OFF);
@@ -1131,13 +1152,13 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                         if (live[r][0] && live[r][1]) {
     #pragma unroll
                             for (int v = 0; v < S; ++v)
-                                *reinterpret_cast<float2*>(a.dst + (long long)v * a.vol + gi) = make_float2(yv[0][v], yv[1][v]);
+                                st_global(a.dst + (long long)v * a.vol + gi, make_float2(yv[0][v], yv[1][v]));
                         } else if (live[r][0] || live[r][1]) {
     #pragma unroll
                             for (int e = 0; e < 2; ++e)
                                 if (live[r][e])
     #pragma unroll
-                                    for (int v = 0; v < S; ++v) a.dst[(long long)v * a.vol + gi + e] = yv[e][v];
+                                    for (int v = 0; v < S; ++v) st_global(a.dst + (long long)v * a.vol + gi + e, yv[e][v]);
                         }
     #pragma unroll
                         for (int e = 0; e < 2; ++e) {
@@ -1150,7 +1171,10 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                 }
     
                     __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[(jb + t) % NS]);
+                if (lane == 0) mbar_arrive(&empty[sp]);
+                sp = sc;
+                sc = sn;
+                sn = sn + 1 == NS ? 0 : sn + 1;
             }
             __syncwarp();
             if (!PLANAR && lane == 0) {

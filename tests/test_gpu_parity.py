@@ -143,6 +143,24 @@ def test_isotropic_2d_fhn_ragged_sheet(bbx):
     _check_state(osim, G, w)
 
 
+@pytest.mark.parametrize("shape,ty,masked", [((150, 90), 7, False), ((150, 90), 14, False), ((131, 61), 28, False),
+                                             ((64, 200), 14, False), ((97, 83), 14, True)])
+def test_anisotropic_sheet_tiles_march_along_y(bbx, shape, ty, masked):
+    """Sheets (nz = 1) with smooth fibres that leave the plane (f_z != 0, so the
+    z terms must vanish): several tiles per piece, a ragged last tile, and a
+    masked sheet whose interior bit counts in-plane neighbours only."""
+    nx, ny = shape
+    rng = np.random.default_rng(nx + 1000 * ty)
+    fib = wl.smooth_fibres(nx, ny, 1, 0.5)
+    mask = (rng.random((1, ny, nx)) < 0.8).astype(np.uint8) if masked else None
+    if masked:
+        mask[:, ny // 3:ny // 3 + 20, nx // 4:nx // 4 + 30] = 1  # an all-tissue block: interior nodes
+    w = wl.Workload("zfk_sheet", nx, ny, 1, 0.5, 0.01, wl.ZFK, [0.13], 1.0, 0.3, mask=mask, fibres=fib,
+                    ic_fields={0: rng.random((1, ny, nx))}, theta=0.5)
+    osim, G = _pair(bbx, w, 60, ty, 1)
+    _check_state(osim, G, w)
+
+
 def test_stimulus_current(bbx):
     w = wl.fhn_sheet(70, 50)
     w.ic_fields = {}
