@@ -111,9 +111,10 @@ def test_br_slab_100_steps(bbx):
     _check_state(osim, G, w)
 
 
-def test_br_shell_masked_100_steps_and_bricks(bbx):
+@pytest.mark.parametrize("ty,tz", [(14, 8), (7, 4)])
+def test_br_shell_masked_100_steps_and_bricks(bbx, ty, tz):
     w = wl.br_shell(64)
-    osim, G = _pair(bbx, w, 100, 14, 8)
+    osim, G = _pair(bbx, w, 100, ty, tz)
     _check_state(osim, G, w)
     _check_activation(osim, G, 100)
     og = osim.grid
