@@ -51,7 +51,7 @@ class Geom(ctypes.Structure):
 class RunCfg(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int), ("par", ctypes.c_void_p), ("npar", ctypes.c_int),
                 ("stim", ctypes.c_void_p), ("amp", ctypes.c_double), ("t_on", ctypes.c_double),
-                ("t_off", ctypes.c_double), ("theta", ctypes.c_double)]
+                ("t_off", ctypes.c_double), ("theta", ctypes.c_double), ("split", ctypes.c_int)]
 
 
 _lib = None
@@ -178,8 +178,11 @@ def br_currents(y, par=None):
 class Sim:
     """Whole-grid stepping on the oracle: state is float64 [nvars][nz][ny][nx]."""
 
-    def __init__(self, grid: Grid, model, par=None, theta=None, state=None):
+    def __init__(self, grid: Grid, model, par=None, theta=None, state=None, split=False):
+        """split: Lie operator splitting (a diffusion substep, then the
+        kinetics step) instead of the unsplit step."""
         self.grid = grid
+        self.split = bool(split)
         self.model = model
         self.S = NVARS[model]
         self.par = np.zeros(0) if par is None else np.ascontiguousarray(par, dtype=np.float64)
@@ -206,7 +209,7 @@ class Sim:
 
     def _cfg(self):
         return RunCfg(self.model, _ptr(self.par) if self.par.size else None, self.par.size,
-                      _ptr(self.stim), self.amp, self.t_on, self.t_off, self.theta)
+                      _ptr(self.stim), self.amp, self.t_on, self.t_off, self.theta, int(self.split))
 
     def step(self, dt, n_steps=1):
         cfg = self._cfg()

@@ -393,7 +393,27 @@ typedef struct {
     const unsigned char* stim; /* NULL: no stimulus region */
     double amp, t_on, t_off;
     double theta;
+    int split; /* 0: unsplit (diff + euler); 1: Lie splitting (diffstep, then the kinetics step) */
 } orc_run_cfg;
+
+/* The update of one tissue node from its state y, its diffusion term L and
+ * stimulus Is, under the run's scheme.  Unsplit (section "Computation of
+ * intermediate expressions"): L enters the voltage equation of the kinetics
+ * step.  Lie splitting (section "Operator splitting"): first the diffusion
+ * substep V_{n+1/2} = V_n + dt L on its own, then the kinetics step from
+ * (V_{n+1/2}, the other variables at n) with no diffusion term; the stimulus
+ * belongs to the kinetics step. */
+static void node_update(const orc_run_cfg* c, const double* y, double L, double Is, double dt, double* yn) {
+    if (!c->split) {
+        orc_cell_update(c->model, c->par, c->npar, y, L, Is, dt, yn);
+        return;
+    }
+    double yh[8];
+    const int S = orc_nvars(c->model);
+    for (int v = 0; v < S; v++) yh[v] = y[v];
+    yh[0] = y[0] + dt * L;
+    orc_cell_update(c->model, c->par, c->npar, yh, 0.0, Is, dt, yn);
+}
 
 /* n_steps unsplit steps (section "Computation of intermediate expressions":
  * diff + euler/rushlarsen) in place on state (SoA, nvars*N doubles).
@@ -434,7 +454,7 @@ int orc_run(const orc_geom* g, const orc_run_cfg* c, double* state, double dt, i
             size_t p = gidx(g, cx[3 * i], cx[3 * i + 1], cx[3 * i + 2]);
             for (int v = 0; v < S; v++) y[v] = state[(size_t)v * N + p];
             double Is = (on && c->stim && c->stim[p]) ? c->amp : 0.0;
-            orc_cell_update(c->model, c->par, c->npar, y, L[i], Is, dt, yn);
+            node_update(c, y, L[i], Is, dt, yn);
             for (int v = 0; v < S; v++) state[(size_t)v * N + p] = yn[v];
             if (act && act[p] == INT32_MAX && y[0] < c->theta && c->theta <= yn[0])
                 act[p] = (int32_t)(*n + 1);
@@ -469,7 +489,7 @@ int orc_step_cells(const orc_geom* g, const orc_run_cfg* c, const double* state,
         orc_cell_weights(g, x, yy, z, W);
         double Lp = apply_weights(g, W, state, x, yy, z);
         double Is = (on && c->stim && c->stim[p]) ? c->amp : 0.0;
-        orc_cell_update(c->model, c->par, c->npar, y, Lp, Is, dt, yn);
+        node_update(c, y, Lp, Is, dt, yn);
         for (int v = 0; v < S; v++) out[(size_t)i * S + v] = yn[v];
     }
     return ORC_OK;
