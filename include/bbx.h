@@ -74,6 +74,10 @@ extern "C" {
 
 #define BBX_ACT_NONE 2147483647 /* activation map value of a node never activated */
 
+/* Time-stepping schemes (bbx_set_scheme). */
+#define BBX_SCHEME_UNSPLIT 0 /* diff + euler/rushlarsen: L enters the voltage equation */
+#define BBX_SCHEME_LIE 1     /* diffstep, then euler/rushlarsen: Lie operator splitting */
+
 typedef struct bbx_grid bbx_grid;
 
 typedef struct {
@@ -136,6 +140,15 @@ int bbx_set_stimulus(bbx_grid* g, const uint8_t* region_host, double amp, double
 /* Activation threshold theta (k_poincare device): a node's activation step is
  * the first n+1 with V^n < theta <= V^{n+1}.  Default: the model's threshold. */
 int bbx_set_threshold(bbx_grid* g, double theta);
+
+/* Time-stepping scheme.  BBX_SCHEME_UNSPLIT (default; section "Computation of
+ * intermediate expressions"): V^{n+1} = V^n + dt (f(V^n, g^n) + L V^n +
+ * I_stim), the other variables from (V^n, g^n).  BBX_SCHEME_LIE (section
+ * "Operator splitting"): first V^{n+1/2} = V^n + dt L V^n alone, then the
+ * kinetics step (Euler / Rush-Larsen, with the stimulus, without diffusion)
+ * from (V^{n+1/2}, g^n).  Applies to the following steps, in solo and batch
+ * stepping.  Errors: BBX_ERR_ARG (null grid, unknown scheme). */
+int bbx_set_scheme(bbx_grid* g, int scheme);
 
 /* Advance n_steps explicit steps of size dt (asynchronous on the grid's
  * stream).  Each step also writes the double-precision sum of the new V over

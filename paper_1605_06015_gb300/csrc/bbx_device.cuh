@@ -61,6 +61,7 @@ struct TissueArgs {  // (CUtensorMap members impose its alignment)
     double dt_d;           // time step, for t_{n+1} = t_n + dt
     int nx, ny, nz, px;
     float dt, theta, stim_amp;
+    int split;  // 1: Lie operator splitting (diffusion substep, then kinetics); 0: unsplit
     // diffusion constants over h^2: anisotropic D = Dperp I + (Dpar-Dperp) f f^T
     // gives c_perp = Dperp/h^2, c_d = (Dpar-Dperp)/h^2, c_dh = c_d/2 (edge
     // weights), c_s = c_d/4 (Wtilde); isotropic D gives c_iso = D/h^2.
@@ -741,6 +742,7 @@ struct PieceSlot : Coef {
     const uint8_t* stim;
     float stim_amp, dt, theta;
     int step_next;
+    int split;
     const SurrogateData* surr;  // nullptr: exact reaction everywhere
     float mp[8];
 };
@@ -869,6 +871,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                         r.dt = T->dt;
                         r.theta = T->theta;
                         r.step_next = (int)((L.single ? d0.n : D->n) + 1);
+                        r.split = T->split;
                         r.c_perp = T->c_perp; r.c_d = T->c_d; r.c_dh = T->c_dh; r.c_s = T->c_s; r.c_iso = T->c_iso;
                         r.surr = T->surr;
 #pragma unroll
@@ -1111,6 +1114,15 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                         for (int e = 0; e < 2; ++e) {
                             Isr[e] = 0.0f;
                             if (stim_on && live[r][e] && a.stim[gi + e]) Isr[e] = a.stim_amp;
+                        }
+                        if (a.split) {
+                            // Lie splitting: the diffusion substep on its own, then
+                            // the kinetics step from the half-step voltage
+#pragma unroll
+                            for (int e = 0; e < 2; ++e) {
+                                yv[e][0] += a.dt * Lr[r][e];
+                                Lr[r][e] = 0.0f;
+                            }
                         }
                         if constexpr (SURR && MODEL == BBX_BR) {
                             // the surrogate where the state is inside the training

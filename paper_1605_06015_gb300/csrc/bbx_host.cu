@@ -622,6 +622,7 @@ struct bbx_grid {
 
     SurrogateData* d_surr = nullptr;  // reaction surrogate (Beeler-Reuter), owned
     bool surr_on = false;
+    int split = 0;  // time-stepping scheme (bbx_set_scheme)
 
     double* d_partials = nullptr;  // bbx_total scratch
     unsigned int* d_ticket = nullptr;
@@ -788,6 +789,7 @@ int encode_targs(const bbx_grid* g, int ty, TissueArgs* t) {
     t->px = g->px;
     t->dt = (float)g->dt;
     t->theta = (float)g->theta;
+    t->split = g->split;
     t->stim_amp = g->d_stim ? (float)g->stim_amp : 0.0f;
     const double ih2 = 1.0 / (g->h * g->h);
     const double cd = (g->Dpar - g->Dperp) * ih2;
@@ -832,6 +834,7 @@ int refresh_targs(bbx_grid* g) {
     g->h_t.dt_d = g->dt;
     g->h_t.dt = (float)g->dt;
     g->h_t.theta = (float)g->theta;
+    g->h_t.split = g->split;
     g->h_t.stim = g->d_stim;
     g->h_t.stim_amp = g->d_stim ? (float)g->stim_amp : 0.0f;
     BBX_CUDA(cudaMemcpyAsync(g->d_t, &g->h_t, sizeof(TissueArgs), cudaMemcpyHostToDevice, g->stream));
@@ -1215,6 +1218,12 @@ int bbx_set_stimulus(bbx_grid* g, const uint8_t* region, double amp, double t_on
 int bbx_set_threshold(bbx_grid* g, double theta) {
     if (!g || !std::isfinite(theta)) return BBX_ERR_ARG;
     g->theta = theta;
+    return g->model ? refresh_targs(g) : BBX_OK;
+}
+
+int bbx_set_scheme(bbx_grid* g, int scheme) {
+    if (!g || (scheme != BBX_SCHEME_UNSPLIT && scheme != BBX_SCHEME_LIE)) return BBX_ERR_ARG;
+    g->split = scheme == BBX_SCHEME_LIE ? 1 : 0;
     return g->model ? refresh_targs(g) : BBX_OK;
 }
 

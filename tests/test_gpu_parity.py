@@ -162,6 +162,49 @@ def test_anisotropic_sheet_tiles_march_along_y(bbx, shape, ty, masked):
     _check_state(osim, G, w)
 
 
+@pytest.mark.parametrize("name", ["fhn", "barkley", "br"])
+def test_lie_splitting_matches_the_oracle(bbx, name):
+    """bbx_set_scheme(BBX_SCHEME_LIE): the diffusion substep, then the
+    kinetics step from the half-step voltage (section "Operator splitting"),
+    against the oracle's split mode."""
+    w = {"fhn": lambda: wl.fhn_sheet(90, 70), "barkley": lambda: wl.barkley_slab(70, 30, 12),
+         "br": lambda: wl.br_slab(72, 20, 8)}[name]()
+    rest = oracle.rest_state(w.model, w.params)
+    st0 = w.initial_state(rest).astype(np.float32)
+    og = oracle.Grid(w.nx, w.ny, w.nz, w.h, w.mask, w.fibres, w.D_par, w.D_perp)
+    osim = oracle.Sim(og, w.model, par=w.params, theta=w.theta, state=st0.astype(np.float64), split=True)
+    G = _gpu_grid(bbx, w)
+    G.set_scheme(bbx.BBX_SCHEME_LIE)
+    G.write_all(st0)
+    osim.step(w.dt, 100)
+    G.step(w.dt, 100)
+    _check_state(osim, G, w)
+    _check_activation(osim, G, 100)
+    # and the unsplit oracle is measurably different (the mode is not ignored)
+    ou = oracle.Sim(og, w.model, par=w.params, theta=w.theta, state=st0.astype(np.float64))
+    ou.step(w.dt, 100)
+    got = G.read_all()[0]
+    assert _rel_linf(got, ou.state[0], og.psi) > 10 * _rel_linf(got, osim.state[0], og.psi)
+
+
+def test_lie_splitting_of_pure_diffusion_is_the_unsplit_step(bbx):
+    w = wl.barkley_slab(40, 24, 10)
+    rng = np.random.default_rng(8)
+    st0 = rng.random((1,) + w.shape).astype(np.float32)
+    out = []
+    for scheme in (bbx.BBX_SCHEME_UNSPLIT, bbx.BBX_SCHEME_LIE):
+        G = bbx.Grid(w.nx, w.ny, w.nz, w.h, None)
+        G.set_fibres(w.fibres, w.D_par, w.D_perp)
+        G.set_ionic_model(bbx.BBX_DIFFUSION, None)
+        G.set_scheme(scheme)
+        G.write_all(st0)
+        G.step(w.dt, 50)
+        out.append(G.read_all())
+    assert np.abs(out[0] - out[1]).max() <= 2e-7 * np.abs(out[0]).max()
+    with pytest.raises(bbx.BbxError):
+        G.set_scheme(7)
+
+
 def test_stimulus_current(bbx):
     w = wl.fhn_sheet(70, 50)
     w.ic_fields = {}
