@@ -51,7 +51,8 @@ class Geom(ctypes.Structure):
 class RunCfg(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int), ("par", ctypes.c_void_p), ("npar", ctypes.c_int),
                 ("stim", ctypes.c_void_p), ("amp", ctypes.c_double), ("t_on", ctypes.c_double),
-                ("t_off", ctypes.c_double), ("theta", ctypes.c_double), ("split", ctypes.c_int)]
+                ("t_off", ctypes.c_double), ("theta", ctypes.c_double), ("split", ctypes.c_int),
+                ("rk4", ctypes.c_int)]
 
 
 _lib = None
@@ -71,6 +72,8 @@ def lib():
         L.orc_rest_state.argtypes = [I, P, I, P]
         L.orc_rest_state.restype = I
         L.orc_cell_update.argtypes = [I, P, I, P, D, D, D, P]
+        L.orc_cell_update_rk4.argtypes = [I, P, I, P, D, D, D, P]
+        L.orc_cell_update_rk4.restype = I
         L.orc_br_rates.argtypes = [D, P, P]
         L.orc_br_currents.argtypes = [P, P, P]
         L.orc_run.argtypes = [P, P, P, D, I, P, P, P]
@@ -161,6 +164,18 @@ def cell_update(model, y, L=0.0, Istim=0.0, dt=0.01, par=None):
     return yn[:NVARS[model]].copy()
 
 
+def cell_update_rk4(model, y, L=0.0, Istim=0.0, dt=0.01, par=None):
+    """One classical RK4 step of a single node (rhs models)."""
+    par = np.zeros(0) if par is None else np.ascontiguousarray(par, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    yn = np.zeros(8)
+    rc = lib().orc_cell_update_rk4(model, _ptr(par) if par.size else None, par.size, y.ctypes.data,
+                                   float(L), float(Istim), float(dt), yn.ctypes.data)
+    if rc != 0:
+        raise RuntimeError("oracle orc_cell_update_rk4 failed: %d" % rc)
+    return yn[:NVARS[model]].copy()
+
+
 def br_rates(V):
     a = np.zeros(6); b = np.zeros(6)
     lib().orc_br_rates(float(V), a.ctypes.data, b.ctypes.data)
@@ -178,11 +193,14 @@ def br_currents(y, par=None):
 class Sim:
     """Whole-grid stepping on the oracle: state is float64 [nvars][nz][ny][nx]."""
 
-    def __init__(self, grid: Grid, model, par=None, theta=None, state=None, split=False):
+    def __init__(self, grid: Grid, model, par=None, theta=None, state=None, split=False, rk4=False):
         """split: Lie operator splitting (a diffusion substep, then the
-        kinetics step) instead of the unsplit step."""
+        kinetics step) instead of the unsplit step.  rk4: the kinetics step by
+        the classical fourth-order Runge-Kutta scheme instead of forward Euler
+        (models given by a right-hand side)."""
         self.grid = grid
         self.split = bool(split)
+        self.rk4 = bool(rk4)
         self.model = model
         self.S = NVARS[model]
         self.par = np.zeros(0) if par is None else np.ascontiguousarray(par, dtype=np.float64)
@@ -209,7 +227,8 @@ class Sim:
 
     def _cfg(self):
         return RunCfg(self.model, _ptr(self.par) if self.par.size else None, self.par.size,
-                      _ptr(self.stim), self.amp, self.t_on, self.t_off, self.theta, int(self.split))
+                      _ptr(self.stim), self.amp, self.t_on, self.t_off, self.theta, int(self.split),
+                      int(self.rk4))
 
     def step(self, dt, n_steps=1):
         cfg = self._cfg()

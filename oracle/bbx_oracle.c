@@ -347,6 +347,51 @@ void orc_cell_update(int model, const double* par, int npar, const double* y, do
     }
 }
 
+/* Right-hand side of the ODE form of a model (section "Explicit solvers",
+ * Eq. (ODE)) with the diffusion term and stimulus together as a source I held
+ * fixed over the step on the voltage equation.  Models given by a right-hand
+ * side only (FHN, Barkley, ZFK, diffusion); returns ORC_ERR_ARG otherwise. */
+static int model_rhs(int model, const double* p, const double* y, double I, double* dy) {
+    switch (model) {
+        case ORC_FHN:
+            dy[0] = (y[0] - y[0] * y[0] * y[0] / 3.0 - y[1]) / p[0] + I;
+            dy[1] = p[0] * (y[0] + p[1] - p[2] * y[1]);
+            return ORC_OK;
+        case ORC_BARKLEY:
+            dy[0] = y[0] * (1.0 - y[0]) * (y[0] - (y[1] + p[1]) / p[0]) / p[2] + I;
+            dy[1] = y[0] - y[1];
+            return ORC_OK;
+        case ORC_ZFK:
+            dy[0] = y[0] * (y[0] - p[0]) * (1.0 - y[0]) + I;
+            return ORC_OK;
+        case ORC_DIFFUSION:
+            dy[0] = I;
+            return ORC_OK;
+    }
+    return ORC_ERR_ARG;
+}
+
+/* One step of the classical fourth-order Runge-Kutta scheme (the rk4
+ * kinetics solver of section "Explicit solvers") for the ODE of model_rhs with
+ * the source L + Istim: stages at t, t + dt/2, t + dt/2 and t + dt, weights
+ * 1/6, 1/3, 1/3, 1/6. */
+int orc_cell_update_rk4(int model, const double* par, int npar, const double* y, double L, double Istim,
+                        double dt, double* yn) {
+    double p[8], k1[8], k2[8], k3[8], k4[8], t[8];
+    model_params(model, par, npar, p);
+    const int S = orc_nvars(model);
+    const double I = L + Istim;
+    if (model_rhs(model, p, y, I, k1)) return ORC_ERR_ARG;
+    for (int v = 0; v < S; v++) t[v] = y[v] + 0.5 * dt * k1[v];
+    model_rhs(model, p, t, I, k2);
+    for (int v = 0; v < S; v++) t[v] = y[v] + 0.5 * dt * k2[v];
+    model_rhs(model, p, t, I, k3);
+    for (int v = 0; v < S; v++) t[v] = y[v] + dt * k3[v];
+    model_rhs(model, p, t, I, k4);
+    for (int v = 0; v < S; v++) yn[v] = y[v] + dt / 6.0 * (k1[v] + 2.0 * k2[v] + 2.0 * k3[v] + k4[v]);
+    return ORC_OK;
+}
+
 /* Rest state of a model: FHN by Newton on the cubic, Barkley and ZFK at 0,
  * BR by integrating the space-clamped cell (dt = 0.01 ms) for 20 s. */
 int orc_rest_state(int model, const double* par, int npar, double* y) {
@@ -394,7 +439,15 @@ typedef struct {
     double amp, t_on, t_off;
     double theta;
     int split; /* 0: unsplit (diff + euler); 1: Lie splitting (diffstep, then the kinetics step) */
+    int rk4;   /* kinetics solver: 0 forward Euler (Rush-Larsen gates for BR), 1 classical RK4 (rhs models) */
 } orc_run_cfg;
+
+static void kinetics(const orc_run_cfg* c, const double* y, double L, double Is, double dt, double* yn) {
+    if (c->rk4)
+        orc_cell_update_rk4(c->model, c->par, c->npar, y, L, Is, dt, yn);
+    else
+        orc_cell_update(c->model, c->par, c->npar, y, L, Is, dt, yn);
+}
 
 /* The update of one tissue node from its state y, its diffusion term L and
  * stimulus Is, under the run's scheme.  Unsplit (section "Computation of
@@ -405,14 +458,14 @@ typedef struct {
  * belongs to the kinetics step. */
 static void node_update(const orc_run_cfg* c, const double* y, double L, double Is, double dt, double* yn) {
     if (!c->split) {
-        orc_cell_update(c->model, c->par, c->npar, y, L, Is, dt, yn);
+        kinetics(c, y, L, Is, dt, yn);
         return;
     }
     double yh[8];
     const int S = orc_nvars(c->model);
     for (int v = 0; v < S; v++) yh[v] = y[v];
     yh[0] = y[0] + dt * L;
-    orc_cell_update(c->model, c->par, c->npar, yh, 0.0, Is, dt, yn);
+    kinetics(c, yh, 0.0, Is, dt, yn);
 }
 
 /* n_steps unsplit steps (section "Computation of intermediate expressions":
@@ -425,7 +478,7 @@ int orc_run(const orc_geom* g, const orc_run_cfg* c, double* state, double dt, i
             double* t, long long* n, int32_t* act) {
     const size_t N = (size_t)g->nx * g->ny * g->nz;
     const int S = orc_nvars(c->model);
-    if (S == 0) return ORC_ERR_ARG;
+    if (S == 0 || (c->rk4 && c->model == ORC_BR)) return ORC_ERR_ARG;
     int rc = orc_check_fibres(g);
     if (rc) return rc;
     size_t nt = 0;
@@ -473,7 +526,7 @@ int orc_step_cells(const orc_geom* g, const orc_run_cfg* c, const double* state,
                    double t, const long long* cells, int ncells, double* out) {
     const size_t N = (size_t)g->nx * g->ny * g->nz;
     const int S = orc_nvars(c->model);
-    if (S == 0) return ORC_ERR_ARG;
+    if (S == 0 || (c->rk4 && c->model == ORC_BR)) return ORC_ERR_ARG;
     int on = c->amp != 0.0 && t >= c->t_on && t < c->t_off;
     double W[27], y[8], yn[8];
     for (int i = 0; i < ncells; i++) {
