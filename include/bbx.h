@@ -78,6 +78,10 @@ extern "C" {
 #define BBX_SCHEME_UNSPLIT 0 /* diff + euler/rushlarsen: L enters the voltage equation */
 #define BBX_SCHEME_LIE 1     /* diffstep, then euler/rushlarsen: Lie operator splitting */
 
+/* Kinetics solvers (bbx_set_solver). */
+#define BBX_SOLVER_EULER 0 /* forward Euler; Rush-Larsen for the Beeler-Reuter gates */
+#define BBX_SOLVER_RK4 1   /* classical fourth-order Runge-Kutta (models given by a right-hand side) */
+
 typedef struct bbx_grid bbx_grid;
 
 typedef struct {
@@ -149,6 +153,16 @@ int bbx_set_threshold(bbx_grid* g, double theta);
  * from (V^{n+1/2}, g^n).  Applies to the following steps, in solo and batch
  * stepping.  Errors: BBX_ERR_ARG (null grid, unknown scheme). */
 int bbx_set_scheme(bbx_grid* g, int scheme);
+
+/* Kinetics solver (section "Explicit solvers").  BBX_SOLVER_EULER (default):
+ * forward Euler, Eq. (Euler), with Rush-Larsen gates for Beeler-Reuter.
+ * BBX_SOLVER_RK4: one classical fourth-order Runge-Kutta step of the model's
+ * ODE per time step, with the diffusion term and the stimulus held fixed over
+ * the step (unsplit scheme) or absent (Lie scheme); for FHN, Barkley, ZFK and
+ * pure diffusion.  Setting a Beeler-Reuter model resets it to Euler.  Errors:
+ * BBX_ERR_ARG (null grid, unknown solver), BBX_ERR_UNSUPPORTED (RK4 for
+ * Beeler-Reuter). */
+int bbx_set_solver(bbx_grid* g, int solver);
 
 /* Advance n_steps explicit steps of size dt (asynchronous on the grid's
  * stream).  Each step also writes the double-precision sum of the new V over

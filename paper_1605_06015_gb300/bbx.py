@@ -31,6 +31,7 @@ BBX_FHN, BBX_BARKLEY, BBX_BR, BBX_ZFK, BBX_DIFFUSION = 1, 2, 3, 4, 5
 NVARS = {BBX_FHN: 2, BBX_BARKLEY: 2, BBX_BR: 8, BBX_ZFK: 1, BBX_DIFFUSION: 1}
 BBX_ACT_NONE = 2147483647
 BBX_SCHEME_UNSPLIT, BBX_SCHEME_LIE = 0, 1
+BBX_SOLVER_EULER, BBX_SOLVER_RK4 = 0, 1
 
 
 class BbxError(RuntimeError):
@@ -77,6 +78,7 @@ def _load():
         "bbx_clear_device_error": [P],
         "bbx_set_timestep": [P, D],
         "bbx_set_scheme": [P, I],
+        "bbx_set_solver": [P, I],
         "bbx_batch_create": [ctypes.POINTER(P), ctypes.POINTER(P), I],
         "bbx_batch_step": [P, I],
         "bbx_batch_sync": [P],
@@ -310,6 +312,10 @@ def bbx_clear_device_error(g):
 
 def bbx_set_scheme(g, scheme):
     _check(_lib.bbx_set_scheme(g, int(scheme)), "bbx_set_scheme")
+
+
+def bbx_set_solver(g, solver):
+    _check(_lib.bbx_set_solver(g, int(solver)), "bbx_set_solver")
 
 
 def bbx_set_timestep(g, dt):

@@ -62,6 +62,7 @@ struct TissueArgs {  // (CUtensorMap members impose its alignment)
     int nx, ny, nz, px;
     float dt, theta, stim_amp;
     int split;  // 1: Lie operator splitting (diffusion substep, then kinetics); 0: unsplit
+    int rk4;    // kinetics solver: 1 classical RK4 (right-hand-side models), 0 forward Euler / Rush-Larsen
     // diffusion constants over h^2: anisotropic D = Dperp I + (Dpar-Dperp) f f^T
     // gives c_perp = Dperp/h^2, c_d = (Dpar-Dperp)/h^2, c_dh = c_d/2 (edge
     // weights), c_s = c_d/4 (Wtilde); isotropic D gives c_iso = D/h^2.
@@ -337,6 +338,12 @@ struct Model<BBX_FHN> {
         y[0] = u + dt * du;
         y[1] = v + dt * dv;
     }
+    // right-hand side with the source I (diffusion term + stimulus) on u
+    __device__ static __forceinline__ void rhs(const float* mp, const float* y, float I, float* dy) {
+        const float u = y[0], v = y[1];
+        dy[0] = (u - u * u * u * (1.0f / 3.0f) - v) * mp[0] + I;
+        dy[1] = mp[1] * (u + mp[2] - mp[3] * v);
+    }
 };
 
 // Barkley (1991): mp = {1/a, b, 1/eps}.
@@ -349,6 +356,11 @@ struct Model<BBX_BARKLEY> {
         y[0] = u + dt * du;
         y[1] = v + dt * (u - v);
     }
+    __device__ static __forceinline__ void rhs(const float* mp, const float* y, float I, float* dy) {
+        const float u = y[0], v = y[1];
+        dy[0] = u * (1.0f - u) * (u - (v + mp[1]) * mp[0]) * mp[2] + I;
+        dy[1] = u - v;
+    }
 };
 
 // ZFK / Nagumo reaction of Eq. (ZFKbidomV): mp = {alpha}.
@@ -359,6 +371,10 @@ struct Model<BBX_ZFK> {
         const float u = y[0];
         y[0] = u + dt * (u * (u - mp[0]) * (1.0f - u) + L + Is);
     }
+    __device__ static __forceinline__ void rhs(const float* mp, const float* y, float I, float* dy) {
+        const float u = y[0];
+        dy[0] = u * (u - mp[0]) * (1.0f - u) + I;
+    }
 };
 
 // Diffusion equation alone.
@@ -368,7 +384,32 @@ struct Model<BBX_DIFFUSION> {
     __device__ static __forceinline__ void update(const float*, float* y, float L, float Is, float dt) {
         y[0] = y[0] + dt * (L + Is);
     }
+    __device__ static __forceinline__ void rhs(const float*, const float*, float I, float* dy) { dy[0] = I; }
 };
+
+// One classical fourth-order Runge-Kutta step (the rk4 kinetics solver of
+// section "Explicit solvers") of a model given by its right-hand side, with
+// the diffusion term and stimulus held fixed over the step as a source on the
+// first variable: stages at t, t + dt/2, t + dt/2, t + dt; weights 1, 2, 2, 1
+// over 6.
+template <int MODEL>
+__device__ __forceinline__ void rk4_update(const float* mp, float* y, float L, float Is, float dt) {
+    constexpr int S = Model<MODEL>::S;
+    const float I = L + Is, h2 = 0.5f * dt;
+    float k1[S], k2[S], k3[S], k4[S], t[S];
+    Model<MODEL>::rhs(mp, y, I, k1);
+#pragma unroll
+    for (int v = 0; v < S; ++v) t[v] = y[v] + h2 * k1[v];
+    Model<MODEL>::rhs(mp, t, I, k2);
+#pragma unroll
+    for (int v = 0; v < S; ++v) t[v] = y[v] + h2 * k2[v];
+    Model<MODEL>::rhs(mp, t, I, k3);
+#pragma unroll
+    for (int v = 0; v < S; ++v) t[v] = y[v] + dt * k3[v];
+    Model<MODEL>::rhs(mp, t, I, k4);
+#pragma unroll
+    for (int v = 0; v < S; ++v) y[v] += (dt * (1.0f / 6.0f)) * ((k1[v] + k4[v]) + 2.0f * (k2[v] + k3[v]));
+}
 
 // Beeler-Reuter (1977).  State (V, Ca, x1, m, h, j, d, f); mp = {gNa, gNaC,
 // ENa, gs}.  V in mV, t in ms, Ca in mol/L, currents in uA/cm^2, Cm = 1.
@@ -742,7 +783,7 @@ struct PieceSlot : Coef {
     const uint8_t* stim;
     float stim_amp, dt, theta;
     int step_next;
-    int split;
+    int split, rk4;
     const SurrogateData* surr;  // nullptr: exact reaction everywhere
     float mp[8];
 };
@@ -872,6 +913,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                         r.theta = T->theta;
                         r.step_next = (int)((L.single ? d0.n : D->n) + 1);
                         r.split = T->split;
+                        r.rk4 = T->rk4;
                         r.c_perp = T->c_perp; r.c_d = T->c_d; r.c_dh = T->c_dh; r.c_s = T->c_s; r.c_iso = T->c_iso;
                         r.surr = T->surr;
 #pragma unroll
@@ -1153,6 +1195,14 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                                         Model<MODEL>::update(mp, yv[e], Lr[r][e], Isr[e], a.dt);
                                     }
                                 }
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < 2; ++e) Model<MODEL>::update(mp, yv[e], Lr[r][e], Isr[e], a.dt);
+                            }
+                        } else if constexpr (MODEL != BBX_BR) {
+                            if (a.rk4) {
+#pragma unroll
+                                for (int e = 0; e < 2; ++e) rk4_update<MODEL>(mp, yv[e], Lr[r][e], Isr[e], a.dt);
                             } else {
 #pragma unroll
                                 for (int e = 0; e < 2; ++e) Model<MODEL>::update(mp, yv[e], Lr[r][e], Isr[e], a.dt);

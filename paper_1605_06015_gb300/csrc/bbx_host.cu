@@ -623,6 +623,7 @@ struct bbx_grid {
     SurrogateData* d_surr = nullptr;  // reaction surrogate (Beeler-Reuter), owned
     bool surr_on = false;
     int split = 0;  // time-stepping scheme (bbx_set_scheme)
+    int rk4 = 0;    // kinetics solver (bbx_set_solver)
 
     double* d_partials = nullptr;  // bbx_total scratch
     unsigned int* d_ticket = nullptr;
@@ -790,6 +791,7 @@ int encode_targs(const bbx_grid* g, int ty, TissueArgs* t) {
     t->dt = (float)g->dt;
     t->theta = (float)g->theta;
     t->split = g->split;
+    t->rk4 = g->rk4;
     t->stim_amp = g->d_stim ? (float)g->stim_amp : 0.0f;
     const double ih2 = 1.0 / (g->h * g->h);
     const double cd = (g->Dpar - g->Dperp) * ih2;
@@ -835,6 +837,7 @@ int refresh_targs(bbx_grid* g) {
     g->h_t.dt = (float)g->dt;
     g->h_t.theta = (float)g->theta;
     g->h_t.split = g->split;
+    g->h_t.rk4 = g->rk4;
     g->h_t.stim = g->d_stim;
     g->h_t.stim_amp = g->d_stim ? (float)g->stim_amp : 0.0f;
     BBX_CUDA(cudaMemcpyAsync(g->d_t, &g->h_t, sizeof(TissueArgs), cudaMemcpyHostToDevice, g->stream));
@@ -1126,6 +1129,7 @@ int bbx_set_ionic_model(bbx_grid* g, int model, const double* params, int n_para
         return BBX_ERR_NOMEM;
     }
     if (model != BBX_BR) g->surr_on = false;
+    if (model == BBX_BR) g->rk4 = 0;  // Beeler-Reuter keeps Euler / Rush-Larsen
     g->model = model;
     g->S = S;
     for (int i = 0; i < 8; ++i) g->par[i] = p[i];
@@ -1224,6 +1228,13 @@ int bbx_set_threshold(bbx_grid* g, double theta) {
 int bbx_set_scheme(bbx_grid* g, int scheme) {
     if (!g || (scheme != BBX_SCHEME_UNSPLIT && scheme != BBX_SCHEME_LIE)) return BBX_ERR_ARG;
     g->split = scheme == BBX_SCHEME_LIE ? 1 : 0;
+    return g->model ? refresh_targs(g) : BBX_OK;
+}
+
+int bbx_set_solver(bbx_grid* g, int solver) {
+    if (!g || (solver != BBX_SOLVER_EULER && solver != BBX_SOLVER_RK4)) return BBX_ERR_ARG;
+    if (solver == BBX_SOLVER_RK4 && g->model == BBX_BR) return BBX_ERR_UNSUPPORTED;
+    g->rk4 = solver == BBX_SOLVER_RK4 ? 1 : 0;
     return g->model ? refresh_targs(g) : BBX_OK;
 }
 

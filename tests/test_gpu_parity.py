@@ -205,6 +205,44 @@ def test_lie_splitting_of_pure_diffusion_is_the_unsplit_step(bbx):
         G.set_scheme(7)
 
 
+@pytest.mark.parametrize("name,split", [("fhn", False), ("barkley", False), ("zfk", False), ("barkley", True)])
+def test_rk4_kinetics_matches_the_oracle(bbx, name, split):
+    """bbx_set_solver(BBX_SOLVER_RK4): one classical RK4 step of the kinetics
+    per time step (diffusion term frozen, or the Lie scheme), against the
+    oracle's RK4 mode; and Euler is measurably different."""
+    if name == "zfk":
+        nx, ny, nz = 50, 30, 9
+        rng = np.random.default_rng(4)
+        w = wl.Workload("zfk", nx, ny, nz, 0.5, 0.02, wl.ZFK, [0.13], 1.0, 0.3, fibres=wl.smooth_fibres(nx, ny, nz, 0.5),
+                        ic_fields={0: rng.random((nz, ny, nx))}, theta=0.5)
+    else:
+        w = {"fhn": lambda: wl.fhn_sheet(90, 70), "barkley": lambda: wl.barkley_slab(70, 30, 12)}[name]()
+    rest = oracle.rest_state(w.model, w.params)
+    st0 = w.initial_state(rest).astype(np.float32)
+    og = oracle.Grid(w.nx, w.ny, w.nz, w.h, w.mask, w.fibres, w.D_par, w.D_perp)
+    osim = oracle.Sim(og, w.model, par=w.params, theta=w.theta, state=st0.astype(np.float64), split=split, rk4=True)
+    G = _gpu_grid(bbx, w)
+    G.set_solver(bbx.BBX_SOLVER_RK4)
+    if split:
+        G.set_scheme(bbx.BBX_SCHEME_LIE)
+    G.write_all(st0)
+    osim.step(w.dt, 100)
+    G.step(w.dt, 100)
+    _check_state(osim, G, w)
+    _check_activation(osim, G, 100)
+    oe = oracle.Sim(og, w.model, par=w.params, theta=w.theta, state=st0.astype(np.float64), split=split)
+    oe.step(w.dt, 100)
+    got = G.read_all()[0]
+    assert _rel_linf(got, oe.state[0], og.psi) > 10 * _rel_linf(got, osim.state[0], og.psi)
+
+
+def test_rk4_refused_for_beeler_reuter(bbx):
+    w = wl.br_slab(20, 10, 4)
+    G = _gpu_grid(bbx, w)
+    with pytest.raises(bbx.BbxError):
+        G.set_solver(bbx.BBX_SOLVER_RK4)
+
+
 def test_stimulus_current(bbx):
     w = wl.fhn_sheet(70, 50)
     w.ic_fields = {}
