@@ -151,7 +151,9 @@ int bbx_set_threshold(bbx_grid* g, double theta);
  * "Operator splitting"): first V^{n+1/2} = V^n + dt L V^n alone, then the
  * kinetics step (Euler / Rush-Larsen, with the stimulus, without diffusion)
  * from (V^{n+1/2}, g^n).  Applies to the following steps, in solo and batch
- * stepping.  Errors: BBX_ERR_ARG (null grid, unknown scheme). */
+ * stepping.  The Lie scheme and the RK4 solver run on 7- and 14-row tiles
+ * only: a grid on 28-row tiles moves to 14.  Errors: BBX_ERR_ARG (null grid,
+ * unknown scheme). */
 int bbx_set_scheme(bbx_grid* g, int scheme);
 
 /* Kinetics solver (section "Explicit solvers").  BBX_SOLVER_EULER (default):

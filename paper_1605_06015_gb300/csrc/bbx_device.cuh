@@ -812,6 +812,10 @@ __device__ __forceinline__ void consumers_sync(int nthreads) {
 // Warp-specialised step kernel: warps 0..RY-1 compute (2 x CY nodes per
 // thread), warp RY is the producer.
 //
+// GEN: the variant that honours the per-grid scheme and solver settings (Lie
+// splitting, RK4 kinetics); the default variant (unsplit, Euler/Rush-Larsen)
+// carries no code for them.
+//
 // PLANAR (grids with nz = 1): a piece is a run of tiles down one column of
 // the sheet, pieces[i] = (x0, -, first tile, end tile); each stage holds one
 // tile with its one-row halo and the consumers march along y.  The z
@@ -822,7 +826,7 @@ __device__ __forceinline__ void consumers_sync(int nthreads) {
 // rings: full[s] completes when the plane's bulk copies have landed, empty[s]
 // when all RY consumer warps are done with the plane.  No CTA-wide barrier is
 // taken per plane.
-template <int MODEL, bool MASKED, bool ANISO, int TY, bool SURR = false, bool PLANAR = false>
+template <int MODEL, bool MASKED, bool ANISO, int TY, bool SURR = false, bool PLANAR = false, bool GEN = false>
 __global__ void __launch_bounds__(32 * rows_of_threads(TY) + 32, ctas_per_sm(MASKED, ANISO, TY, SURR))
 step_kernel(const __grid_constant__ LaunchArgs L) {
     using P = Plan<MODEL, MASKED, ANISO, TY, SURR>;
@@ -1157,7 +1161,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                             Isr[e] = 0.0f;
                             if (stim_on && live[r][e] && a.stim[gi + e]) Isr[e] = a.stim_amp;
                         }
-                        if (a.split) {
+                        if (GEN && a.split) {
                             // Lie splitting: the diffusion substep on its own, then
                             // the kinetics step from the half-step voltage
 #pragma unroll
@@ -1199,7 +1203,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
 #pragma unroll
                                 for (int e = 0; e < 2; ++e) Model<MODEL>::update(mp, yv[e], Lr[r][e], Isr[e], a.dt);
                             }
-                        } else if constexpr (MODEL != BBX_BR) {
+                        } else if constexpr (MODEL != BBX_BR && GEN) {
                             if (a.rk4) {
 #pragma unroll
                                 for (int e = 0; e < 2; ++e) rk4_update<MODEL>(mp, yv[e], Lr[r][e], Isr[e], a.dt);

@@ -14,11 +14,11 @@
 #include "bbx_mlp.cuh"
 
 namespace bbx {
-StepKernel step_kernel_fhn(bool masked, bool aniso, int ty, bool planar);
-StepKernel step_kernel_barkley(bool masked, bool aniso, int ty, bool planar);
-StepKernel step_kernel_br(bool masked, bool aniso, int ty, bool planar);
-StepKernel step_kernel_zfk(bool masked, bool aniso, int ty, bool planar);
-StepKernel step_kernel_diffusion(bool masked, bool aniso, int ty, bool planar);
+StepKernel step_kernel_fhn(bool masked, bool aniso, int ty, bool planar, bool general);
+StepKernel step_kernel_barkley(bool masked, bool aniso, int ty, bool planar, bool general);
+StepKernel step_kernel_br(bool masked, bool aniso, int ty, bool planar, bool general);
+StepKernel step_kernel_zfk(bool masked, bool aniso, int ty, bool planar, bool general);
+StepKernel step_kernel_diffusion(bool masked, bool aniso, int ty, bool planar, bool general);
 StepKernel step_kernel_br_surrogate(bool masked, bool aniso, int ty);
 }  // namespace bbx
 
@@ -75,16 +75,17 @@ void model_kernel_params(int model, const double* p, float* mp) {
 }
 
 // planar: a grid with nz = 1 (sheet kernels, tiles marched along y).  The
-// surrogate kernels exist for 3D grids only.
-StepKernel lookup_kernel(int model, bool masked, bool aniso, int ty, bool surrogate, bool planar) {
+// surrogate kernels exist for 3D grids only.  general: the grid uses the Lie
+// scheme or the RK4 solver (kernels for 7- and 14-row tiles).
+StepKernel lookup_kernel(int model, bool masked, bool aniso, int ty, bool surrogate, bool planar, bool general) {
     if (surrogate)
         return model == BBX_BR && !planar ? step_kernel_br_surrogate(masked, aniso, ty) : StepKernel{nullptr, 0, 0, 0};
     switch (model) {
-        case BBX_FHN: return step_kernel_fhn(masked, aniso, ty, planar);
-        case BBX_BARKLEY: return step_kernel_barkley(masked, aniso, ty, planar);
-        case BBX_BR: return step_kernel_br(masked, aniso, ty, planar);
-        case BBX_ZFK: return step_kernel_zfk(masked, aniso, ty, planar);
-        case BBX_DIFFUSION: return step_kernel_diffusion(masked, aniso, ty, planar);
+        case BBX_FHN: return step_kernel_fhn(masked, aniso, ty, planar, general);
+        case BBX_BARKLEY: return step_kernel_barkley(masked, aniso, ty, planar, general);
+        case BBX_BR: return step_kernel_br(masked, aniso, ty, planar, general);
+        case BBX_ZFK: return step_kernel_zfk(masked, aniso, ty, planar, general);
+        case BBX_DIFFUSION: return step_kernel_diffusion(masked, aniso, ty, planar, general);
     }
     return StepKernel{nullptr, 0, 0, 0};
 }
@@ -548,8 +549,8 @@ cudaError_t launch(const LaunchPlan& lp, const LaunchArgs& L, cudaStream_t s) {
 // Select the kernel for a configuration, check it fits, and return the CTA
 // budget (resident CTAs on the whole GPU).
 int select_kernel(int model, bool masked, bool aniso, int ty, int device, int num_sms, StepKernel* out,
-                  int* ctas, bool surrogate, bool planar) {
-    StepKernel k = lookup_kernel(model, masked, aniso, ty, surrogate, planar);
+                  int* ctas, bool surrogate, bool planar, bool general) {
+    StepKernel k = lookup_kernel(model, masked, aniso, ty, surrogate, planar, general);
     if (!k.fn) return BBX_ERR_UNSUPPORTED;
     int smem_optin = 0;
     if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
@@ -813,7 +814,7 @@ int prepare(bbx_grid* g) {
     StepKernel k;
     int ctas = 0;
     int rc = select_kernel(g->model, g->d_mask != nullptr, g->aniso, g->ty, g->device, g->num_sms, &k, &ctas,
-                           g->surr_on && g->model == BBX_BR, g->nz == 1);
+                           g->surr_on && g->model == BBX_BR, g->nz == 1, g->split || g->rk4);
     if (rc) return rc;
     if ((rc = encode_targs(g, g->ty, &g->h_t))) return rc;
     BBX_CUDA(cudaMemcpyAsync(g->d_t, &g->h_t, sizeof(TissueArgs), cudaMemcpyHostToDevice, g->stream));
@@ -1225,17 +1226,25 @@ int bbx_set_threshold(bbx_grid* g, double theta) {
     return g->model ? refresh_targs(g) : BBX_OK;
 }
 
+// The scheme and solver select the kernel variant (the general one has no
+// 28-row tiles: such a grid moves to 14 rows).
+static int apply_kinetics_setting(bbx_grid* g) {
+    if (!g->model) return BBX_OK;
+    if ((g->split || g->rk4) && g->ty == 28) return bbx_set_tiling(g, 14, g->zb);
+    return prepare(g);
+}
+
 int bbx_set_scheme(bbx_grid* g, int scheme) {
     if (!g || (scheme != BBX_SCHEME_UNSPLIT && scheme != BBX_SCHEME_LIE)) return BBX_ERR_ARG;
     g->split = scheme == BBX_SCHEME_LIE ? 1 : 0;
-    return g->model ? refresh_targs(g) : BBX_OK;
+    return apply_kinetics_setting(g);
 }
 
 int bbx_set_solver(bbx_grid* g, int solver) {
     if (!g || (solver != BBX_SOLVER_EULER && solver != BBX_SOLVER_RK4)) return BBX_ERR_ARG;
     if (solver == BBX_SOLVER_RK4 && g->model == BBX_BR) return BBX_ERR_UNSUPPORTED;
     g->rk4 = solver == BBX_SOLVER_RK4 ? 1 : 0;
-    return g->model ? refresh_targs(g) : BBX_OK;
+    return apply_kinetics_setting(g);
 }
 
 int bbx_set_timestep(bbx_grid* g, double dt) {
@@ -1563,7 +1572,7 @@ extern "C" int bbx_sample_reaction_pairs(bbx_grid* g, long long n, unsigned long
 struct bbx_batch {
     struct Group {
         int model = 0;
-        bool masked = false, aniso = false, surr = false, planar = false;
+        bool masked = false, aniso = false, surr = false, planar = false, general = false;
         int ty = 14;
         std::vector<int> members;  // indices into grids
         TissueArgs* d_t = nullptr;  // one TissueArgs per member (tensor maps for this group's ty)
@@ -1620,7 +1629,8 @@ int batch_build(bbx_batch* b, const std::vector<int>* tys) {
         for (; gi < b->groups.size(); ++gi) {
             auto& gr = b->groups[gi];
             if (gr.model == g->model && gr.masked == (g->d_mask != nullptr) && gr.aniso == g->aniso &&
-                gr.surr == (g->surr_on && g->model == BBX_BR) && gr.planar == (g->nz == 1))
+                gr.surr == (g->surr_on && g->model == BBX_BR) && gr.planar == (g->nz == 1) &&
+                gr.general == (g->split || g->rk4))
                 break;
         }
         if (gi == b->groups.size()) {
@@ -1630,6 +1640,7 @@ int batch_build(bbx_batch* b, const std::vector<int>* tys) {
             gr.aniso = g->aniso;
             gr.surr = g->surr_on && g->model == BBX_BR;
             gr.planar = g->nz == 1;
+            gr.general = g->split || g->rk4;
             b->groups.push_back(gr);
         }
         b->groups[gi].members.push_back((int)i);
@@ -1675,7 +1686,7 @@ int batch_build(bbx_batch* b, const std::vector<int>* tys) {
         auto& gr = b->groups[gi];
         int ctas = 0;
         int rc = select_kernel(gr.model, gr.masked, gr.aniso, gr.ty, b->device, b->num_sms, &gr.lp.k, &ctas, gr.surr,
-                               gr.planar);
+                               gr.planar, gr.general);
         if (rc) return rc;
         long long share = total_work > 0 ? (long long)((double)ctas * gr.work / total_work + 0.5) : 1;
         if (share < 1) share = 1;

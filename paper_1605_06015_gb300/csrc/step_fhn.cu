@@ -3,18 +3,22 @@
 
 namespace bbx {
 
-template <bool MA, bool AN, int TY, bool PL>
+template <bool MA, bool AN, int TY, bool PL, bool GE>
 static StepKernel make_fhn() {
     using P = Plan<BBX_FHN, MA, AN, TY>;
-    return StepKernel{reinterpret_cast<const void*>(&step_kernel<BBX_FHN, MA, AN, TY, false, PL>), P::SMEM, P::THREADS,
-                      TY};
+    return StepKernel{reinterpret_cast<const void*>(&step_kernel<BBX_FHN, MA, AN, TY, false, PL, GE>), P::SMEM,
+                      P::THREADS, TY};
 }
 
-// planar: grids with nz = 1 (tiles marched along y)
-StepKernel step_kernel_fhn(bool masked, bool aniso, int ty, bool planar) {
+// planar: grids with nz = 1 (tiles marched along y); general: the variant
+// for the Lie scheme or the RK4 solver (7- and 14-row tiles)
+StepKernel step_kernel_fhn(bool masked, bool aniso, int ty, bool planar, bool general) {
 #define BBX_CASE(MA, AN, T) \
-    if (masked == MA && aniso == AN && ty == T) \
-        return planar ? make_fhn<MA, AN, T, true>() : make_fhn<MA, AN, T, false>();
+    if (masked == MA && aniso == AN && ty == T) { \
+        if (general && T == 28) return StepKernel{nullptr, 0, 0, 0}; \
+        if (general) return planar ? make_fhn<MA, AN, T, true, T != 28>() : make_fhn<MA, AN, T, false, T != 28>(); \
+        return planar ? make_fhn<MA, AN, T, true, false>() : make_fhn<MA, AN, T, false, false>(); \
+    }
     BBX_CASE(false, false, 7) BBX_CASE(false, false, 14) BBX_CASE(false, false, 28)
     BBX_CASE(false, true, 7) BBX_CASE(false, true, 14) BBX_CASE(false, true, 28)
     BBX_CASE(true, false, 7) BBX_CASE(true, false, 14) BBX_CASE(true, false, 28)
