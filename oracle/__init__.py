@@ -8,6 +8,8 @@ by passage (each function names its equation).
 Parity status per function (see ``bbx_oracle.c`` for the passages):
   tensor, weights, L, FHN, Barkley, ZFK, Euler, Rush-Larsen, activation,
   total, active bricks: pinned by the tests in ``tests/test_oracle_*.py``.
+  output.py (byte quantisation, colour map, phase singularities): pinned by
+  tests/test_oracle_output.py.
   Beeler-Reuter constants: PARITY UNPINNED (the paper does not print them;
   transcribed from Beeler & Reuter 1977, checked only qualitatively).
 """
