@@ -145,6 +145,33 @@ int bbx_set_stimulus(bbx_grid* g, const uint8_t* region_host, double amp, double
  * the first n+1 with V^n < theta <= V^{n+1}.  Default: the model's threshold. */
 int bbx_set_threshold(bbx_grid* g, double theta);
 
+/* Headless output, 1 byte per value (the ppmout device, section "Input and
+ * output"): for every node, in the order z, y, x (x fastest), three bytes
+ * (R, G, B), channel c = floor(255 t + 0.5) with t = (V_c - lo[c]) / (hi[c] -
+ * lo[c]) clamped to [0, 1], evaluated in float32 with one rounding per
+ * operation, V_c the current value of state variable layers[c]; layers[c] =
+ * -1 gives a dark channel, void nodes are black.  out_dev: device buffer of
+ * 3 nx ny nz bytes, owned by the caller.  The sample script's colour map
+ * (red = u, green = v / 0.8) is layers {0, 1, -1}, lo {0, 0, 0}, hi {1, 0.8,
+ * 1}.  Asynchronous on the grid's stream (after a synchronising read of the
+ * buffer parity).  Errors: BBX_ERR_ARG (null pointers, layer out of range,
+ * hi == lo or non-finite bounds), BBX_ERR_STATE (no model). */
+int bbx_ppm_frame(bbx_grid* g, const int* layers, const double* lo, const double* hi, uint8_t* out_dev);
+
+/* Phase singularities (the singz device, section "Input and output"): in every
+ * z cross-section, the intersections of the isolines var_a = iso_a and var_b =
+ * iso_b inside grid cells whose four corners are tissue.  An isoline crosses a
+ * cell edge where V - iso is > 0 at one end only, at the linearly
+ * interpolated point; a cell with exactly two crossings of each isoline holds
+ * one piece of each, and their intersection, when it lies on both pieces, is
+ * reported as (x, y, z) in grid units (float32).  Up to max_points points are
+ * written to xyz_dev (3 floats each, device memory owned by the caller), in
+ * no particular order; *n_found receives the number found (which may exceed
+ * max_points).  Synchronises the grid's stream.  Errors: BBX_ERR_ARG,
+ * BBX_ERR_STATE, BBX_ERR_NOMEM (its 4-byte counter, allocated on first use). */
+int bbx_phase_singularities(bbx_grid* g, int var_a, double iso_a, int var_b, double iso_b, float* xyz_dev,
+                            int max_points, int* n_found);
+
 /* Time-stepping scheme.  BBX_SCHEME_UNSPLIT (default; section "Computation of
  * intermediate expressions"): V^{n+1} = V^n + dt (f(V^n, g^n) + L V^n +
  * I_stim), the other variables from (V^n, g^n).  BBX_SCHEME_LIE (section

@@ -79,6 +79,8 @@ def _load():
         "bbx_set_timestep": [P, D],
         "bbx_set_scheme": [P, I],
         "bbx_set_solver": [P, I],
+        "bbx_ppm_frame": [P, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D), P],
+        "bbx_phase_singularities": [P, I, D, I, D, P, I, ctypes.POINTER(I)],
         "bbx_batch_create": [ctypes.POINTER(P), ctypes.POINTER(P), I],
         "bbx_batch_step": [P, I],
         "bbx_batch_sync": [P],
@@ -257,6 +259,23 @@ def bbx_total(g, var=0):
     out = ctypes.c_double()
     _check(_lib.bbx_total(g, int(var), ctypes.byref(out)), "bbx_total")
     return out.value
+
+
+def bbx_ppm_frame(g, layers, lo, hi, out_dev):
+    """out_dev: a device uint8 tensor of 3*nx*ny*nz bytes (filled on the grid's stream)."""
+    ly = (ctypes.c_int * 3)(*[int(v) for v in layers])
+    l3 = (ctypes.c_double * 3)(*[float(v) for v in lo])
+    h3 = (ctypes.c_double * 3)(*[float(v) for v in hi])
+    _check(_lib.bbx_ppm_frame(g, ly, l3, h3, _devptr(out_dev)), "bbx_ppm_frame")
+
+
+def bbx_phase_singularities(g, var_a, iso_a, var_b, iso_b, xyz_dev, max_points):
+    """Fills xyz_dev (a device float32 tensor of 3*max_points) and returns the
+    number of points found."""
+    n = ctypes.c_int()
+    _check(_lib.bbx_phase_singularities(g, int(var_a), float(iso_a), int(var_b), float(iso_b), _devptr(xyz_dev),
+                                        int(max_points), ctypes.byref(n)), "bbx_phase_singularities")
+    return n.value
 
 
 def bbx_step_total(g):

@@ -20,6 +20,12 @@ StepKernel step_kernel_br(bool masked, bool aniso, int ty, bool planar, bool gen
 StepKernel step_kernel_zfk(bool masked, bool aniso, int ty, bool planar, bool general);
 StepKernel step_kernel_diffusion(bool masked, bool aniso, int ty, bool planar, bool general);
 StepKernel step_kernel_br_surrogate(bool masked, bool aniso, int ty);
+cudaError_t launch_ppm(const float* state, const uint8_t* mask, long long vol, int nx, int ny, int nz, int px,
+                       long long plane, const int layer[3], const float lo[3], const float hi[3], uint8_t* out,
+                       int num_sms, cudaStream_t s);
+cudaError_t launch_singz(const float* fa, const float* fb, float iso_a, float iso_b, const uint8_t* mask, int nx,
+                         int ny, int nz, int px, long long plane, float* xyz, int max_points, int* d_count,
+                         int num_sms, cudaStream_t s);
 }  // namespace bbx
 
 using namespace bbx;
@@ -630,6 +636,7 @@ struct bbx_grid {
     unsigned int* d_ticket = nullptr;
     double* d_total2 = nullptr;
     int* d_err = nullptr;
+    int* d_count = nullptr;  // phase-singularity counter (allocated on first use)
     int poison = 0;
 };
 
@@ -945,6 +952,7 @@ void bbx_destroy_grid(bbx_grid* g) {
     cudaFree(g->d_ticket);
     cudaFree(g->d_total2);
     cudaFree(g->d_err);
+    cudaFree(g->d_count);
     cudaGetLastError();
     delete g;
 }
@@ -1340,6 +1348,48 @@ int bbx_total(bbx_grid* g, int var, double* out) {
                                            g->nz, g->px, g->plane, g->d_partials, g->d_ticket, g->d_total2, g->d_err);
     BBX_CUDA(cudaGetLastError());
     BBX_CUDA(cudaMemcpyAsync(out, g->d_total2, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    return check_sticky(g);
+}
+
+int bbx_ppm_frame(bbx_grid* g, const int* layers, const double* lo, const double* hi, uint8_t* out_dev) {
+    if (!g || !layers || !lo || !hi || !out_dev) return BBX_ERR_ARG;
+    if (!g->model) return BBX_ERR_STATE;
+    int ly[3];
+    float l[3], h[3];
+    for (int c = 0; c < 3; ++c) {
+        ly[c] = layers[c];
+        l[c] = (float)lo[c];
+        h[c] = (float)hi[c];
+        if (ly[c] < -1 || ly[c] >= g->S) return BBX_ERR_ARG;
+        if (ly[c] >= 0 && !(std::isfinite(l[c]) && std::isfinite(h[c]) && h[c] != l[c])) return BBX_ERR_ARG;
+    }
+    TissueDyn d;
+    int rc = read_dyn(g, &d);
+    if (rc) return rc;
+    BBX_CUDA(launch_ppm(g->d_state[d.cur], g->d_mask, g->vol, g->nx, g->ny, g->nz, g->px, g->plane, ly, l, h,
+                        out_dev, g->num_sms, g->stream));
+    return BBX_OK;
+}
+
+int bbx_phase_singularities(bbx_grid* g, int var_a, double iso_a, int var_b, double iso_b, float* xyz_dev,
+                            int max_points, int* n_found) {
+    if (!g || !n_found || max_points < 0 || (max_points > 0 && !xyz_dev)) return BBX_ERR_ARG;
+    if (!g->model) return BBX_ERR_STATE;
+    if (var_a < 0 || var_a >= g->S || var_b < 0 || var_b >= g->S || !std::isfinite(iso_a) || !std::isfinite(iso_b))
+        return BBX_ERR_ARG;
+    if (!g->d_count && dmalloc(&g->d_count, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return BBX_ERR_NOMEM;
+    }
+    TissueDyn d;
+    int rc = read_dyn(g, &d);
+    if (rc) return rc;
+    const float* st = g->d_state[d.cur];
+    BBX_CUDA(launch_singz(st + (size_t)var_a * g->vol, st + (size_t)var_b * g->vol, (float)iso_a, (float)iso_b,
+                          g->d_mask, g->nx, g->ny, g->nz, g->px, g->plane, xyz_dev, max_points, g->d_count,
+                          g->num_sms, g->stream));
+    BBX_CUDA(cudaMemcpyAsync(n_found, g->d_count, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    BBX_CUDA(cudaStreamSynchronize(g->stream));
     return check_sticky(g);
 }
 

@@ -1,0 +1,139 @@
+// Headless output kernels: the 1-byte quantisation of three layers of the
+// grid (the ppmout device of section "Input and output"), and phase
+// singularities in z cross-sections as intersections of the isolines of two
+// fields inside a grid cell (the singz device of the same section).  Both
+// read the current state in its padded device layout; neither allocates.
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace bbx {
+
+namespace {
+
+constexpr uint8_t kTissue = 1;  // mask bit 0: the node is tissue
+
+// t = (v - lo) / (hi - lo) clamped to [0, 1]; code = floor(255 t + 0.5), each
+// operation rounded once (no contraction), so the host can reproduce it.
+__device__ __forceinline__ uint8_t quantise(float v, float lo, float span) {
+    float t = __fdiv_rn(__fsub_rn(v, lo), span);
+    t = fminf(fmaxf(t, 0.0f), 1.0f);
+    return (uint8_t)floorf(__fadd_rn(__fmul_rn(t, 255.0f), 0.5f));
+}
+
+__global__ void k_ppm(const float* __restrict__ state, const uint8_t* __restrict__ mask, long long vol, int nx,
+                      int ny, int nz, int px, long long plane, int3 layer, float3 lo, float3 span,
+                      uint8_t* __restrict__ out) {
+    const long long n = (long long)nx * ny * nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = int(i % nx);
+        const long long r = i / nx;
+        const int y = int(r % ny), z = int(r / ny);
+        const long long gi = z * plane + (long long)y * px + x;
+        uint8_t c0 = 0, c1 = 0, c2 = 0;
+        if (!mask || (mask[gi] & kTissue)) {
+            if (layer.x >= 0) c0 = quantise(state[layer.x * vol + gi], lo.x, span.x);
+            if (layer.y >= 0) c1 = quantise(state[layer.y * vol + gi], lo.y, span.y);
+            if (layer.z >= 0) c2 = quantise(state[layer.z * vol + gi], lo.z, span.z);
+        }
+        out[3 * i] = c0;
+        out[3 * i + 1] = c1;
+        out[3 * i + 2] = c2;
+    }
+}
+
+// Crossings of the isoline f = 0 (g = f - f*) with the four edges of a cell
+// (corners (0,0), (1,0), (1,1), (0,1)); an edge is crossed where g > 0 at one
+// end only.  Returns the number of crossings; the first two are in p.
+__device__ __forceinline__ int cell_crossings(const float g[4], float2 p[2]) {
+    const float cx[4] = {0.0f, 1.0f, 1.0f, 0.0f}, cy[4] = {0.0f, 0.0f, 1.0f, 1.0f};
+    int n = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int j = (i + 1) & 3;
+        if ((g[i] > 0.0f) != (g[j] > 0.0f)) {
+            const float s = __fdiv_rn(g[i], __fsub_rn(g[i], g[j]));
+            if (n < 2) p[n] = make_float2(cx[i] + s * (cx[j] - cx[i]), cy[i] + s * (cy[j] - cy[i]));
+            ++n;
+        }
+    }
+    return n;
+}
+
+__global__ void k_singz(const float* __restrict__ fa, const float* __restrict__ fb, float iso_a, float iso_b,
+                        const uint8_t* __restrict__ mask, int nx, int ny, int nz, int px, long long plane,
+                        float* __restrict__ xyz, int max_points, int* __restrict__ count) {
+    const long long cx = nx - 1, cy = ny - 1;
+    const long long n = cx * cy * nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = int(i % cx);
+        const long long r = i / cx;
+        const int y = int(r % cy), z = int(r / cy);
+        const long long g0 = z * plane + (long long)y * px + x;
+        const long long gi[4] = {g0, g0 + 1, g0 + px + 1, g0 + px};  // corners in cell order
+        bool tis = true;
+        if (mask) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) tis = tis && (mask[gi[k]] & kTissue);
+        }
+        if (!tis) continue;
+        float ga[4], gb[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            ga[k] = __fsub_rn(fa[gi[k]], iso_a);
+            gb[k] = __fsub_rn(fb[gi[k]], iso_b);
+        }
+        float2 pa[2], pb[2];
+        if (cell_crossings(ga, pa) != 2 || cell_crossings(gb, pb) != 2) continue;
+        // pa0 + al (pa1 - pa0) = pb0 + be (pb1 - pb0)
+        const float d1x = pa[1].x - pa[0].x, d1y = pa[1].y - pa[0].y;
+        const float d2x = pb[1].x - pb[0].x, d2y = pb[1].y - pb[0].y;
+        const float det = d1y * d2x - d1x * d2y;
+        if (det == 0.0f) continue;
+        const float rx = pb[0].x - pa[0].x, ry = pb[0].y - pa[0].y;
+        const float al = (ry * d2x - rx * d2y) / det;
+        const float be = (d1x * ry - d1y * rx) / det;
+        if (!(al >= 0.0f && al <= 1.0f && be >= 0.0f && be <= 1.0f)) continue;
+        const int k = atomicAdd(count, 1);
+        if (k < max_points) {
+            xyz[3 * k] = (float)x + pa[0].x + al * d1x;
+            xyz[3 * k + 1] = (float)y + pa[0].y + al * d1y;
+            xyz[3 * k + 2] = (float)z;
+        }
+    }
+}
+
+int blocks_for(long long n, int num_sms) {
+    long long b = (n + 255) / 256;
+    const long long cap = (long long)num_sms * 8;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+}  // namespace
+
+cudaError_t launch_ppm(const float* state, const uint8_t* mask, long long vol, int nx, int ny, int nz, int px,
+                       long long plane, const int layer[3], const float lo[3], const float hi[3], uint8_t* out,
+                       int num_sms, cudaStream_t s) {
+    const long long n = (long long)nx * ny * nz;
+    k_ppm<<<blocks_for(n, num_sms), 256, 0, s>>>(state, mask, vol, nx, ny, nz, px, plane,
+                                                 make_int3(layer[0], layer[1], layer[2]),
+                                                 make_float3(lo[0], lo[1], lo[2]),
+                                                 make_float3(hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]), out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_singz(const float* fa, const float* fb, float iso_a, float iso_b, const uint8_t* mask, int nx,
+                         int ny, int nz, int px, long long plane, float* xyz, int max_points, int* d_count,
+                         int num_sms, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    const long long n = (long long)(nx - 1) * (ny - 1) * nz;
+    if (n <= 0) return cudaSuccess;
+    k_singz<<<blocks_for(n, num_sms), 256, 0, s>>>(fa, fb, iso_a, iso_b, mask, nx, ny, nz, px, plane, xyz, max_points,
+                                                   d_count);
+    return cudaGetLastError();
+}
+
+}  // namespace bbx
