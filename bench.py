@@ -39,8 +39,11 @@ METRIC = "cell-updates/s"
 
 
 def kernel_source_hash():
+    """Hash of the step kernel's sources (the device header and the per-model
+    instantiations): DRAM counters taken on other sources do not apply."""
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1605_06015_gb300", "csrc", "*"))):
+    csrc = os.path.join(ROOT, "paper_1605_06015_gb300", "csrc")
+    for p in sorted(glob.glob(os.path.join(csrc, "bbx_device.cuh")) + glob.glob(os.path.join(csrc, "step_*.cu"))):
         with open(p, "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -435,6 +438,41 @@ def run_configs(args, dev, stream, dist=None, n_ranks=1):
     return out
 
 
+def run_output(args, dev, stream, G, w, n_tissue):
+    """The headless output kernels on the bench slab: a 3-layer byte frame
+    (15 B per node: three float layers read, three bytes written) and the
+    phase singularities of (u, v) (8 B per node), device-timed, L2 flushed
+    before each call."""
+    import torch
+    peak, _ = load_peaks()
+    frame = torch.empty(3 * w.n_cells, dtype=torch.uint8, device=dev)
+    xyz = torch.empty(3 * 65536, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {}
+    for name in ("ppm_frame", "phase_singularities"):
+        ts, found = [], 0
+        for i in range(12):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if name == "ppm_frame":
+                G.ppm_frame((0, 1, -1), (0.0, 0.0, 0.0), (1.0, 0.8, 1.0), frame)
+            else:
+                found = G.phase_singularities(0, 0.5, 1, 0.3, xyz, 65536)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= 2:
+                ts.append(e0.elapsed_time(e1) * 1e-3)
+        sec = sum(ts) / len(ts)
+        b = 15 if name == "ppm_frame" else 8
+        res[name] = {"us_per_call": sec * 1e6, "bytes_per_node": b, "GB_s": b * w.n_cells / sec / 1e9,
+                     "roofline_frac": b * w.n_cells / sec / 1e9 / peak}
+        if name != "ppm_frame":
+            res[name]["points"] = found
+    return res
+
+
 def run_bbx(args):
     import numpy as np
     import torch
@@ -512,6 +550,7 @@ def run_bbx(args):
     batched = None
     if not args.no_batched:
         batched = run_batched(args, dev, stream, dist, ws)
+    output = run_output(args, dev, stream, G, w, n_tissue)
     configs = None
     if args.configs:
         configs = run_configs(args, dev, stream, dist, ws)
@@ -541,6 +580,7 @@ def run_bbx(args):
         "batched": batched,
         "surrogate": surrogate,
         "configs": configs,
+        "output_kernels": output,
         "gpu_launches": args.steps,
         "clocks": clk,
         "tissue_total_V": total_v,

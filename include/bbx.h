@@ -153,8 +153,7 @@ int bbx_set_threshold(bbx_grid* g, double theta);
  * -1 gives a dark channel, void nodes are black.  out_dev: device buffer of
  * 3 nx ny nz bytes, owned by the caller.  The sample script's colour map
  * (red = u, green = v / 0.8) is layers {0, 1, -1}, lo {0, 0, 0}, hi {1, 0.8,
- * 1}.  Asynchronous on the grid's stream (after a synchronising read of the
- * buffer parity).  Errors: BBX_ERR_ARG (null pointers, layer out of range,
+ * 1}.  Asynchronous on the grid's stream.  Errors: BBX_ERR_ARG (null pointers, layer out of range,
  * hi == lo or non-finite bounds), BBX_ERR_STATE (no model). */
 int bbx_ppm_frame(bbx_grid* g, const int* layers, const double* lo, const double* hi, uint8_t* out_dev);
 

@@ -680,11 +680,15 @@ __device__ __forceinline__ float lap_general(const Coef& a, const Nb& n, const P
 // [out][in] as 32-bit pairs (W1 padded to 16 inputs), FP32 biases, the
 // normalisation and envelope, and the upstroke threshold.
 struct SurrogateData {
-    uint32_t W1[64 * 8];   // [64][16] bf16
-    uint32_t W2[64 * 32];  // [64][64] bf16
-    uint32_t W3[8 * 32];   // [8][64] bf16
+    // BF16 pairs in MMA-fragment order: for output row n and lane t (of
+    // the 4 lanes sharing a row group), the words holding input columns
+    // (2t, 2t+1) and (2t+8, 2t+9) of each 16-wide k-step are adjacent.
+    uint32_t W1[64 * 8];   // [64 rows][4 lanes][b0, b1]      (inputs padded to 16)
+    uint32_t W2[64 * 32];  // [64 rows][4 lanes][4 k-steps][b0, b1]
+    uint32_t W3[8 * 32];   // [8 rows][4 lanes][4 k-steps][b0, b1]
     float b1[64], b2[64], b3[8];
     float norm[48];        // mu_in, sd_in, mu_out, sd_out, lo, hi (8 each)
+    float inv_sd_in[8];    // 1 / sd_in
     float v_up;            // the exact model runs where V >= v_up
 };
 
@@ -701,10 +705,21 @@ __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint32_t b
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// ReLU and BF16 packing of two FP32 values in one instruction (lo in the low
+// half, as the MMA fragments expect).
+__device__ __forceinline__ uint32_t relu_pack_bf16(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
 // The network on the 64 nodes of one warp row (2 per lane) with tensor-core
 // MMAs (m16n8k16, BF16 inputs, FP32 accumulation), four m-tiles of 16 nodes.
 // Hidden activations stay in registers: the accumulators of two adjacent
-// 8-column tiles are the A fragment of the next layer's 16-wide k-tile.
+// 8-column tiles are the A fragment of the next layer's 16-wide k-tile.  The
+// accumulators start from the bias, ReLU and BF16 packing are one instruction
+// per pair, and each lane's B fragments are stored contiguously
+// (k_build_surrogate), one 64- or 128-bit load per MMA or pair of MMAs.
 // wbuf: this warp's 2 KB of shared memory (64 rows of 32 bytes), first the
 // BF16 inputs of a row, then, row by row, its 8 FP32 outputs.  All 32 lanes
 // must call it.  s: the two nodes' raw states; d: their raw increments.
@@ -717,12 +732,15 @@ __device__ __forceinline__ void surrogate_warp64(const SurrogateData* __restrict
         uint32_t* row = reinterpret_cast<uint32_t*>(wbuf + (lane * 2 + e) * 32);
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            row[k] = pack_bf16((s[e][2 * k] - nrm[2 * k]) / nrm[8 + 2 * k],
-                               (s[e][2 * k + 1] - nrm[2 * k + 1]) / nrm[8 + 2 * k + 1]);
+            row[k] = pack_bf16((s[e][2 * k] - nrm[2 * k]) * W->inv_sd_in[2 * k],
+                               (s[e][2 * k + 1] - nrm[2 * k + 1]) * W->inv_sd_in[2 * k + 1]);
 #pragma unroll
         for (int k = 4; k < 8; ++k) row[k] = 0u;
     }
     __syncwarp();
+    const uint2* W1 = reinterpret_cast<const uint2*>(W->W1);  // [row][lane t]: (b0, b1)
+    const uint4* W2 = reinterpret_cast<const uint4*>(W->W2);  // [row][lane t][kk pair]: (b0, b1, b0', b1')
+    const uint4* W3 = reinterpret_cast<const uint4*>(W->W3);
 #pragma unroll 1
     for (int q = 0; q < 4; ++q) {
         uint32_t* X = reinterpret_cast<uint32_t*>(wbuf + q * 16 * 32);
@@ -731,42 +749,47 @@ __device__ __forceinline__ void surrogate_warp64(const SurrogateData* __restrict
         uint32_t h[4][4];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            float c[4] = {0.f, 0.f, 0.f, 0.f};
-            mma_bf16(c, a, W->W1[(8 * j + g) * 8 + t], W->W1[(8 * j + g) * 8 + t + 4]);
-            const float bl = W->b1[8 * j + 2 * t], bh = W->b1[8 * j + 2 * t + 1];
-            const uint32_t lo = pack_bf16(fmaxf(c[0] + bl, 0.f), fmaxf(c[1] + bh, 0.f));
-            const uint32_t hi = pack_bf16(fmaxf(c[2] + bl, 0.f), fmaxf(c[3] + bh, 0.f));
+            const float2 bias = *reinterpret_cast<const float2*>(W->b1 + 8 * j + 2 * t);
+            float c[4] = {bias.x, bias.y, bias.x, bias.y};
+            const uint2 b = W1[(8 * j + g) * 4 + t];
+            mma_bf16(c, a, b.x, b.y);
+            const uint32_t lo = relu_pack_bf16(c[0], c[1]), hi = relu_pack_bf16(c[2], c[3]);
             if (j & 1) { h[j >> 1][2] = lo; h[j >> 1][3] = hi; }
             else { h[j >> 1][0] = lo; h[j >> 1][1] = hi; }
         }
         uint32_t h2[4][4];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-                mma_bf16(c, h[kk], W->W2[(8 * j + g) * 32 + 8 * kk + t], W->W2[(8 * j + g) * 32 + 8 * kk + t + 4]);
-            const float bl = W->b2[8 * j + 2 * t], bh = W->b2[8 * j + 2 * t + 1];
-            const uint32_t lo = pack_bf16(fmaxf(c[0] + bl, 0.f), fmaxf(c[1] + bh, 0.f));
-            const uint32_t hi = pack_bf16(fmaxf(c[2] + bl, 0.f), fmaxf(c[3] + bh, 0.f));
+            const float2 bias = *reinterpret_cast<const float2*>(W->b2 + 8 * j + 2 * t);
+            float c[4] = {bias.x, bias.y, bias.x, bias.y};
+            const uint4 b01 = W2[((8 * j + g) * 4 + t) * 2], b23 = W2[((8 * j + g) * 4 + t) * 2 + 1];
+            mma_bf16(c, h[0], b01.x, b01.y);
+            mma_bf16(c, h[1], b01.z, b01.w);
+            mma_bf16(c, h[2], b23.x, b23.y);
+            mma_bf16(c, h[3], b23.z, b23.w);
+            const uint32_t lo = relu_pack_bf16(c[0], c[1]), hi = relu_pack_bf16(c[2], c[3]);
             if (j & 1) { h2[j >> 1][2] = lo; h2[j >> 1][3] = hi; }
             else { h2[j >> 1][0] = lo; h2[j >> 1][1] = hi; }
         }
-        float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) mma_bf16(c, h2[kk], W->W3[g * 32 + 8 * kk + t], W->W3[g * 32 + 8 * kk + t + 4]);
+        const float2 b3 = *reinterpret_cast<const float2*>(W->b3 + 2 * t);
+        float c[4] = {b3.x, b3.y, b3.x, b3.y};
+        const uint4 b01 = W3[(g * 4 + t) * 2], b23 = W3[(g * 4 + t) * 2 + 1];
+        mma_bf16(c, h2[0], b01.x, b01.y);
+        mma_bf16(c, h2[1], b01.z, b01.w);
+        mma_bf16(c, h2[2], b23.x, b23.y);
+        mma_bf16(c, h2[3], b23.z, b23.w);
         float* Y = reinterpret_cast<float*>(X);
-        Y[g * 8 + 2 * t] = c[0] + W->b3[2 * t];
-        Y[g * 8 + 2 * t + 1] = c[1] + W->b3[2 * t + 1];
-        Y[(g + 8) * 8 + 2 * t] = c[2] + W->b3[2 * t];
-        Y[(g + 8) * 8 + 2 * t + 1] = c[3] + W->b3[2 * t + 1];
+        *reinterpret_cast<float2*>(Y + g * 8 + 2 * t) = make_float2(c[0], c[1]);
+        *reinterpret_cast<float2*>(Y + (g + 8) * 8 + 2 * t) = make_float2(c[2], c[3]);
     }
     __syncwarp();
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-        const float* y = reinterpret_cast<const float*>(wbuf + (lane * 2 + e) * 32);
+        const float4* y = reinterpret_cast<const float4*>(wbuf + (lane * 2 + e) * 32);
+        const float4 y0 = y[0], y1 = y[1];
+        const float yy[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
 #pragma unroll
-        for (int k = 0; k < 8; ++k) d[e][k] = fmaf(y[k], nrm[24 + k], nrm[16 + k]);
+        for (int k = 0; k < 8; ++k) d[e][k] = fmaf(yy[k], nrm[24 + k], nrm[16 + k]);
     }
     __syncwarp();  // the buffer is reused by the next row
 }

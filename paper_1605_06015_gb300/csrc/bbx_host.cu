@@ -20,12 +20,12 @@ StepKernel step_kernel_br(bool masked, bool aniso, int ty, bool planar, bool gen
 StepKernel step_kernel_zfk(bool masked, bool aniso, int ty, bool planar, bool general);
 StepKernel step_kernel_diffusion(bool masked, bool aniso, int ty, bool planar, bool general);
 StepKernel step_kernel_br_surrogate(bool masked, bool aniso, int ty);
-cudaError_t launch_ppm(const float* state, const uint8_t* mask, long long vol, int nx, int ny, int nz, int px,
-                       long long plane, const int layer[3], const float lo[3], const float hi[3], uint8_t* out,
-                       int num_sms, cudaStream_t s);
-cudaError_t launch_singz(const float* fa, const float* fb, float iso_a, float iso_b, const uint8_t* mask, int nx,
-                         int ny, int nz, int px, long long plane, float* xyz, int max_points, int* d_count,
-                         int num_sms, cudaStream_t s);
+cudaError_t launch_ppm(const float* s0, const float* s1, const int* cur, const uint8_t* mask, long long vol, int nx,
+                       int ny, int nz, int px, long long plane, const int layer[3], const float lo[3],
+                       const float hi[3], uint8_t* out, int num_sms, cudaStream_t s);
+cudaError_t launch_singz(const float* s0, const float* s1, const int* cur, long long off_a, long long off_b,
+                         float iso_a, float iso_b, const uint8_t* mask, int nx, int ny, int nz, int px,
+                         long long plane, float* xyz, int max_points, int* d_count, int num_sms, cudaStream_t s);
 }  // namespace bbx
 
 using namespace bbx;
@@ -354,16 +354,18 @@ __global__ void k_build_surrogate(const float* __restrict__ P, const float* __re
         __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
         return *reinterpret_cast<uint32_t*>(&v);
     };
-    if (i < 64 * 8) {  // W1 [64][16]: word i = row i/8, columns 2(i%8), 2(i%8)+1
-        const int n = i / 8, c = 2 * (i % 8);
+    // MMA-fragment order (see SurrogateData): word (lane t, k-step kk, half h)
+    // of a row holds input columns 16 kk + 2 t + 8 h and the next one
+    if (i < 64 * 8) {  // W1 [64][16], inputs 8..15 are zero padding
+        const int n = i / 8, t = (i % 8) / 2, h = i % 2, c = 2 * t + 8 * h;
         out->W1[i] = pair(c < 8 ? P[kOffW1 + n * 8 + c] : 0.0f, c + 1 < 8 ? P[kOffW1 + n * 8 + c + 1] : 0.0f);
     }
     if (i < 64 * 32) {
-        const int n = i / 32, c = 2 * (i % 32);
+        const int n = i / 32, t = (i % 32) / 8, kk = (i % 8) / 2, h = i % 2, c = 16 * kk + 2 * t + 8 * h;
         out->W2[i] = pair(P[kOffW2 + n * 64 + c], P[kOffW2 + n * 64 + c + 1]);
     }
     if (i < 8 * 32) {
-        const int n = i / 32, c = 2 * (i % 32);
+        const int n = i / 32, t = (i % 32) / 8, kk = (i % 8) / 2, h = i % 2, c = 16 * kk + 2 * t + 8 * h;
         out->W3[i] = pair(P[kOffW3 + n * 64 + c], P[kOffW3 + n * 64 + c + 1]);
     }
     if (i < 64) {
@@ -372,6 +374,7 @@ __global__ void k_build_surrogate(const float* __restrict__ P, const float* __re
     }
     if (i < 8) out->b3[i] = P[kOffB3 + i];
     if (i < kNormSize) out->norm[i] = norm[i];
+    if (i < 8) out->inv_sd_in[i] = 1.0f / norm[8 + i];
     if (i == 0) out->v_up = v_up;
 }
 
@@ -1363,11 +1366,8 @@ int bbx_ppm_frame(bbx_grid* g, const int* layers, const double* lo, const double
         if (ly[c] < -1 || ly[c] >= g->S) return BBX_ERR_ARG;
         if (ly[c] >= 0 && !(std::isfinite(l[c]) && std::isfinite(h[c]) && h[c] != l[c])) return BBX_ERR_ARG;
     }
-    TissueDyn d;
-    int rc = read_dyn(g, &d);
-    if (rc) return rc;
-    BBX_CUDA(launch_ppm(g->d_state[d.cur], g->d_mask, g->vol, g->nx, g->ny, g->nz, g->px, g->plane, ly, l, h,
-                        out_dev, g->num_sms, g->stream));
+    BBX_CUDA(launch_ppm(g->d_state[0], g->d_state[1], &g->d_dyn->cur, g->d_mask, g->vol, g->nx, g->ny, g->nz, g->px,
+                        g->plane, ly, l, h, out_dev, g->num_sms, g->stream));
     return BBX_OK;
 }
 
@@ -1381,13 +1381,9 @@ int bbx_phase_singularities(bbx_grid* g, int var_a, double iso_a, int var_b, dou
         cudaGetLastError();
         return BBX_ERR_NOMEM;
     }
-    TissueDyn d;
-    int rc = read_dyn(g, &d);
-    if (rc) return rc;
-    const float* st = g->d_state[d.cur];
-    BBX_CUDA(launch_singz(st + (size_t)var_a * g->vol, st + (size_t)var_b * g->vol, (float)iso_a, (float)iso_b,
-                          g->d_mask, g->nx, g->ny, g->nz, g->px, g->plane, xyz_dev, max_points, g->d_count,
-                          g->num_sms, g->stream));
+    BBX_CUDA(launch_singz(g->d_state[0], g->d_state[1], &g->d_dyn->cur, (long long)var_a * g->vol,
+                          (long long)var_b * g->vol, (float)iso_a, (float)iso_b, g->d_mask, g->nx, g->ny, g->nz, g->px,
+                          g->plane, xyz_dev, max_points, g->d_count, g->num_sms, g->stream));
     BBX_CUDA(cudaMemcpyAsync(n_found, g->d_count, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
     BBX_CUDA(cudaStreamSynchronize(g->stream));
     return check_sticky(g);

@@ -21,25 +21,59 @@ __device__ __forceinline__ uint8_t quantise(float v, float lo, float span) {
     return (uint8_t)floorf(__fadd_rn(__fmul_rn(t, 255.0f), 0.5f));
 }
 
-__global__ void k_ppm(const float* __restrict__ state, const uint8_t* __restrict__ mask, long long vol, int nx,
-                      int ny, int nz, int px, long long plane, int3 layer, float3 lo, float3 span,
-                      uint8_t* __restrict__ out) {
-    const long long n = (long long)nx * ny * nz;
+// One thread per group of 4 consecutive nodes of a row: float4 loads from the
+// padded rows (px is a multiple of 32) and three 32-bit stores of the 12
+// bytes, except in a row's last partial group.  The current buffer is picked
+// on the device from the grid's parity, so the call does not synchronise.
+__global__ void k_ppm(const float* __restrict__ s0, const float* __restrict__ s1, const int* __restrict__ cur,
+                      const uint8_t* __restrict__ mask, long long vol, int nx, int ny, int nz, int px,
+                      long long plane, int3 layer, float3 lo, float3 span, uint8_t* __restrict__ out) {
+    const float* state = *cur ? s1 : s0;
+    const int gx = (nx + 3) / 4;
+    const long long n = (long long)gx * ny * nz;
+    const int ly[3] = {layer.x, layer.y, layer.z};
+    const float l[3] = {lo.x, lo.y, lo.z}, sp[3] = {span.x, span.y, span.z};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const int x = int(i % nx);
-        const long long r = i / nx;
+        const int x = int(i % gx) * 4;
+        const long long r = i / gx;
         const int y = int(r % ny), z = int(r / ny);
         const long long gi = z * plane + (long long)y * px + x;
-        uint8_t c0 = 0, c1 = 0, c2 = 0;
-        if (!mask || (mask[gi] & kTissue)) {
-            if (layer.x >= 0) c0 = quantise(state[layer.x * vol + gi], lo.x, span.x);
-            if (layer.y >= 0) c1 = quantise(state[layer.y * vol + gi], lo.y, span.y);
-            if (layer.z >= 0) c2 = quantise(state[layer.z * vol + gi], lo.z, span.z);
+        const long long oi = ((long long)z * ny + y) * nx + x;  // first node of the group in the output
+        uint8_t c[4][3] = {};
+        bool tis[4] = {true, true, true, true};
+        if (mask) {
+            const uchar4 m = *reinterpret_cast<const uchar4*>(mask + gi);
+            tis[0] = m.x & kTissue; tis[1] = m.y & kTissue; tis[2] = m.z & kTissue; tis[3] = m.w & kTissue;
         }
-        out[3 * i] = c0;
-        out[3 * i + 1] = c1;
-        out[3 * i + 2] = c2;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            if (ly[ch] < 0) continue;
+            const float4 v = *reinterpret_cast<const float4*>(state + ly[ch] * vol + gi);
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) c[k][ch] = tis[k] ? quantise(vv[k], l[ch], sp[ch]) : 0;
+        }
+        if (x + 4 <= nx && (oi & 3) == 0) {
+            uint32_t w[3];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                w[b] = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int byte = 4 * b + k;  // byte of the 12-byte group
+                    w[b] |= (uint32_t)c[byte / 3][byte % 3] << (8 * k);
+                }
+            }
+            uint32_t* o = reinterpret_cast<uint32_t*>(out + 3 * oi);
+            o[0] = w[0];
+            o[1] = w[1];
+            o[2] = w[2];
+        } else {
+            for (int k = 0; k < 4 && x + k < nx; ++k)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) out[3 * (oi + k) + ch] = c[k][ch];
+        }
     }
 }
 
@@ -61,9 +95,13 @@ __device__ __forceinline__ int cell_crossings(const float g[4], float2 p[2]) {
     return n;
 }
 
-__global__ void k_singz(const float* __restrict__ fa, const float* __restrict__ fb, float iso_a, float iso_b,
-                        const uint8_t* __restrict__ mask, int nx, int ny, int nz, int px, long long plane,
-                        float* __restrict__ xyz, int max_points, int* __restrict__ count) {
+__global__ void k_singz(const float* __restrict__ s0, const float* __restrict__ s1, const int* __restrict__ cur,
+                        long long off_a, long long off_b, float iso_a, float iso_b, const uint8_t* __restrict__ mask,
+                        int nx, int ny, int nz, int px, long long plane, float* __restrict__ xyz, int max_points,
+                        int* __restrict__ count) {
+    const float* st = *cur ? s1 : s0;  // the current buffer, from the grid's parity
+    const float* fa = st + off_a;
+    const float* fb = st + off_b;
     const long long cx = nx - 1, cy = ny - 1;
     const long long n = cx * cy * nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -113,26 +151,26 @@ int blocks_for(long long n, int num_sms) {
 
 }  // namespace
 
-cudaError_t launch_ppm(const float* state, const uint8_t* mask, long long vol, int nx, int ny, int nz, int px,
-                       long long plane, const int layer[3], const float lo[3], const float hi[3], uint8_t* out,
-                       int num_sms, cudaStream_t s) {
-    const long long n = (long long)nx * ny * nz;
-    k_ppm<<<blocks_for(n, num_sms), 256, 0, s>>>(state, mask, vol, nx, ny, nz, px, plane,
+cudaError_t launch_ppm(const float* s0, const float* s1, const int* cur, const uint8_t* mask, long long vol, int nx,
+                       int ny, int nz, int px, long long plane, const int layer[3], const float lo[3],
+                       const float hi[3], uint8_t* out, int num_sms, cudaStream_t s) {
+    const long long n = (long long)((nx + 3) / 4) * ny * nz;
+    k_ppm<<<blocks_for(n, num_sms), 256, 0, s>>>(s0, s1, cur, mask, vol, nx, ny, nz, px, plane,
                                                  make_int3(layer[0], layer[1], layer[2]),
                                                  make_float3(lo[0], lo[1], lo[2]),
                                                  make_float3(hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]), out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_singz(const float* fa, const float* fb, float iso_a, float iso_b, const uint8_t* mask, int nx,
-                         int ny, int nz, int px, long long plane, float* xyz, int max_points, int* d_count,
-                         int num_sms, cudaStream_t s) {
+cudaError_t launch_singz(const float* s0, const float* s1, const int* cur, long long off_a, long long off_b,
+                         float iso_a, float iso_b, const uint8_t* mask, int nx, int ny, int nz, int px,
+                         long long plane, float* xyz, int max_points, int* d_count, int num_sms, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     const long long n = (long long)(nx - 1) * (ny - 1) * nz;
     if (n <= 0) return cudaSuccess;
-    k_singz<<<blocks_for(n, num_sms), 256, 0, s>>>(fa, fb, iso_a, iso_b, mask, nx, ny, nz, px, plane, xyz, max_points,
-                                                   d_count);
+    k_singz<<<blocks_for(n, num_sms), 256, 0, s>>>(s0, s1, cur, off_a, off_b, iso_a, iso_b, mask, nx, ny, nz, px,
+                                                   plane, xyz, max_points, d_count);
     return cudaGetLastError();
 }
 
