@@ -23,6 +23,8 @@ StepKernel step_kernel_br_surrogate(bool masked, bool aniso, int ty);
 cudaError_t launch_ppm(const float* s0, const float* s1, const int* cur, const uint8_t* mask, long long vol, int nx,
                        int ny, int nz, int px, long long plane, const int layer[3], const float lo[3],
                        const float hi[3], uint8_t* out, int num_sms, cudaStream_t s);
+cudaError_t resident_sheet_steps(int model, const TissueArgs* d_t, int nx, int ny, int n_steps, int* d_err,
+                                 cudaStream_t s, bool check_only, bool* ok);
 cudaError_t launch_singz(const float* s0, const float* s1, const int* cur, long long off_a, long long off_b,
                          float iso_a, float iso_b, const uint8_t* mask, int nx, int ny, int nz, int px,
                          long long plane, float* xyz, int max_points, int* d_count, int num_sms, cudaStream_t s);
@@ -634,6 +636,7 @@ struct bbx_grid {
     bool surr_on = false;
     int split = 0;  // time-stepping scheme (bbx_set_scheme)
     int rk4 = 0;    // kinetics solver (bbx_set_solver)
+    int resident = 0;  // multi-step resident kernel requested (bbx_set_resident)
 
     double* d_partials = nullptr;  // bbx_total scratch
     unsigned int* d_ticket = nullptr;
@@ -1237,6 +1240,31 @@ int bbx_set_threshold(bbx_grid* g, double theta) {
     return g->model ? refresh_targs(g) : BBX_OK;
 }
 
+// The resident multi-step kernel serves small unmasked isotropic sheets of the
+// models given by a right-hand side, with the default scheme and solver.
+static bool resident_eligible(const bbx_grid* g) {
+    return g->nz == 1 && !g->d_mask && !g->aniso && !g->split && !g->rk4 && !g->surr_on && !g->poison &&
+           (g->model == BBX_FHN || g->model == BBX_BARKLEY || g->model == BBX_ZFK || g->model == BBX_DIFFUSION);
+}
+
+int bbx_set_resident(bbx_grid* g, int on) {
+    if (!g) return BBX_ERR_ARG;
+    if (!on) {
+        g->resident = 0;
+        return BBX_OK;
+    }
+    if (!g->model) return BBX_ERR_STATE;
+    if (!resident_eligible(g)) return BBX_ERR_UNSUPPORTED;
+    bool ok = false;
+    if (resident_sheet_steps(g->model, nullptr, g->nx, g->ny, 0, nullptr, g->stream, true, &ok) != cudaSuccess) {
+        cudaGetLastError();
+        return BBX_ERR_CUDA;
+    }
+    if (!ok) return BBX_ERR_UNSUPPORTED;
+    g->resident = 1;
+    return BBX_OK;
+}
+
 // The scheme and solver select the kernel variant (the general one has no
 // 28-row tiles: such a grid moves to 14 rows).
 static int apply_kinetics_setting(bbx_grid* g) {
@@ -1297,6 +1325,21 @@ int bbx_step(bbx_grid* g, double dt, int n_steps) {
         if ((rc = write_dyn(g, d))) return rc;
         g->stepped = true;
         return BBX_OK;
+    }
+    if (g->resident && n_steps >= 2 && resident_eligible(g)) {
+        int done = 0;
+        while (done < n_steps) {
+            const int chunk = std::min(n_steps - done, 1 << 16);
+            bool ok = false;
+            const cudaError_t e = resident_sheet_steps(g->model, g->d_t, g->nx, g->ny, chunk, g->d_err, g->stream,
+                                                       false, &ok);
+            if (e != cudaSuccess) return fail_cuda(e);
+            if (!ok) break;  // not launchable after all: the tiled kernel takes the rest
+            done += chunk;
+        }
+        if (done > 0) g->stepped = true;
+        n_steps -= done;
+        if (n_steps == 0) return BBX_OK;
     }
     const LaunchArgs L = launch_args(g->lp, g->d_t, g->d_err, g->poison, &g->h_t);
     for (int s = 0; s < n_steps; ++s) {
