@@ -882,13 +882,23 @@ int check_sticky_ptr(cudaStream_t s, int* d_err) {
 
 int check_sticky(bbx_grid* g) { return check_sticky_ptr(g->stream, g->d_err); }
 
+// Dense host field <-> pitched device field; one linear copy when the rows
+// are not padded (nx a multiple of 32).
 int copy_in(bbx_grid* g, void* dst, const void* src, size_t elem) {
+    if (g->px == g->nx) {
+        BBX_CUDA(cudaMemcpyAsync(dst, src, (size_t)g->ncell * elem, cudaMemcpyHostToDevice, g->stream));
+        return BBX_OK;
+    }
     BBX_CUDA(cudaMemcpy2DAsync(dst, (size_t)g->px * elem, src, (size_t)g->nx * elem, (size_t)g->nx * elem,
                                (size_t)g->ny * g->nz, cudaMemcpyHostToDevice, g->stream));
     return BBX_OK;
 }
 
 int copy_out(bbx_grid* g, void* dst, const void* src, size_t elem) {
+    if (g->px == g->nx) {
+        BBX_CUDA(cudaMemcpyAsync(dst, src, (size_t)g->ncell * elem, cudaMemcpyDeviceToHost, g->stream));
+        return BBX_OK;
+    }
     BBX_CUDA(cudaMemcpy2DAsync(dst, (size_t)g->nx * elem, src, (size_t)g->px * elem, (size_t)g->nx * elem,
                                (size_t)g->ny * g->nz, cudaMemcpyDeviceToHost, g->stream));
     return BBX_OK;
