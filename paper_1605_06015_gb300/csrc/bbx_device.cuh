@@ -42,7 +42,8 @@ struct TissueDyn {
     double total;   // tissue sum of V after the most recent step
     long long n;    // steps taken
     int cur;        // buffer holding the current state (0 or 1)
-    int pad;
+    int total_pending;  // 1: total is still to be summed from the per-piece
+                        // partials of the grid's last single-grid launch
 };
 
 // Host-written description of one grid for the step kernel (in device memory,
@@ -241,11 +242,31 @@ __device__ __forceinline__ void grid_total_finalize(double block_partial, double
     }
 }
 
-// End of a step, in the last CTA to finish: per-grid totals from the
-// per-piece partials (fixed order), then t += dt, n += 1 and the buffer
-// parity flip of every grid of the launch.
-__device__ __forceinline__ void step_finalize(const LaunchArgs& L, double* scratch32, const TissueDyn* dyn0) {
+// Single-grid launch, producer lane of every CTA, once its t, n and parity
+// are read: the CTA that arrives last (all others have read them too)
+// advances them, marks the total as pending and resets the ticket.
+__device__ __forceinline__ void start_ticket(const LaunchArgs& L, const TissueDyn& d0) {
+    __threadfence();
+    const unsigned int t = atomicAdd(L.ticket, 1u);
+    if (t == gridDim.x - 1) {
+        TissueDyn* d = L.t0.dyn;
+        d->t = d0.t + L.t0.dt_d;
+        d->n = d0.n + 1;
+        d->cur = d0.cur ^ 1;
+        d->total_pending = 1;
+        *L.ticket = 0u;
+    }
+}
+
+// End of a launch over several grids, in the last CTA to finish: per-grid
+// totals from the per-piece partials (fixed order), then t += dt, n += 1 and
+// the buffer parity flip of every grid of the launch.  A single-grid launch
+// has no end step: its producers advance t, n and the parity as soon as
+// every CTA has read them (start_ticket), and the grid's total is summed
+// from the partials when it is asked for.
+__device__ __forceinline__ void step_finalize(const LaunchArgs& L, double* scratch32) {
     __shared__ bool last;
+    if (L.single) return;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -268,6 +289,7 @@ __device__ __forceinline__ void step_finalize(const LaunchArgs& L, double* scrat
         d->t = d->t + T->dt_d;
         d->n = d->n + 1;
         d->cur = d->cur ^ 1;
+        d->total_pending = 0;
     };
     // direct: slots k0..k1 of partials; otherwise through tissue_pieces
     auto strided_sum = [&](int k0, int k1, int first, int stride, bool direct) {
@@ -284,23 +306,7 @@ __device__ __forceinline__ void step_finalize(const LaunchArgs& L, double* scrat
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         return s;
     };
-    if (L.single) {
-        // every slot (unused ones hold 0) in index order; t, n and the buffer
-        // parity as the producer warps read them at the start of the launch
-        const double s = strided_sum(0, L.n_slots, threadIdx.x, blockDim.x, true);
-        if (lane == 0) scratch32[warp] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < nwarps; ++w) t += scratch32[w];
-            TissueDyn* d = L.t0.dyn;
-            if (!isfinite(t)) atomicOr(L.err, ERRBIT_NAN);
-            d->total = t;
-            d->t = dyn0->t + L.t0.dt_d;
-            d->n = dyn0->n + 1;
-            d->cur = dyn0->cur ^ 1;
-        }
-    } else if (L.n_tissues == 1) {
+    if (L.n_tissues == 1) {
         const double s = strided_sum(__ldcg(&L.tissue_off[0]), __ldcg(&L.tissue_off[1]), threadIdx.x, blockDim.x,
                                      false);
         if (lane == 0) scratch32[warp] = s;
@@ -867,7 +873,6 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
     uint64_t* empty = full + NS;
     PieceSlot* ring = reinterpret_cast<PieceSlot*>(empty + NS);
     __shared__ double red_scratch[32];
-    __shared__ TissueDyn dyn0;  // single-grid launch: the grid's t, n, parity at launch
     __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x;
@@ -894,13 +899,13 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
             // the loads the first plane waits for, issued together: the first
             // piece (its slot always exists) and, for one grid, its t, n, parity
             int4 pc_next = L.pieces[piece_begin];
-            TissueDyn d0;
+            TissueDyn d0 = {};
+            bool ticketed = !L.single;  // a single-grid launch takes one start ticket per CTA
             if (L.single) {
                 const TissueDyn* D = L.t0.dyn;
                 d0.t = D->t;
                 d0.n = D->n;
                 d0.cur = D->cur;
-                dyn0 = d0;
             }
             for (int pi = piece_begin; pi < piece_end && !stop; ++pi, ++lp) {
                 const int4 pc = pc_next;
@@ -912,6 +917,11 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                 const int nload = PLANAR ? pc.w - pc.z : pc.w - pc.z + 2;
                 for (int off = 0; off < nload; ++off) {
                     const int slot = issued % NS;
+                    if (!ticketed && issued == NS) {
+                        // the ring is full: the ticket's round trip overlaps the copies
+                        start_ticket(L, d0);
+                        ticketed = true;
+                    }
                     if (L.poison_first_load && blockIdx.x == 0 && issued == 0) {
                         // fault injection: wait for an empty-slot phase that no
                         // consumer completes; the bounded wait runs out
@@ -963,6 +973,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                     ++issued;
                 }
             }
+            if (!ticketed) start_ticket(L, d0);  // every CTA takes it, also on a short or aborted run
             if (stop) abort_flag = 1;
         }
         __syncwarp();
@@ -1281,6 +1292,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                 double s = 0.0;
                 for (int w = 0; w < NCW; ++w) s += red_scratch[w];
                 L.partials[pi] = s;
+                if (!isfinite(s)) atomicOr(L.err, ERRBIT_NAN);
             }
             consumers_sync(NCT);
             vsum.hi = vsum.lo = 0.0f;
@@ -1296,7 +1308,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
         for (int j = issued > NS ? issued - NS : 0; j < issued; ++j)
             (void)mbar_wait_bounded(&full[j % NS], (j / NS) & 1, L.wait_limit);
     }
-    step_finalize(L, red_scratch, &dyn0);
+    step_finalize(L, red_scratch);
 }
 
 // host-visible description of one compiled step kernel

@@ -307,6 +307,22 @@ __global__ void k_total(const float* __restrict__ u, const uint8_t* __restrict__
     grid_total_finalize(bs, partials, ticket, out, err, false, scratch);
 }
 
+// The total of a grid's last single-grid step, summed from the step's
+// per-piece partials in slot order (unused slots hold 0) when it is asked
+// for; nothing happens if no total is pending.  One CTA.
+__global__ void k_finish_total(const double* __restrict__ partials, int n_slots, TissueDyn* dyn, int* err) {
+    __shared__ double scratch[32];
+    if (!dyn->total_pending) return;  // uniform: every thread reads the same flag
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n_slots; k += blockDim.x) s += partials[k];
+    const double total = block_sum_double(s, scratch);
+    if (threadIdx.x == 0) {
+        if (!isfinite(total)) atomicOr(err, ERRBIT_NAN);
+        dyn->total = total;
+        dyn->total_pending = 0;
+    }
+}
+
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
     z += 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -819,11 +835,16 @@ int encode_targs(const bbx_grid* g, int ty, TissueArgs* t) {
     return BBX_OK;
 }
 
+int finish_total(bbx_grid* g);
+
 // Bring h_t, d_t and the single-grid launch plan in line with the settings.
 int prepare(bbx_grid* g) {
     g->ready = false;
     ++g->version;
     if (!g->model || !g->d_state[0]) return BBX_ERR_STATE;
+    int rc0 = finish_total(g);  // the plan's partials are about to be replaced
+    if (rc0) return rc0;
+    BBX_CUDA(cudaStreamSynchronize(g->stream));
     StepKernel k;
     int ctas = 0;
     int rc = select_kernel(g->model, g->d_mask != nullptr, g->aniso, g->ty, g->device, g->num_sms, &k, &ctas,
@@ -868,6 +889,16 @@ int read_dyn(bbx_grid* g, TissueDyn* d) {
 int write_dyn(bbx_grid* g, const TissueDyn& d) {
     BBX_CUDA(cudaMemcpyAsync(g->d_dyn, &d, sizeof(TissueDyn), cudaMemcpyHostToDevice, g->stream));
     BBX_CUDA(cudaStreamSynchronize(g->stream));
+    return BBX_OK;
+}
+
+// Enqueue the sum of a pending single-grid total from the plan's partials
+// (nothing happens on the device when none is pending).  Called before
+// anything that reads the total or overwrites the partials.
+int finish_total(bbx_grid* g) {
+    if (!g->lp.d_partials || g->lp.n_slots <= 0 || !g->d_dyn) return BBX_OK;
+    k_finish_total<<<1, 256, 0, g->stream>>>(g->lp.d_partials, g->lp.n_slots, g->d_dyn, g->d_err);
+    BBX_CUDA(cudaGetLastError());
     return BBX_OK;
 }
 
@@ -1332,6 +1363,7 @@ int bbx_step(bbx_grid* g, double dt, int n_steps) {
             d.n += 1;
         }
         d.total = 0.0;
+        d.total_pending = 0;
         if ((rc = write_dyn(g, d))) return rc;
         g->stepped = true;
         return BBX_OK;
@@ -1445,9 +1477,10 @@ int bbx_phase_singularities(bbx_grid* g, int var_a, double iso_a, int var_b, dou
 int bbx_step_total(bbx_grid* g, double* out) {
     if (!g || !out) return BBX_ERR_ARG;
     if (!g->stepped) return BBX_ERR_STATE;
-    TissueDyn d;
-    int rc = read_dyn(g, &d);
+    int rc = finish_total(g);
     if (rc) return rc;
+    TissueDyn d;
+    if ((rc = read_dyn(g, &d))) return rc;
     *out = d.total;
     return check_sticky(g);
 }
@@ -1554,7 +1587,7 @@ int bbx_autotune(bbx_grid* g, double dt, double* best_ms) {
         return BBX_ERR_NOMEM;
     }
     TissueDyn d0;
-    if ((rc = read_dyn(g, &d0))) {
+    if ((rc = finish_total(g)) || (rc = read_dyn(g, &d0))) {
         cudaFree(save);
         cudaFree(save_act);
         return rc;

@@ -145,6 +145,7 @@ __global__ void __cluster_dims__(kResCtas, 1, 1) __launch_bounds__(kResThreads, 
         for (int k = 0; k < kResCtas; ++k) tot += cl_part[k];
         if (!isfinite(tot)) atomicOr(err, ERRBIT_NAN);
         D->total = tot;
+        D->total_pending = 0;
         D->t = t;
         D->n = n;
         D->cur = cur1;

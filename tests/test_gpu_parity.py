@@ -264,6 +264,57 @@ def test_totals_fused_and_standalone(bbx):
     assert G.step_total() == pytest.approx(ref0, rel=1e-12)
 
 
+
+def test_step_total_across_retiling_batches_and_autotune(bbx):
+    # A single-grid step leaves its total as per-piece partials, summed when
+    # asked for: it must survive a new tile shape (which replaces the
+    # partials), follow batch steps of the same grid, and be restored by the
+    # autotuner together with the state.
+    w = wl.barkley_slab(70, 40, 10)
+    rest = oracle.rest_state(w.model, w.params)
+    st0 = w.initial_state(rest).astype(np.float32)
+    og = oracle.Grid(w.nx, w.ny, w.nz, w.h, w.mask, w.fibres, w.D_par, w.D_perp)
+    G = _gpu_grid(bbx, w, 14, 4)
+    G.write_all(st0)
+
+    def sum_now():
+        return og.total(G.read_state(0).astype(np.float64))
+
+    G.step(w.dt, 3)
+    t3 = sum_now()
+    G.set_tiling(7, 8)
+    assert G.step_total() == pytest.approx(t3, rel=1e-12)
+    G.step(w.dt, 2)
+    assert G.step_total() == pytest.approx(sum_now(), rel=1e-12)
+    H = _gpu_grid(bbx, wl.fhn_sheet(50, 30))
+    H.set_timestep(0.01)
+    B = bbx.Batch([G, H])
+    B.step(2)
+    B.sync()
+    assert G.step_total() == pytest.approx(sum_now(), rel=1e-12)
+    G.step(w.dt, 1)
+    t_before = G.step_total()
+    assert t_before == pytest.approx(sum_now(), rel=1e-12)
+    G.step(w.dt, 1)
+    t_now = sum_now()
+    G.autotune(w.dt)
+    assert G.step_total() == pytest.approx(t_now, rel=1e-12)
+    assert sum_now() == t_now
+
+
+def test_non_finite_state_is_reported(bbx):
+    w = wl.fhn_sheet(64, 32)
+    G = _gpu_grid(bbx, w)
+    st = np.zeros((2, 1, 32, 64), np.float32)
+    st[0, 0, 10, 20] = 3e38  # the cubic overflows: inf, then nan
+    G.write_all(st)
+    G.step(w.dt, 2)
+    with pytest.raises(bbx.BbxError) as e:
+        G.step_total()
+    assert e.value.code == bbx.BBX_ERR_NAN
+    G.clear_device_error()
+
+
 def test_conservation_uniform_fibres_masked_diffusion(bbx):
     mask, _ = wl.random_geometry(70, 30, 12, 9, tissue_frac=0.8, aniso=False)
     fib = np.zeros((12, 30, 70, 3), np.float32)
