@@ -10,6 +10,8 @@ Parity status per function (see ``bbx_oracle.c`` for the passages):
   total, active bricks: pinned by the tests in ``tests/test_oracle_*.py``.
   output.py (byte quantisation, colour map, phase singularities): pinned by
   tests/test_oracle_output.py.
+  Matrix Rush-Larsen (transition matrix of the Markov form of the BR sodium
+  activation, the BR_MRL model): pinned by tests/test_oracle_markov.py.
   Beeler-Reuter constants: PARITY UNPINNED (the paper does not print them;
   transcribed from Beeler & Reuter 1977, checked only qualitatively).
 """
@@ -26,8 +28,9 @@ _SRC = os.path.join(_HERE, "bbx_oracle.c")
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
 
-FHN, BARKLEY, BR, ZFK, DIFFUSION = 1, 2, 3, 4, 5
-NVARS = {FHN: 2, BARKLEY: 2, BR: 8, ZFK: 1, DIFFUSION: 1}
+FHN, BARKLEY, BR, ZFK, DIFFUSION, BR_MRL = 1, 2, 3, 4, 5, 6
+NVARS = {FHN: 2, BARKLEY: 2, BR: 8, ZFK: 1, DIFFUSION: 1, BR_MRL: 11}
+MAXS = 11
 INT32_MAX = np.iinfo(np.int32).max
 
 
@@ -78,6 +81,8 @@ def lib():
         L.orc_cell_update_rk4.restype = I
         L.orc_br_rates.argtypes = [D, P, P]
         L.orc_br_currents.argtypes = [P, P, P]
+        L.orc_mrl_generator.argtypes = [D, P]
+        L.orc_mrl_transition.argtypes = [D, D, P]
         L.orc_run.argtypes = [P, P, P, D, I, P, P, P]
         L.orc_run.restype = I
         L.orc_step_cells.argtypes = [P, P, P, D, D, P, I, P]
@@ -151,7 +156,7 @@ class Grid:
 
 def rest_state(model, par=None):
     par = np.zeros(0) if par is None else np.ascontiguousarray(par, dtype=np.float64)
-    y = np.zeros(8)
+    y = np.zeros(MAXS)
     rc = lib().orc_rest_state(model, _ptr(par) if par.size else None, par.size, y.ctypes.data)
     assert rc == 0
     return y[:NVARS[model]].copy()
@@ -160,7 +165,7 @@ def rest_state(model, par=None):
 def cell_update(model, y, L=0.0, Istim=0.0, dt=0.01, par=None):
     par = np.zeros(0) if par is None else np.ascontiguousarray(par, dtype=np.float64)
     y = np.ascontiguousarray(y, dtype=np.float64)
-    yn = np.zeros(8)
+    yn = np.zeros(MAXS)
     lib().orc_cell_update(model, _ptr(par) if par.size else None, par.size, y.ctypes.data,
                           float(L), float(Istim), float(dt), yn.ctypes.data)
     return yn[:NVARS[model]].copy()
@@ -170,7 +175,7 @@ def cell_update_rk4(model, y, L=0.0, Istim=0.0, dt=0.01, par=None):
     """One classical RK4 step of a single node (rhs models)."""
     par = np.zeros(0) if par is None else np.ascontiguousarray(par, dtype=np.float64)
     y = np.ascontiguousarray(y, dtype=np.float64)
-    yn = np.zeros(8)
+    yn = np.zeros(MAXS)
     rc = lib().orc_cell_update_rk4(model, _ptr(par) if par.size else None, par.size, y.ctypes.data,
                                    float(L), float(Istim), float(dt), yn.ctypes.data)
     if rc != 0:
@@ -182,6 +187,21 @@ def br_rates(V):
     a = np.zeros(6); b = np.zeros(6)
     lib().orc_br_rates(float(V), a.ctypes.data, b.ctypes.data)
     return a, b
+
+
+def mrl_generator(V):
+    """Transition-rate matrix A(V) of the Markov form of the BR sodium
+    activation (4 x 4, A[i, j] = rate from state j into state i)."""
+    A = np.zeros(16)
+    lib().orc_mrl_generator(float(V), A.ctypes.data)
+    return A.reshape(4, 4)
+
+
+def mrl_transition(V, dt):
+    """T = exp(dt A(V)), the matrix Rush-Larsen step of the chain."""
+    T = np.zeros(16)
+    lib().orc_mrl_transition(float(V), float(dt), T.ctypes.data)
+    return T.reshape(4, 4)
 
 
 def br_currents(y, par=None):
@@ -207,7 +227,7 @@ class Sim:
         self.S = NVARS[model]
         self.par = np.zeros(0) if par is None else np.ascontiguousarray(par, dtype=np.float64)
         if theta is None:
-            theta = {FHN: 0.0, BARKLEY: 0.5, BR: -40.0, ZFK: 0.5, DIFFUSION: 0.5}[model]
+            theta = {FHN: 0.0, BARKLEY: 0.5, BR: -40.0, ZFK: 0.5, DIFFUSION: 0.5, BR_MRL: -40.0}[model]
         self.theta = float(theta)
         if state is None:
             rs = rest_state(model, self.par if self.par.size else None)

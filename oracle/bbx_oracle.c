@@ -27,6 +27,16 @@
  *                                       constants are Beeler & Reuter (1977).
  *                                       PARITY UNPINNED for the BR constants:
  *                                       the paper does not print them.
+ *   - matrix Rush-Larsen                Eq. (markov-generic) and the scheme
+ *                                       u_{n+1} = T(V_n) u_n, T = exp(dt A(V_n))
+ *                                       that follows it (section "Exponential
+ *                                       solvers"), on the Markov form of the
+ *                                       BR sodium activation m^3: a chain of
+ *                                       the number k = 0..3 of activated
+ *                                       subunits (the paper prints no Markov
+ *                                       model).  T is the matrix exponential
+ *                                       by its power series (scaling and
+ *                                       squaring), not by diagonalisation.
  *   - activation time                   k_poincare device (Appendix, sample.bbs)
  *   - total over tissue                 reduce device (Appendix, sample.bbs)
  *   - idle-partition elision            section "Domain partitioning"
@@ -55,7 +65,8 @@
 #define ORC_ERR_FIBRE (-3)
 #define ORC_ERR_NOMEM (-8)
 
-enum { ORC_FHN = 1, ORC_BARKLEY = 2, ORC_BR = 3, ORC_ZFK = 4, ORC_DIFFUSION = 5 };
+enum { ORC_FHN = 1, ORC_BARKLEY = 2, ORC_BR = 3, ORC_ZFK = 4, ORC_DIFFUSION = 5, ORC_BR_MRL = 6 };
+#define ORC_MAXS 11
 
 typedef struct {
     int nx, ny, nz;
@@ -225,6 +236,7 @@ int orc_nvars(int model) {
         case ORC_ZFK: return 1;
         case ORC_BR: return 8;
         case ORC_DIFFUSION: return 1;
+        case ORC_BR_MRL: return 11;
     }
     return 0;
 }
@@ -237,7 +249,8 @@ static void model_params(int model, const double* par, int npar, double* p) {
         case ORC_FHN: d[0] = 0.3; d[1] = 0.71; d[2] = 0.5; n = 3; break;   /* eps, beta, gamma */
         case ORC_BARKLEY: d[0] = 0.75; d[1] = 0.02; d[2] = 0.02; n = 3; break; /* a, b, eps */
         case ORC_ZFK: d[0] = 0.13; n = 1; break;                            /* alpha */
-        case ORC_BR: d[0] = 4.0; d[1] = 0.003; d[2] = 50.0; d[3] = 0.09; n = 4; break;
+        case ORC_BR:
+        case ORC_BR_MRL: d[0] = 4.0; d[1] = 0.003; d[2] = 50.0; d[3] = 0.09; n = 4; break;
             /* gNa, gNaC, ENa, gs */
     }
     for (int i = 0; i < 8; i++) p[i] = (i < npar && i < n && par) ? par[i] : d[i];
@@ -284,13 +297,13 @@ void orc_br_rates(double V, double* alpha6, double* beta6) {
     }
 }
 
-/* BR (1977) membrane currents in uA/cm^2 and dCa/dt.  out[0] = I_ion,
+/* BR (1977) membrane currents in uA/cm^2 and dCa/dt, with the open
+ * probability m3 of the sodium activation given.  out[0] = I_ion,
  * out[1] = I_s, out[2] = dCa/dt. */
-void orc_br_currents(const double* p, const double* y, double* out) {
-    double V = y[BR_V], Ca = y[BR_CA];
+static void br_currents_m3(const double* p, double V, double Ca, double x1, double m3, double hh, double j,
+                           double d, double f, double* out) {
     double gNa = p[0], gNaC = p[1], ENa = p[2], gs = p[3];
-    double m = y[BR_M], hh = y[BR_H], j = y[BR_J], d = y[BR_D], f = y[BR_F], x1 = y[BR_X1];
-    double INa = (gNa * m * m * m * hh * j + gNaC) * (V - ENa);
+    double INa = (gNa * m3 * hh * j + gNaC) * (V - ENa);
     double Es = -82.3 - 13.0287 * log(Ca);
     double Is = gs * d * f * (V - Es);
     double Ix1 = x1 * 0.8 * (exp(0.04 * (V + 77.0)) - 1.0) / exp(0.04 * (V + 35.0));
@@ -302,6 +315,72 @@ void orc_br_currents(const double* p, const double* y, double* out) {
     out[0] = INa + Is + Ix1 + IK1;
     out[1] = Is;
     out[2] = -1e-7 * Is + 0.07 * (1e-7 - Ca);
+}
+
+void orc_br_currents(const double* p, const double* y, double* out) {
+    double m = y[BR_M];
+    br_currents_m3(p, y[BR_V], y[BR_CA], y[BR_X1], m * m * m, y[BR_H], y[BR_J], y[BR_D], y[BR_F], out);
+}
+
+/* ---- Markov form of the BR sodium activation (matrix Rush-Larsen) ------- */
+
+/* State order of the Markov variant: V, Ca, x1, h, j, d, f, then P0..P3, the
+ * probabilities that k = 0..3 of the three activation subunits are open
+ * (P3 takes the place of m^3). */
+enum { MR_V = 0, MR_CA, MR_X1, MR_H, MR_J, MR_D, MR_F, MR_P0 };
+
+/* Transition-rate matrix of Eq. (markov-generic), du/dt = A u, for the
+ * chain: k -> k+1 at (3-k) alpha_m, k -> k-1 at k beta_m.  Row-major,
+ * A[i][j] = rate from state j into state i (columns sum to zero). */
+void orc_mrl_generator(double V, double* A16) {
+    double al[6], be[6];
+    orc_br_rates(V, al, be);
+    const double a = al[1], b = be[1]; /* alpha_m, beta_m */
+    for (int i = 0; i < 16; i++) A16[i] = 0.0;
+    for (int k = 0; k < 4; k++) {
+        double out = 0.0;
+        if (k < 3) { A16[(k + 1) * 4 + k] = (3 - k) * a; out += (3 - k) * a; }
+        if (k > 0) { A16[(k - 1) * 4 + k] = k * b; out += k * b; }
+        A16[k * 4 + k] = -out;
+    }
+}
+
+static void mat4_mul(const double* X, const double* Y, double* Z) {
+    double t[16];
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++) {
+            double s = 0.0;
+            for (int k = 0; k < 4; k++) s += X[i * 4 + k] * Y[k * 4 + j];
+            t[i * 4 + j] = s;
+        }
+    memcpy(Z, t, sizeof(t));
+}
+
+/* T = exp(dt A(V)) of the scheme u_{n+1} = T(V_n) u_n: the power series
+ * sum_k M^k / k! of M = dt A / 2^s (s chosen so that the largest absolute
+ * row sum of M is at most 1/2; 30 terms), squared s times. */
+void orc_mrl_transition(double V, double dt, double* T16) {
+    double M[16];
+    orc_mrl_generator(V, M);
+    double nrm = 0.0;
+    for (int i = 0; i < 4; i++) {
+        double r = 0.0;
+        for (int j = 0; j < 4; j++) r += fabs(M[i * 4 + j]) * dt;
+        if (r > nrm) nrm = r;
+    }
+    int s = 0;
+    while (nrm > 0.5) { nrm *= 0.5; s++; }
+    const double sc = dt / ldexp(1.0, s);
+    for (int i = 0; i < 16; i++) M[i] *= sc;
+    double term[16], E[16];
+    for (int i = 0; i < 16; i++) term[i] = E[i] = (i % 5 == 0) ? 1.0 : 0.0;
+    for (int k = 1; k <= 30; k++) {
+        mat4_mul(term, M, term);
+        for (int i = 0; i < 16; i++) term[i] /= k;
+        for (int i = 0; i < 16; i++) E[i] += term[i];
+    }
+    for (int q = 0; q < s; q++) mat4_mul(E, E, E);
+    memcpy(T16, E, sizeof(E));
 }
 
 /* One unsplit step of one node: Eq. (Euler) for the non-gate variables with
@@ -344,6 +423,29 @@ void orc_cell_update(int model, const double* par, int npar, const double* y, do
                 yn[BR_X1 + g] = A * y[BR_X1 + g] + B;
             }
         } break;
+        case ORC_BR_MRL: {
+            /* as ORC_BR, with m^3 = P3 and the chain advanced by matrix
+             * Rush-Larsen; the gates x1, h, j, d, f by Eq. (RL) */
+            const double Cm = 1.0;
+            double cur[3], al[6], be[6], T[16];
+            br_currents_m3(p, y[MR_V], y[MR_CA], y[MR_X1], y[MR_P0 + 3], y[MR_H], y[MR_J], y[MR_D], y[MR_F], cur);
+            orc_br_rates(y[MR_V], al, be);
+            yn[MR_V] = y[MR_V] + dt * (-(cur[0] - Istim) / Cm + L);
+            yn[MR_CA] = y[MR_CA] + dt * cur[2];
+            const int gate_of[5] = {0, 2, 3, 4, 5}; /* x1, h, j, d, f in the rate table */
+            for (int q = 0; q < 5; q++) {
+                const int g = gate_of[q];
+                double A = exp(-(al[g] + be[g]) * dt);
+                double B = al[g] / (al[g] + be[g]) * (1.0 - A);
+                yn[MR_X1 + q] = A * y[MR_X1 + q] + B;
+            }
+            orc_mrl_transition(y[MR_V], dt, T);
+            for (int i = 0; i < 4; i++) {
+                double s = 0.0;
+                for (int j = 0; j < 4; j++) s += T[i * 4 + j] * y[MR_P0 + j];
+                yn[MR_P0 + i] = s;
+            }
+        } break;
     }
 }
 
@@ -377,7 +479,7 @@ static int model_rhs(int model, const double* p, const double* y, double I, doub
  * 1/6, 1/3, 1/3, 1/6. */
 int orc_cell_update_rk4(int model, const double* par, int npar, const double* y, double L, double Istim,
                         double dt, double* yn) {
-    double p[8], k1[8], k2[8], k3[8], k4[8], t[8];
+    double p[8], k1[ORC_MAXS], k2[ORC_MAXS], k3[ORC_MAXS], k4[ORC_MAXS], t[ORC_MAXS];
     model_params(model, par, npar, p);
     const int S = orc_nvars(model);
     const double I = L + Istim;
@@ -423,6 +525,19 @@ int orc_rest_state(int model, const double* par, int npar, double* y) {
                 memcpy(y, yn, sizeof(double) * 8);
             }
         } return ORC_OK;
+        case ORC_BR_MRL: {
+            /* the BR rest state with the chain at the binomial distribution
+             * of m (independent subunits) */
+            double r[8];
+            orc_rest_state(ORC_BR, par, npar, r);
+            const double m = r[BR_M];
+            y[MR_V] = r[BR_V]; y[MR_CA] = r[BR_CA]; y[MR_X1] = r[BR_X1];
+            y[MR_H] = r[BR_H]; y[MR_J] = r[BR_J]; y[MR_D] = r[BR_D]; y[MR_F] = r[BR_F];
+            y[MR_P0 + 0] = (1 - m) * (1 - m) * (1 - m);
+            y[MR_P0 + 1] = 3 * m * (1 - m) * (1 - m);
+            y[MR_P0 + 2] = 3 * m * m * (1 - m);
+            y[MR_P0 + 3] = m * m * m;
+        } return ORC_OK;
     }
     return ORC_ERR_ARG;
 }
@@ -461,7 +576,7 @@ static void node_update(const orc_run_cfg* c, const double* y, double L, double 
         kinetics(c, y, L, Is, dt, yn);
         return;
     }
-    double yh[8];
+    double yh[ORC_MAXS];
     const int S = orc_nvars(c->model);
     for (int v = 0; v < S; v++) yh[v] = y[v];
     yh[0] = y[0] + dt * L;
@@ -478,7 +593,7 @@ int orc_run(const orc_geom* g, const orc_run_cfg* c, double* state, double dt, i
             double* t, long long* n, int32_t* act) {
     const size_t N = (size_t)g->nx * g->ny * g->nz;
     const int S = orc_nvars(c->model);
-    if (S == 0 || (c->rk4 && c->model == ORC_BR)) return ORC_ERR_ARG;
+    if (S == 0 || (c->rk4 && (c->model == ORC_BR || c->model == ORC_BR_MRL))) return ORC_ERR_ARG;
     int rc = orc_check_fibres(g);
     if (rc) return rc;
     size_t nt = 0;
@@ -498,7 +613,7 @@ int orc_run(const orc_geom* g, const orc_run_cfg* c, double* state, double dt, i
                     orc_cell_weights(g, x, y, z, W + 27 * m);
                     m++;
                 }
-    double y[8], yn[8];
+    double y[ORC_MAXS], yn[ORC_MAXS];
     for (int s = 0; s < n_steps; s++) {
         int on = c->amp != 0.0 && *t >= c->t_on && *t < c->t_off;
         for (size_t i = 0; i < nt; i++)
@@ -526,9 +641,9 @@ int orc_step_cells(const orc_geom* g, const orc_run_cfg* c, const double* state,
                    double t, const long long* cells, int ncells, double* out) {
     const size_t N = (size_t)g->nx * g->ny * g->nz;
     const int S = orc_nvars(c->model);
-    if (S == 0 || (c->rk4 && c->model == ORC_BR)) return ORC_ERR_ARG;
+    if (S == 0 || (c->rk4 && (c->model == ORC_BR || c->model == ORC_BR_MRL))) return ORC_ERR_ARG;
     int on = c->amp != 0.0 && t >= c->t_on && t < c->t_off;
-    double W[27], y[8], yn[8];
+    double W[27], y[ORC_MAXS], yn[ORC_MAXS];
     for (int i = 0; i < ncells; i++) {
         long long p = cells[i];
         int x = (int)(p % g->nx), yy = (int)((p / g->nx) % g->ny), z = (int)(p / ((long long)g->nx * g->ny));
