@@ -65,12 +65,26 @@ extern "C" {
  *  BBX_ZFK       1 var.  alpha=0.13.  dV = V(V-alpha)(1-V), Eq. (ZFKbidomV).
  *                threshold 0.5.
  *  BBX_DIFFUSION 1 var, no reaction (the diffusion equation alone).
- *                threshold 0.5. */
+ *                threshold 0.5.
+ *  BBX_BR_MRL    11 vars (V, Ca, x1, h, j, d, f, P0, P1, P2, P3).  Parameters
+ *                and threshold as BBX_BR.  Beeler-Reuter with the sodium
+ *                activation m^3 in its Markov form: Pk = probability that k of
+ *                the three activation subunits are open (P3 in place of m^3),
+ *                du/dt = A(V) u (Eq. markov-generic) with k -> k+1 at
+ *                (3-k) alpha_m, k -> k-1 at k beta_m, advanced by the matrix
+ *                Rush-Larsen scheme u_{n+1} = exp(dt A(V_n)) u_n (section
+ *                "Exponential solvers"), the matrix tabulated in V from
+ *                -120 to +80 mV every 0.025 mV and interpolated linearly
+ *                (built on the device whenever dt changes; V outside the
+ *                range takes the end entry).  Unsplit Euler / Rush-Larsen
+ *                only: bbx_set_scheme(BBX_SCHEME_LIE), bbx_set_solver(
+ *                BBX_SOLVER_RK4) and the surrogate are refused. */
 #define BBX_FHN 1
 #define BBX_BARKLEY 2
 #define BBX_BR 3
 #define BBX_ZFK 4
 #define BBX_DIFFUSION 5
+#define BBX_BR_MRL 6
 
 #define BBX_ACT_NONE 2147483647 /* activation map value of a node never activated */
 

@@ -17,8 +17,9 @@
 //     gates) is fused, the new state is stored straight from registers;
 //   - the activation map is written on the first upward crossing only;
 //   - the sum of the new V over tissue nodes is reduced in the same pass
-//     (compensated float pairs per thread and warp, double across warps and
-//     CTAs, deterministic last-CTA finalisation).
+//     (compensated float pairs per thread and warp, one double per piece;
+//     the fixed-order sum of the pieces when the total is read, or at the
+//     end of a batch launch).
 #pragma once
 
 #include <cuda.h>
@@ -36,7 +37,9 @@ namespace bbx {
 
 enum : int { ERRBIT_TIMEOUT = 1, ERRBIT_NAN = 2 };
 
-// Device-updated state of one grid: written only by the last CTA of a step.
+// Device-updated state of one grid: written once per step, by the CTA that
+// takes the last start ticket (single-grid launch) or by the last CTA to
+// finish (batch launch), and by the on-demand sum of a pending total.
 struct TissueDyn {
     double t;       // model time t_n
     double total;   // tissue sum of V after the most recent step
@@ -70,6 +73,7 @@ struct TissueArgs {  // (CUtensorMap members impose its alignment)
     float c_perp, c_d, c_dh, c_s, c_iso;
     float mp[8];  // model parameters in kernel form
     const struct SurrogateData* surr;  // reaction surrogate (Beeler-Reuter), or nullptr
+    const float4* mrl;                 // matrix Rush-Larsen table (BBX_BR_MRL), or nullptr
 };
 
 // One launch: a balanced schedule of pieces over the grids of one kernel type.
@@ -433,11 +437,18 @@ struct Model<BBX_BR> {
     // 1 - A by expm1f (no cancellation when (alpha+beta) dt is small).
     __device__ static __forceinline__ void increment(const float* mp, const float* y, float L, float Is, float dt,
                                                      float* d) {
+        increment_m3(mp, y, y[3] * y[3] * y[3], L, Is, dt, d);
+    }
+
+    // The same with the open probability m3 of the sodium activation given
+    // (y[3] only feeds the m-gate increment d[3]).
+    __device__ static __forceinline__ void increment_m3(const float* mp, const float* y, float m3, float L,
+                                                        float Is, float dt, float* d) {
         const float V = y[0], Ca = y[1];
         const float x1 = y[2], m = y[3], h = y[4], j = y[5], dd = y[6], f = y[7];
 
         // membrane currents
-        const float INa = (mp[0] * m * m * m * h * j + mp[1]) * (V - mp[2]);
+        const float INa = (mp[0] * m3 * h * j + mp[1]) * (V - mp[2]);
         const float Es = -82.3f - 13.0287f * __logf(Ca);
         const float Is_ = mp[3] * dd * f * (V - Es);
         const float Ix1 = x1 * 0.8f * (__expf(0.04f * (V + 77.0f)) - 1.0f) * __expf(-0.04f * (V + 35.0f));
@@ -485,6 +496,53 @@ struct Model<BBX_BR> {
         increment(mp, y, L, Is, dt, d);
 #pragma unroll
         for (int v = 0; v < 8; ++v) y[v] = y[v] + d[v];
+    }
+};
+
+// Beeler-Reuter with the sodium activation m^3 in its Markov form: the
+// probabilities P0..P3 that k = 0..3 of the three activation subunits are
+// open (P3 in place of m^3), du/dt = A(V) u with k -> k+1 at (3-k) alpha_m
+// and k -> k-1 at k beta_m, advanced by the matrix Rush-Larsen scheme
+// u_{n+1} = T(V_n) u_n, T = exp(dt A) (section "Exponential solvers").  T is
+// tabulated in V (kMrlN entries kMrlDv mV apart from kMrlVmin, 16 floats
+// each, row-major; built on the device for the grid's dt) and interpolated
+// linearly; V outside the table takes the end entry.  x1, h, j, d, f by
+// Eq. (RL), V and Ca by Eq. (Euler), as Model<BBX_BR>.
+// State: V, Ca, x1, h, j, d, f, P0, P1, P2, P3.
+constexpr float kMrlVmin = -120.0f, kMrlDv = 0.025f, kMrlInvDv = 40.0f;
+constexpr int kMrlN = 8001;  // V from -120 to +80 mV
+
+template <>
+struct Model<BBX_BR_MRL> {
+    static constexpr int S = 11;
+
+    __device__ static __forceinline__ void update_tab(const float* mp, const float4* __restrict__ tab, float* y,
+                                                      float L, float Is, float dt) {
+        const float yb[8] = {y[0], y[1], y[2], 0.0f, y[3], y[4], y[5], y[6]};
+        float d[8];
+        Model<BBX_BR>::increment_m3(mp, yb, y[10], L, Is, dt, d);
+        // the chain, from V at the start of the step
+        float xi = (y[0] - kMrlVmin) * kMrlInvDv;
+        xi = fminf(fmaxf(xi, 0.0f), (float)(kMrlN - 1));
+        int i = (int)xi;
+        if (i > kMrlN - 2) i = kMrlN - 2;
+        const float w = xi - (float)i;
+        const float4* t0 = tab + 4 * i;
+        float pn[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float4 a = __ldg(t0 + r), b = __ldg(t0 + 4 + r);
+            const float qa = fmaf(a.x, y[7], fmaf(a.y, y[8], fmaf(a.z, y[9], a.w * y[10])));
+            const float qb = fmaf(b.x, y[7], fmaf(b.y, y[8], fmaf(b.z, y[9], b.w * y[10])));
+            pn[r] = fmaf(w, qb - qa, qa);
+        }
+        y[0] += d[0];
+        y[1] += d[1];
+        y[2] += d[2];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) y[3 + g] += d[4 + g];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) y[7 + r] = pn[r];
     }
 };
 
@@ -814,6 +872,7 @@ struct PieceSlot : Coef {
     int step_next;
     int split, rk4;
     const SurrogateData* surr;  // nullptr: exact reaction everywhere
+    const float4* mrl;          // matrix Rush-Larsen table (BBX_BR_MRL)
     float mp[8];
 };
 static_assert(sizeof(PieceSlot) <= 176, "piece ring slot size");
@@ -953,6 +1012,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                         r.rk4 = T->rk4;
                         r.c_perp = T->c_perp; r.c_d = T->c_d; r.c_dh = T->c_dh; r.c_s = T->c_s; r.c_iso = T->c_iso;
                         r.surr = T->surr;
+                        r.mrl = T->mrl;
 #pragma unroll
                         for (int i = 0; i < 8; ++i) r.mp[i] = T->mp[i];
                     }
@@ -1245,6 +1305,10 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
 #pragma unroll
                                 for (int e = 0; e < 2; ++e) Model<MODEL>::update(mp, yv[e], Lr[r][e], Isr[e], a.dt);
                             }
+                        } else if constexpr (MODEL == BBX_BR_MRL) {
+#pragma unroll
+                            for (int e = 0; e < 2; ++e)
+                                Model<MODEL>::update_tab(mp, a.mrl, yv[e], Lr[r][e], Isr[e], a.dt);
                         } else {
 #pragma unroll
                             for (int e = 0; e < 2; ++e) Model<MODEL>::update(mp, yv[e], Lr[r][e], Isr[e], a.dt);

@@ -19,6 +19,8 @@ StepKernel step_kernel_barkley(bool masked, bool aniso, int ty, bool planar, boo
 StepKernel step_kernel_br(bool masked, bool aniso, int ty, bool planar, bool general);
 StepKernel step_kernel_zfk(bool masked, bool aniso, int ty, bool planar, bool general);
 StepKernel step_kernel_diffusion(bool masked, bool aniso, int ty, bool planar, bool general);
+StepKernel step_kernel_br_mrl(bool masked, bool aniso, int ty, bool planar, bool general);
+cudaError_t mrl_build_table(float4* tab, double dt, cudaStream_t s);
 StepKernel step_kernel_br_surrogate(bool masked, bool aniso, int ty);
 cudaError_t launch_ppm(const float* s0, const float* s1, const int* cur, const uint8_t* mask, long long vol, int nx,
                        int ny, int nz, int px, long long plane, const int layer[3], const float lo[3],
@@ -46,6 +48,7 @@ int model_nvars(int model) {
         case BBX_BR: return 8;
         case BBX_ZFK: return 1;
         case BBX_DIFFUSION: return 1;
+        case BBX_BR_MRL: return 11;
     }
     return 0;
 }
@@ -53,7 +56,8 @@ int model_nvars(int model) {
 double model_threshold(int model) {
     switch (model) {
         case BBX_FHN: return 0.0;
-        case BBX_BR: return -40.0;
+        case BBX_BR:
+        case BBX_BR_MRL: return -40.0;
         default: return 0.5;
     }
 }
@@ -63,7 +67,8 @@ int model_defaults(int model, double* p) {
     switch (model) {
         case BBX_FHN: p[0] = 0.3; p[1] = 0.71; p[2] = 0.5; return 3;
         case BBX_BARKLEY: p[0] = 0.75; p[1] = 0.02; p[2] = 0.02; return 3;
-        case BBX_BR: p[0] = 4.0; p[1] = 0.003; p[2] = 50.0; p[3] = 0.09; return 4;
+        case BBX_BR:
+        case BBX_BR_MRL: p[0] = 4.0; p[1] = 0.003; p[2] = 50.0; p[3] = 0.09; return 4;
         case BBX_ZFK: p[0] = 0.13; return 1;
         case BBX_DIFFUSION: return 0;
     }
@@ -76,7 +81,8 @@ void model_kernel_params(int model, const double* p, float* mp) {
     switch (model) {
         case BBX_FHN: mp[0] = float(1.0 / p[0]); mp[1] = float(p[0]); mp[2] = float(p[1]); mp[3] = float(p[2]); break;
         case BBX_BARKLEY: mp[0] = float(1.0 / p[0]); mp[1] = float(p[1]); mp[2] = float(1.0 / p[2]); break;
-        case BBX_BR: for (int i = 0; i < 4; ++i) mp[i] = float(p[i]); break;
+        case BBX_BR:
+        case BBX_BR_MRL: for (int i = 0; i < 4; ++i) mp[i] = float(p[i]); break;
         case BBX_ZFK: mp[0] = float(p[0]); break;
         default: break;
     }
@@ -94,6 +100,7 @@ StepKernel lookup_kernel(int model, bool masked, bool aniso, int ty, bool surrog
         case BBX_BR: return step_kernel_br(masked, aniso, ty, planar, general);
         case BBX_ZFK: return step_kernel_zfk(masked, aniso, ty, planar, general);
         case BBX_DIFFUSION: return step_kernel_diffusion(masked, aniso, ty, planar, general);
+        case BBX_BR_MRL: return step_kernel_br_mrl(masked, aniso, ty, planar, general);
     }
     return StepKernel{nullptr, 0, 0, 0};
 }
@@ -254,7 +261,7 @@ __global__ void k_compact(const uint8_t* __restrict__ flags, long long n, int* _
 // kernel's own update; Barkley, ZFK, diffusion: 0.
 __global__ void k_rest(int model, const float* mp, double beta_d, double gamma_d, float* out) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    for (int i = 0; i < 8; ++i) out[i] = 0.0f;
+    for (int i = 0; i < 16; ++i) out[i] = 0.0f;
     if (model == BBX_FHN) {
         double u = -1.0;
         for (int it = 0; it < 100; ++it) {
@@ -270,6 +277,20 @@ __global__ void k_rest(int model, const float* mp, double beta_d, double gamma_d
         for (int i = 0; i < 8; ++i) p[i] = mp[i];
         for (int n = 0; n < 200000; ++n) Model<BBX_BR>::update(p, y, 0.0f, 0.0f, 0.05f);
         for (int i = 0; i < 8; ++i) out[i] = y[i];
+    } else if (model == BBX_BR_MRL) {
+        // the Beeler-Reuter rest state, with the chain at the binomial
+        // distribution of the rest value of m (independent subunits)
+        float y[8] = {-84.0f, 1e-7f, 0.0f, 0.0f, 1.0f, 1.0f, 0.0f, 1.0f};
+        float p[8];
+        for (int i = 0; i < 8; ++i) p[i] = mp[i];
+        for (int n = 0; n < 200000; ++n) Model<BBX_BR>::update(p, y, 0.0f, 0.0f, 0.05f);
+        const double m = y[3];
+        out[0] = y[0]; out[1] = y[1]; out[2] = y[2];
+        out[3] = y[4]; out[4] = y[5]; out[5] = y[6]; out[6] = y[7];
+        out[7] = float((1 - m) * (1 - m) * (1 - m));
+        out[8] = float(3 * m * (1 - m) * (1 - m));
+        out[9] = float(3 * m * m * (1 - m));
+        out[10] = float(m * m * m);
     }
 }
 
@@ -628,7 +649,9 @@ struct bbx_grid {
     float* d_state[2] = {nullptr, nullptr};
     bool bound = false;
     int32_t* d_act = nullptr;
-    float* d_rest = nullptr;  // 8 floats
+    float* d_rest = nullptr;  // 16 floats
+    float4* d_mrl = nullptr;  // matrix Rush-Larsen table (BBX_BR_MRL)
+    double mrl_dt = 0.0;      // the time step d_mrl was built for
     float* d_mp = nullptr;    // 8 floats
 
     uint8_t* d_stim = nullptr;
@@ -832,10 +855,20 @@ int encode_targs(const bbx_grid* g, int ty, TissueArgs* t) {
     t->c_iso = (float)(g->Dpar * ih2);
     model_kernel_params(g->model, g->par, t->mp);
     t->surr = (g->surr_on && g->model == BBX_BR) ? g->d_surr : nullptr;
+    t->mrl = g->model == BBX_BR_MRL ? g->d_mrl : nullptr;
     return BBX_OK;
 }
 
 int finish_total(bbx_grid* g);
+
+// The matrix Rush-Larsen table of a BBX_BR_MRL grid, rebuilt on its stream
+// whenever the time step differs from the one it was built for.
+int mrl_refresh(bbx_grid* g) {
+    if (g->model != BBX_BR_MRL || !g->d_mrl || !(g->dt > 0.0) || g->mrl_dt == g->dt) return BBX_OK;
+    BBX_CUDA(mrl_build_table(g->d_mrl, g->dt, g->stream));
+    g->mrl_dt = g->dt;
+    return BBX_OK;
+}
 
 // Bring h_t, d_t and the single-grid launch plan in line with the settings.
 int prepare(bbx_grid* g) {
@@ -843,7 +876,7 @@ int prepare(bbx_grid* g) {
     ++g->version;
     if (!g->model || !g->d_state[0]) return BBX_ERR_STATE;
     int rc0 = finish_total(g);  // the plan's partials are about to be replaced
-    if (rc0) return rc0;
+    if (rc0 || (rc0 = mrl_refresh(g))) return rc0;
     BBX_CUDA(cudaStreamSynchronize(g->stream));
     StepKernel k;
     int ctas = 0;
@@ -865,6 +898,8 @@ int prepare(bbx_grid* g) {
 // time step) without rebuilding the plan.
 int refresh_targs(bbx_grid* g) {
     if (!g->ready) return prepare(g);
+    int rc = mrl_refresh(g);
+    if (rc) return rc;
     ++g->version;
     g->h_t.t_on = g->t_on;
     g->h_t.t_off = g->t_off;
@@ -988,6 +1023,7 @@ void bbx_destroy_grid(bbx_grid* g) {
     }
     cudaFree(g->d_act);
     cudaFree(g->d_rest);
+    cudaFree(g->d_mrl);
     cudaFree(g->d_mp);
     cudaFree(g->d_stim);
     cudaFree(g->d_bricks);
@@ -1035,7 +1071,7 @@ int bbx_create_grid(bbx_grid** out, int nx, int ny, int nz, double h, const uint
         if (dmalloc(&g->d_partials, sizeof(double) * kMaxPartials) != cudaSuccess ||
             dmalloc(&g->d_ticket, sizeof(unsigned int)) != cudaSuccess ||
             dmalloc(&g->d_total2, sizeof(double)) != cudaSuccess || dmalloc(&g->d_err, sizeof(int)) != cudaSuccess ||
-            dmalloc(&g->d_rest, sizeof(float) * 8) != cudaSuccess ||
+            dmalloc(&g->d_rest, sizeof(float) * 16) != cudaSuccess ||
             dmalloc(&g->d_mp, sizeof(float) * 8) != cudaSuccess ||
             dmalloc(&g->d_t, sizeof(TissueArgs)) != cudaSuccess ||
             dmalloc(&g->d_dyn, sizeof(TissueDyn)) != cudaSuccess) {
@@ -1185,7 +1221,15 @@ int bbx_set_ionic_model(bbx_grid* g, int model, const double* params, int n_para
         return BBX_ERR_NOMEM;
     }
     if (model != BBX_BR) g->surr_on = false;
-    if (model == BBX_BR) g->rk4 = 0;  // Beeler-Reuter keeps Euler / Rush-Larsen
+    if (model == BBX_BR || model == BBX_BR_MRL) g->rk4 = 0;  // Beeler-Reuter keeps Euler / Rush-Larsen
+    if (model == BBX_BR_MRL) {
+        g->split = 0;  // unsplit only (no Lie-scheme kernels for this model)
+        if (!g->d_mrl && dmalloc(&g->d_mrl, sizeof(float4) * 4 * (size_t)kMrlN) != cudaSuccess) {
+            cudaGetLastError();
+            return BBX_ERR_NOMEM;
+        }
+        g->mrl_dt = 0.0;  // built for the grid's dt in prepare()
+    }
     g->model = model;
     g->S = S;
     for (int i = 0; i < 8; ++i) g->par[i] = p[i];
@@ -1316,13 +1360,14 @@ static int apply_kinetics_setting(bbx_grid* g) {
 
 int bbx_set_scheme(bbx_grid* g, int scheme) {
     if (!g || (scheme != BBX_SCHEME_UNSPLIT && scheme != BBX_SCHEME_LIE)) return BBX_ERR_ARG;
+    if (scheme == BBX_SCHEME_LIE && g->model == BBX_BR_MRL) return BBX_ERR_UNSUPPORTED;
     g->split = scheme == BBX_SCHEME_LIE ? 1 : 0;
     return apply_kinetics_setting(g);
 }
 
 int bbx_set_solver(bbx_grid* g, int solver) {
     if (!g || (solver != BBX_SOLVER_EULER && solver != BBX_SOLVER_RK4)) return BBX_ERR_ARG;
-    if (solver == BBX_SOLVER_RK4 && g->model == BBX_BR) return BBX_ERR_UNSUPPORTED;
+    if (solver == BBX_SOLVER_RK4 && (g->model == BBX_BR || g->model == BBX_BR_MRL)) return BBX_ERR_UNSUPPORTED;
     g->rk4 = solver == BBX_SOLVER_RK4 ? 1 : 0;
     return apply_kinetics_setting(g);
 }

@@ -17,7 +17,7 @@ import numpy as np
 
 SEED0 = 16050601
 
-FHN, BARKLEY, BR, ZFK = 1, 2, 3, 4
+FHN, BARKLEY, BR, ZFK, BR_MRL = 1, 2, 3, 4, 6
 
 
 @dataclass
@@ -190,6 +190,15 @@ def br_slab(nx=256, ny=256, nz=64, seed=SEED0 + 3, h=0.2, dt=0.02, D_par=0.1, D_
     return Workload("br_slab_%dx%dx%d" % (nx, ny, nz), nx, ny, nz, h, dt, BR, [4.0, 0.003, 50.0, 0.09],
                     D_par, D_perp, fibres=rotational_fibres(nx, ny, nz), ic_region=reg, ic_value=20.0,
                     n_steps=n_steps, theta=-40.0)
+
+
+def br_mrl_slab(nx=256, ny=256, nz=64, **kw):
+    """br_slab with the sodium activation in its Markov form (BR_MRL, matrix
+    Rush-Larsen); same geometry, fibres, physics and initial condition."""
+    w = br_slab(nx, ny, nz, **kw)
+    w.name = "br_mrl_slab_%dx%dx%d" % (nx, ny, nz)
+    w.model = BR_MRL
+    return w
 
 
 # ---------------------------------------------------------------------------
