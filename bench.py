@@ -397,6 +397,11 @@ def run_configs(args, dev, stream, dist=None, n_ranks=1):
                                 "3D Barkley slab 512x512x256, rotating fibres, 19-point"),
         "br_shell_512": (lambda: wl.br_shell(512), (2, 22),
                          "Beeler-Reuter ellipsoidal shell in 512^3 (14 % tissue), helical fibres, masked 19-point"),
+        "br_256x256x64": (lambda: wl.br_slab(256, 256, 64), (2, 22),
+                          "Beeler-Reuter slab 256x256x64, rotating fibres, 19-point, Rush-Larsen gates"),
+        "br_mrl_256x256x64": (lambda: wl.br_mrl_slab(256, 256, 64), (2, 22),
+                              "the same slab with the sodium activation as a 4-state Markov chain, "
+                              "matrix Rush-Larsen with T(V) tabulated"),
     }
     out = {}
     for name in args.configs.split(","):
@@ -614,7 +619,7 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=48)
     ap.add_argument("--tile", default=None, help="TY,TZ brick shape instead of autotuning")
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--configs", default="fhn_200,fhn_16384,barkley_512x512x256,br_shell_512",
+    ap.add_argument("--configs", default="fhn_200,fhn_16384,barkley_512x512x256,br_shell_512,br_256x256x64,br_mrl_256x256x64",
                     help="comma-separated other workloads to time by differencing ('' for none)")
     ap.add_argument("--surrogate-pairs", type=int, default=10_000_000)
     ap.add_argument("--surrogate-traj-steps", type=int, default=6000)
