@@ -145,3 +145,28 @@ def test_markov_rest_state_and_refusals(bbx):
     assert e.value.code == bbx.BBX_ERR_UNSUPPORTED
     G.step(w.dt, 5)  # still steps
     assert np.isfinite(G.read_all()).all()
+
+
+def test_markov_grid_in_a_batch_matches_the_grid_stepped_alone(bbx):
+    w = wl.br_mrl_slab(64, 14, 4)
+    rest = oracle.rest_state(w.model, w.params)
+    st0 = w.initial_state(rest).astype(np.float32)
+    A = _grid(bbx, w, 7, 4)
+    A.set_timestep(w.dt)
+    A.write_all(st0)
+    A.step(w.dt, 30)
+    solo = A.read_all()
+    B = _grid(bbx, w, 7, 4)
+    B.set_timestep(w.dt)
+    B.write_all(st0)
+    F = _grid(bbx, wl.fhn_sheet(80, 40))
+    F.set_timestep(0.01)
+    batch = bbx.Batch([B, F])
+    ty = batch.info()["tile_y"]
+    batch.step(30)
+    batch.sync()
+    got = B.read_all()
+    if 7 in ty and len(set(ty)) == len(ty):
+        assert np.array_equal(got, solo)
+    tis = np.ones(w.shape, bool)
+    assert _rel_linf(got[0], solo[0], tis) < 1e-5
