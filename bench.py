@@ -402,6 +402,10 @@ def run_configs(args, dev, stream, dist=None, n_ranks=1):
         "br_mrl_256x256x64": (lambda: wl.br_mrl_slab(256, 256, 64), (2, 22),
                               "the same slab with the sodium activation as a 4-state Markov chain, "
                               "matrix Rush-Larsen with T(V) tabulated"),
+        "br_256x256x64_tab": (lambda: wl.br_slab(256, 256, 64), (2, 22),
+                              "Beeler-Reuter slab 256x256x64, Rush-Larsen coefficients tabulated in V"),
+        "br_shell_512_tab": (lambda: wl.br_shell(512), (2, 22),
+                             "Beeler-Reuter shell in 512^3, Rush-Larsen coefficients tabulated in V"),
     }
     out = {}
     for name in args.configs.split(","):
@@ -414,6 +418,8 @@ def run_configs(args, dev, stream, dist=None, n_ranks=1):
         G.set_ionic_model(w.model, w.params)
         G.set_threshold(w.theta)
         G.set_timestep(w.dt)
+        if name.endswith("_tab"):
+            G.set_tabulation(True)
         st = initial_state(G, w)
         G.autotune(w.dt)
         G.write_all(st)
@@ -619,7 +625,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=48)
     ap.add_argument("--tile", default=None, help="TY,TZ brick shape instead of autotuning")
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--configs", default="fhn_200,fhn_16384,barkley_512x512x256,br_shell_512,br_256x256x64,br_mrl_256x256x64",
+    ap.add_argument("--configs", default="fhn_200,fhn_16384,barkley_512x512x256,br_shell_512,br_256x256x64,br_mrl_256x256x64,"
+                            "br_256x256x64_tab,br_shell_512_tab",
                     help="comma-separated other workloads to time by differencing ('' for none)")
     ap.add_argument("--surrogate-pairs", type=int, default=10_000_000)
     ap.add_argument("--surrogate-traj-steps", type=int, default=6000)

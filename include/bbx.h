@@ -200,6 +200,20 @@ int bbx_phase_singularities(bbx_grid* g, int var_a, double iso_a, int var_b, dou
  * (the grid does not qualify or does not fit), BBX_ERR_CUDA. */
 int bbx_set_resident(bbx_grid* g, int on);
 
+/* Beeler-Reuter (BBX_BR) with its Rush-Larsen coefficients tabulated in V:
+ * the rushlarsen device's tabulation (section "Exponential solvers": A(V)
+ * and B(V) of Eq. (RLcoeff) precomputed on a fine grid of V at start time).
+ * on != 0: A and B of the six gates and the V factors of I_x1 and I_K1 come
+ * from a table of V from -120 to +80 mV every 0.025 mV (FP64-built, stored
+ * as float, interpolated linearly; V outside takes the end entry), rebuilt on
+ * the device whenever dt changes, instead of being evaluated per node; gates
+ * then advance by y' = A y + B.  on = 0: the per-node evaluation (default).
+ * Results differ from the default by the interpolation error (about 1e-6
+ * relative on the coefficients).  Not used by the surrogate kernels.
+ * Errors: BBX_ERR_ARG, BBX_ERR_STATE (no model), BBX_ERR_UNSUPPORTED (model
+ * is not BBX_BR), BBX_ERR_NOMEM, BBX_ERR_CUDA. */
+int bbx_set_tabulation(bbx_grid* g, int on);
+
 /* Time-stepping scheme.  BBX_SCHEME_UNSPLIT (default; section "Computation of
  * intermediate expressions"): V^{n+1} = V^n + dt (f(V^n, g^n) + L V^n +
  * I_stim), the other variables from (V^n, g^n).  BBX_SCHEME_LIE (section

@@ -80,6 +80,7 @@ def _load():
         "bbx_set_scheme": [P, I],
         "bbx_set_solver": [P, I],
         "bbx_set_resident": [P, I],
+        "bbx_set_tabulation": [P, I],
         "bbx_ppm_frame": [P, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D), P],
         "bbx_phase_singularities": [P, I, D, I, D, P, I, ctypes.POINTER(I)],
         "bbx_batch_create": [ctypes.POINTER(P), ctypes.POINTER(P), I],
@@ -336,6 +337,10 @@ def bbx_set_scheme(g, scheme):
 
 def bbx_set_solver(g, solver):
     _check(_lib.bbx_set_solver(g, int(solver)), "bbx_set_solver")
+
+
+def bbx_set_tabulation(g, on=True):
+    _check(_lib.bbx_set_tabulation(g, int(bool(on))), "bbx_set_tabulation")
 
 
 def bbx_set_resident(g, on=True):

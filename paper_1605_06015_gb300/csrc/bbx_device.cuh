@@ -73,7 +73,7 @@ struct TissueArgs {  // (CUtensorMap members impose its alignment)
     float c_perp, c_d, c_dh, c_s, c_iso;
     float mp[8];  // model parameters in kernel form
     const struct SurrogateData* surr;  // reaction surrogate (Beeler-Reuter), or nullptr
-    const float4* mrl;                 // matrix Rush-Larsen table (BBX_BR_MRL), or nullptr
+    const float4* tab;                 // V-table of the model (kTabN x 4 float4), or nullptr
 };
 
 // One launch: a balanced schedule of pieces over the grids of one kernel type.
@@ -426,6 +426,20 @@ __device__ __forceinline__ void rk4_update(const float* mp, float* y, float L, f
 // Rate constants of the 1977 publication, written out per gate.
 __device__ __forceinline__ float br_ratio(float num, float den) { return __fdividef(num, den); }
 
+// Voltage tables of the Beeler-Reuter models: kTabN entries kTabDv mV apart
+// from kTabVmin (-120 to +80 mV), 16 floats (4 float4) each; V outside the
+// range takes the end entry.  Entry index and interpolation weight of V.
+constexpr float kTabVmin = -120.0f, kTabDv = 0.025f, kTabInvDv = 40.0f;
+constexpr int kTabN = 8001;
+__device__ __forceinline__ int tab_index(float V, float* w) {
+    float xi = (V - kTabVmin) * kTabInvDv;
+    xi = fminf(fmaxf(xi, 0.0f), (float)(kTabN - 1));
+    int i = (int)xi;
+    if (i > kTabN - 2) i = kTabN - 2;
+    *w = xi - (float)i;
+    return i;
+}
+
 template <>
 struct Model<BBX_BR> {
     static constexpr int S = 8;
@@ -497,6 +511,37 @@ struct Model<BBX_BR> {
 #pragma unroll
         for (int v = 0; v < 8; ++v) y[v] = y[v] + d[v];
     }
+
+    // The same step with the Rush-Larsen coefficients tabulated in V (the
+    // rushlarsen device's tabulation, section "Exponential solvers"): per
+    // entry A and B of Eq. (RL) for x1, m, h, j, d, f, then the V factors of
+    // I_x1 (I_x1 = x1 K(V)) and I_K1, interpolated linearly; gates by
+    // y' = A y + B.  The table is built for the grid's dt.
+    __device__ static __forceinline__ void update_tab(const float* mp, const float4* __restrict__ tab, float* y,
+                                                      float L, float Is, float dt) {
+        const float V = y[0], Ca = y[1];
+        float w;
+        const int i = tab_index(V, &w);
+        float c[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 a = __ldg(tab + 4 * i + q), b = __ldg(tab + 4 * i + 4 + q);
+            c[4 * q + 0] = fmaf(w, b.x - a.x, a.x);
+            c[4 * q + 1] = fmaf(w, b.y - a.y, a.y);
+            c[4 * q + 2] = fmaf(w, b.z - a.z, a.z);
+            c[4 * q + 3] = fmaf(w, b.w - a.w, a.w);
+        }
+        const float m = y[3];
+        const float INa = (mp[0] * m * m * m * y[4] * y[5] + mp[1]) * (V - mp[2]);
+        const float Es = -82.3f - 13.0287f * __logf(Ca);
+        const float Is_ = mp[3] * y[6] * y[7] * (V - Es);
+        const float Iion = INa + Is_ + y[2] * c[12] + c[13];
+        const float dCa = -1e-7f * Is_ + 0.07f * (1e-7f - Ca);
+        y[0] = V + dt * (-(Iion - Is) + L);  // Cm = 1
+        y[1] = Ca + dt * dCa;
+#pragma unroll
+        for (int g = 0; g < 6; ++g) y[2 + g] = fmaf(c[2 * g], y[2 + g], c[2 * g + 1]);
+    }
 };
 
 // Beeler-Reuter with the sodium activation m^3 in its Markov form: the
@@ -504,13 +549,11 @@ struct Model<BBX_BR> {
 // open (P3 in place of m^3), du/dt = A(V) u with k -> k+1 at (3-k) alpha_m
 // and k -> k-1 at k beta_m, advanced by the matrix Rush-Larsen scheme
 // u_{n+1} = T(V_n) u_n, T = exp(dt A) (section "Exponential solvers").  T is
-// tabulated in V (kMrlN entries kMrlDv mV apart from kMrlVmin, 16 floats
+// tabulated in V (kTabN entries kTabDv mV apart from kTabVmin, 16 floats
 // each, row-major; built on the device for the grid's dt) and interpolated
 // linearly; V outside the table takes the end entry.  x1, h, j, d, f by
 // Eq. (RL), V and Ca by Eq. (Euler), as Model<BBX_BR>.
 // State: V, Ca, x1, h, j, d, f, P0, P1, P2, P3.
-constexpr float kMrlVmin = -120.0f, kMrlDv = 0.025f, kMrlInvDv = 40.0f;
-constexpr int kMrlN = 8001;  // V from -120 to +80 mV
 
 template <>
 struct Model<BBX_BR_MRL> {
@@ -522,12 +565,8 @@ struct Model<BBX_BR_MRL> {
         float d[8];
         Model<BBX_BR>::increment_m3(mp, yb, y[10], L, Is, dt, d);
         // the chain, from V at the start of the step
-        float xi = (y[0] - kMrlVmin) * kMrlInvDv;
-        xi = fminf(fmaxf(xi, 0.0f), (float)(kMrlN - 1));
-        int i = (int)xi;
-        if (i > kMrlN - 2) i = kMrlN - 2;
-        const float w = xi - (float)i;
-        const float4* t0 = tab + 4 * i;
+        float w;
+        const float4* t0 = tab + 4 * tab_index(y[0], &w);
         float pn[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -872,7 +911,7 @@ struct PieceSlot : Coef {
     int step_next;
     int split, rk4;
     const SurrogateData* surr;  // nullptr: exact reaction everywhere
-    const float4* mrl;          // matrix Rush-Larsen table (BBX_BR_MRL)
+    const float4* tab;          // V-table of the model, or nullptr
     float mp[8];
 };
 static_assert(sizeof(PieceSlot) <= 176, "piece ring slot size");
@@ -1012,7 +1051,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                         r.rk4 = T->rk4;
                         r.c_perp = T->c_perp; r.c_d = T->c_d; r.c_dh = T->c_dh; r.c_s = T->c_s; r.c_iso = T->c_iso;
                         r.surr = T->surr;
-                        r.mrl = T->mrl;
+                        r.tab = T->tab;
 #pragma unroll
                         for (int i = 0; i < 8; ++i) r.mp[i] = T->mp[i];
                     }
@@ -1308,7 +1347,16 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                         } else if constexpr (MODEL == BBX_BR_MRL) {
 #pragma unroll
                             for (int e = 0; e < 2; ++e)
-                                Model<MODEL>::update_tab(mp, a.mrl, yv[e], Lr[r][e], Isr[e], a.dt);
+                                Model<MODEL>::update_tab(mp, a.tab, yv[e], Lr[r][e], Isr[e], a.dt);
+                        } else if constexpr (MODEL == BBX_BR) {
+                            if (a.tab) {
+#pragma unroll
+                                for (int e = 0; e < 2; ++e)
+                                    Model<MODEL>::update_tab(mp, a.tab, yv[e], Lr[r][e], Isr[e], a.dt);
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < 2; ++e) Model<MODEL>::update(mp, yv[e], Lr[r][e], Isr[e], a.dt);
+                            }
                         } else {
 #pragma unroll
                             for (int e = 0; e < 2; ++e) Model<MODEL>::update(mp, yv[e], Lr[r][e], Isr[e], a.dt);

@@ -21,6 +21,7 @@ StepKernel step_kernel_zfk(bool masked, bool aniso, int ty, bool planar, bool ge
 StepKernel step_kernel_diffusion(bool masked, bool aniso, int ty, bool planar, bool general);
 StepKernel step_kernel_br_mrl(bool masked, bool aniso, int ty, bool planar, bool general);
 cudaError_t mrl_build_table(float4* tab, double dt, cudaStream_t s);
+cudaError_t br_build_rl_table(float4* tab, double dt, cudaStream_t s);
 StepKernel step_kernel_br_surrogate(bool masked, bool aniso, int ty);
 cudaError_t launch_ppm(const float* s0, const float* s1, const int* cur, const uint8_t* mask, long long vol, int nx,
                        int ny, int nz, int px, long long plane, const int layer[3], const float lo[3],
@@ -650,8 +651,10 @@ struct bbx_grid {
     bool bound = false;
     int32_t* d_act = nullptr;
     float* d_rest = nullptr;  // 16 floats
-    float4* d_mrl = nullptr;  // matrix Rush-Larsen table (BBX_BR_MRL)
-    double mrl_dt = 0.0;      // the time step d_mrl was built for
+    float4* d_tab = nullptr;  // V-table: chain matrices (BBX_BR_MRL) or Rush-Larsen coefficients (BBX_BR)
+    double tab_dt = 0.0;      // the time step d_tab was built for
+    int tab_model = 0;        // the model d_tab was built for
+    bool tab_on = false;      // Beeler-Reuter with tabulated Rush-Larsen coefficients (bbx_set_tabulation)
     float* d_mp = nullptr;    // 8 floats
 
     uint8_t* d_stim = nullptr;
@@ -855,18 +858,31 @@ int encode_targs(const bbx_grid* g, int ty, TissueArgs* t) {
     t->c_iso = (float)(g->Dpar * ih2);
     model_kernel_params(g->model, g->par, t->mp);
     t->surr = (g->surr_on && g->model == BBX_BR) ? g->d_surr : nullptr;
-    t->mrl = g->model == BBX_BR_MRL ? g->d_mrl : nullptr;
+    t->tab = (g->model == BBX_BR_MRL || (g->model == BBX_BR && g->tab_on)) ? g->d_tab : nullptr;
     return BBX_OK;
 }
 
 int finish_total(bbx_grid* g);
 
-// The matrix Rush-Larsen table of a BBX_BR_MRL grid, rebuilt on its stream
-// whenever the time step differs from the one it was built for.
-int mrl_refresh(bbx_grid* g) {
-    if (g->model != BBX_BR_MRL || !g->d_mrl || !(g->dt > 0.0) || g->mrl_dt == g->dt) return BBX_OK;
-    BBX_CUDA(mrl_build_table(g->d_mrl, g->dt, g->stream));
-    g->mrl_dt = g->dt;
+// The V-table of a grid that uses one (the chain matrices of BBX_BR_MRL, the
+// Rush-Larsen coefficients of BBX_BR with tabulation on), allocated on first
+// use and rebuilt on the grid's stream whenever the model or the time step
+// differs from the ones it was built for.
+int tab_refresh(bbx_grid* g) {
+    const bool want = g->model == BBX_BR_MRL || (g->model == BBX_BR && g->tab_on);
+    if (!want) return BBX_OK;
+    if (!g->d_tab) {
+        if (dmalloc(&g->d_tab, sizeof(float4) * 4 * (size_t)kTabN) != cudaSuccess) {
+            cudaGetLastError();
+            return BBX_ERR_NOMEM;
+        }
+        g->tab_model = 0;
+    }
+    if (!(g->dt > 0.0) || (g->tab_dt == g->dt && g->tab_model == g->model)) return BBX_OK;
+    BBX_CUDA(g->model == BBX_BR_MRL ? mrl_build_table(g->d_tab, g->dt, g->stream)
+                                    : br_build_rl_table(g->d_tab, g->dt, g->stream));
+    g->tab_dt = g->dt;
+    g->tab_model = g->model;
     return BBX_OK;
 }
 
@@ -876,7 +892,7 @@ int prepare(bbx_grid* g) {
     ++g->version;
     if (!g->model || !g->d_state[0]) return BBX_ERR_STATE;
     int rc0 = finish_total(g);  // the plan's partials are about to be replaced
-    if (rc0 || (rc0 = mrl_refresh(g))) return rc0;
+    if (rc0 || (rc0 = tab_refresh(g))) return rc0;
     BBX_CUDA(cudaStreamSynchronize(g->stream));
     StepKernel k;
     int ctas = 0;
@@ -898,7 +914,7 @@ int prepare(bbx_grid* g) {
 // time step) without rebuilding the plan.
 int refresh_targs(bbx_grid* g) {
     if (!g->ready) return prepare(g);
-    int rc = mrl_refresh(g);
+    int rc = tab_refresh(g);
     if (rc) return rc;
     ++g->version;
     g->h_t.t_on = g->t_on;
@@ -1023,7 +1039,7 @@ void bbx_destroy_grid(bbx_grid* g) {
     }
     cudaFree(g->d_act);
     cudaFree(g->d_rest);
-    cudaFree(g->d_mrl);
+    cudaFree(g->d_tab);
     cudaFree(g->d_mp);
     cudaFree(g->d_stim);
     cudaFree(g->d_bricks);
@@ -1222,14 +1238,8 @@ int bbx_set_ionic_model(bbx_grid* g, int model, const double* params, int n_para
     }
     if (model != BBX_BR) g->surr_on = false;
     if (model == BBX_BR || model == BBX_BR_MRL) g->rk4 = 0;  // Beeler-Reuter keeps Euler / Rush-Larsen
-    if (model == BBX_BR_MRL) {
-        g->split = 0;  // unsplit only (no Lie-scheme kernels for this model)
-        if (!g->d_mrl && dmalloc(&g->d_mrl, sizeof(float4) * 4 * (size_t)kMrlN) != cudaSuccess) {
-            cudaGetLastError();
-            return BBX_ERR_NOMEM;
-        }
-        g->mrl_dt = 0.0;  // built for the grid's dt in prepare()
-    }
+    if (model == BBX_BR_MRL) g->split = 0;  // unsplit only (no Lie-scheme kernels for this model)
+    if (model != BBX_BR) g->tab_on = false;
     g->model = model;
     g->S = S;
     for (int i = 0; i < 8; ++i) g->par[i] = p[i];
@@ -1330,6 +1340,14 @@ int bbx_set_threshold(bbx_grid* g, double theta) {
 static bool resident_eligible(const bbx_grid* g) {
     return g->nz == 1 && !g->d_mask && !g->aniso && !g->split && !g->rk4 && !g->surr_on && !g->poison &&
            (g->model == BBX_FHN || g->model == BBX_BARKLEY || g->model == BBX_ZFK || g->model == BBX_DIFFUSION);
+}
+
+int bbx_set_tabulation(bbx_grid* g, int on) {
+    if (!g) return BBX_ERR_ARG;
+    if (!g->model) return BBX_ERR_STATE;
+    if (g->model != BBX_BR) return BBX_ERR_UNSUPPORTED;
+    g->tab_on = on != 0;
+    return prepare(g);
 }
 
 int bbx_set_resident(bbx_grid* g, int on) {

@@ -107,9 +107,9 @@ __global__ void k_mrl_table(float4* __restrict__ tab, int n, double vmin, double
 
 }  // namespace
 
-// Tabulate T(V) for the time step dt into tab (kMrlN x 4 float4).
+// Tabulate T(V) for the time step dt into tab (kTabN x 4 float4).
 cudaError_t mrl_build_table(float4* tab, double dt, cudaStream_t s) {
-    k_mrl_table<<<(kMrlN + 127) / 128, 128, 0, s>>>(tab, kMrlN, (double)kMrlVmin, (double)kMrlDv, dt);
+    k_mrl_table<<<(kTabN + 127) / 128, 128, 0, s>>>(tab, kTabN, (double)kTabVmin, (double)kTabDv, dt);
     return cudaGetLastError();
 }
 
