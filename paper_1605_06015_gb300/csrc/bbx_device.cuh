@@ -1348,7 +1348,9 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
 #pragma unroll
                             for (int e = 0; e < 2; ++e)
                                 Model<MODEL>::update_tab(mp, a.tab, yv[e], Lr[r][e], Isr[e], a.dt);
-                        } else if constexpr (MODEL == BBX_BR) {
+                        } else if constexpr (MODEL == BBX_BR && GEN) {
+                            // tabulated Rush-Larsen coefficients (the general
+                            // variants only, so the default kernel is unchanged)
                             if (a.tab) {
 #pragma unroll
                                 for (int e = 0; e < 2; ++e)

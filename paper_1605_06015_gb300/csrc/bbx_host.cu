@@ -864,6 +864,10 @@ int encode_targs(const bbx_grid* g, int ty, TissueArgs* t) {
 
 int finish_total(bbx_grid* g);
 
+// A grid that needs the general kernel variants (7- and 14-row tiles): the
+// Lie scheme, the RK4 solver, or Beeler-Reuter with tabulated coefficients.
+bool wants_general(const bbx_grid* g) { return g->split || g->rk4 || (g->tab_on && g->model == BBX_BR); }
+
 // The V-table of a grid that uses one (the chain matrices of BBX_BR_MRL, the
 // Rush-Larsen coefficients of BBX_BR with tabulation on), allocated on first
 // use and rebuilt on the grid's stream whenever the model or the time step
@@ -897,7 +901,7 @@ int prepare(bbx_grid* g) {
     StepKernel k;
     int ctas = 0;
     int rc = select_kernel(g->model, g->d_mask != nullptr, g->aniso, g->ty, g->device, g->num_sms, &k, &ctas,
-                           g->surr_on && g->model == BBX_BR, g->nz == 1, g->split || g->rk4);
+                           g->surr_on && g->model == BBX_BR, g->nz == 1, wants_general(g));
     if (rc) return rc;
     if ((rc = encode_targs(g, g->ty, &g->h_t))) return rc;
     BBX_CUDA(cudaMemcpyAsync(g->d_t, &g->h_t, sizeof(TissueArgs), cudaMemcpyHostToDevice, g->stream));
@@ -1342,12 +1346,14 @@ static bool resident_eligible(const bbx_grid* g) {
            (g->model == BBX_FHN || g->model == BBX_BARKLEY || g->model == BBX_ZFK || g->model == BBX_DIFFUSION);
 }
 
+static int apply_kinetics_setting(bbx_grid* g);
+
 int bbx_set_tabulation(bbx_grid* g, int on) {
     if (!g) return BBX_ERR_ARG;
     if (!g->model) return BBX_ERR_STATE;
     if (g->model != BBX_BR) return BBX_ERR_UNSUPPORTED;
     g->tab_on = on != 0;
-    return prepare(g);
+    return apply_kinetics_setting(g);
 }
 
 int bbx_set_resident(bbx_grid* g, int on) {
@@ -1372,7 +1378,7 @@ int bbx_set_resident(bbx_grid* g, int on) {
 // 28-row tiles: such a grid moves to 14 rows).
 static int apply_kinetics_setting(bbx_grid* g) {
     if (!g->model) return BBX_OK;
-    if ((g->split || g->rk4) && g->ty == 28) return bbx_set_tiling(g, 14, g->zb);
+    if (wants_general(g) && g->ty == 28) return bbx_set_tiling(g, 14, g->zb);
     return prepare(g);
 }
 
@@ -1825,7 +1831,7 @@ int batch_build(bbx_batch* b, const std::vector<int>* tys) {
             auto& gr = b->groups[gi];
             if (gr.model == g->model && gr.masked == (g->d_mask != nullptr) && gr.aniso == g->aniso &&
                 gr.surr == (g->surr_on && g->model == BBX_BR) && gr.planar == (g->nz == 1) &&
-                gr.general == (g->split || g->rk4))
+                gr.general == wants_general(g))
                 break;
         }
         if (gi == b->groups.size()) {
@@ -1835,7 +1841,7 @@ int batch_build(bbx_batch* b, const std::vector<int>* tys) {
             gr.aniso = g->aniso;
             gr.surr = g->surr_on && g->model == BBX_BR;
             gr.planar = g->nz == 1;
-            gr.general = g->split || g->rk4;
+            gr.general = wants_general(g);
             b->groups.push_back(gr);
         }
         b->groups[gi].members.push_back((int)i);
