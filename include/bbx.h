@@ -76,7 +76,9 @@ extern "C" {
  *                "Exponential solvers"), the matrix tabulated in V from
  *                -120 to +80 mV every 0.025 mV and interpolated linearly
  *                (built on the device whenever dt changes; V outside the
- *                range takes the end entry).  Unsplit Euler / Rush-Larsen
+ *                range takes the end entry); x1, h, j, d, f by Rush-Larsen
+ *                with coefficients from the same V grid (as
+ *                bbx_set_tabulation does for BBX_BR).  Unsplit Euler / Rush-Larsen
  *                only: bbx_set_scheme(BBX_SCHEME_LIE), bbx_set_solver(
  *                BBX_SOLVER_RK4) and the surrogate are refused. */
 #define BBX_FHN 1

@@ -552,21 +552,32 @@ struct Model<BBX_BR> {
 // tabulated in V (kTabN entries kTabDv mV apart from kTabVmin, 16 floats
 // each, row-major; built on the device for the grid's dt) and interpolated
 // linearly; V outside the table takes the end entry.  x1, h, j, d, f by
-// Eq. (RL), V and Ca by Eq. (Euler), as Model<BBX_BR>.
+// Eq. (RL) with tabulated coefficients (as Model<BBX_BR>::update_tab), V and
+// Ca by Eq. (Euler).
 // State: V, Ca, x1, h, j, d, f, P0, P1, P2, P3.
 
 template <>
 struct Model<BBX_BR_MRL> {
     static constexpr int S = 11;
 
+    // tab: the Rush-Larsen table of Model<BBX_BR>::update_tab (kTabN x 4
+    // float4), followed by the chain's transition matrices (kTabN x 4 float4).
     __device__ static __forceinline__ void update_tab(const float* mp, const float4* __restrict__ tab, float* y,
                                                       float L, float Is, float dt) {
-        const float yb[8] = {y[0], y[1], y[2], 0.0f, y[3], y[4], y[5], y[6]};
-        float d[8];
-        Model<BBX_BR>::increment_m3(mp, yb, y[10], L, Is, dt, d);
-        // the chain, from V at the start of the step
+        const float V = y[0], Ca = y[1];
         float w;
-        const float4* t0 = tab + 4 * tab_index(y[0], &w);
+        const int i = tab_index(V, &w);
+        float c[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 a = __ldg(tab + 4 * i + q), b = __ldg(tab + 4 * i + 4 + q);
+            c[4 * q + 0] = fmaf(w, b.x - a.x, a.x);
+            c[4 * q + 1] = fmaf(w, b.y - a.y, a.y);
+            c[4 * q + 2] = fmaf(w, b.z - a.z, a.z);
+            c[4 * q + 3] = fmaf(w, b.w - a.w, a.w);
+        }
+        // the chain, from V at the start of the step
+        const float4* t0 = tab + 4 * kTabN + 4 * i;
         float pn[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -575,11 +586,17 @@ struct Model<BBX_BR_MRL> {
             const float qb = fmaf(b.x, y[7], fmaf(b.y, y[8], fmaf(b.z, y[9], b.w * y[10])));
             pn[r] = fmaf(w, qb - qa, qa);
         }
-        y[0] += d[0];
-        y[1] += d[1];
-        y[2] += d[2];
+        // currents with P3 in place of m^3; x1, h, j, d, f by y' = A y + B
+        const float INa = (mp[0] * y[10] * y[3] * y[4] + mp[1]) * (V - mp[2]);
+        const float Es = -82.3f - 13.0287f * __logf(Ca);
+        const float Is_ = mp[3] * y[5] * y[6] * (V - Es);
+        const float Iion = INa + Is_ + y[2] * c[12] + c[13];
+        const float dCa = -1e-7f * Is_ + 0.07f * (1e-7f - Ca);
+        y[0] = V + dt * (-(Iion - Is) + L);  // Cm = 1
+        y[1] = Ca + dt * dCa;
+        y[2] = fmaf(c[0], y[2], c[1]);  // x1
 #pragma unroll
-        for (int g = 0; g < 4; ++g) y[3 + g] += d[4 + g];
+        for (int g = 0; g < 4; ++g) y[3 + g] = fmaf(c[4 + 2 * g], y[3 + g], c[5 + 2 * g]);  // h, j, d, f
 #pragma unroll
         for (int r = 0; r < 4; ++r) y[7 + r] = pn[r];
     }

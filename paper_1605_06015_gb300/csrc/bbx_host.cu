@@ -868,23 +868,23 @@ int finish_total(bbx_grid* g);
 // Lie scheme, the RK4 solver, or Beeler-Reuter with tabulated coefficients.
 bool wants_general(const bbx_grid* g) { return g->split || g->rk4 || (g->tab_on && g->model == BBX_BR); }
 
-// The V-table of a grid that uses one (the chain matrices of BBX_BR_MRL, the
-// Rush-Larsen coefficients of BBX_BR with tabulation on), allocated on first
+// The V-table of a grid that uses one (the Rush-Larsen coefficients of BBX_BR
+// with tabulation on; those and the chain matrices of BBX_BR_MRL), allocated on first
 // use and rebuilt on the grid's stream whenever the model or the time step
 // differs from the ones it was built for.
 int tab_refresh(bbx_grid* g) {
     const bool want = g->model == BBX_BR_MRL || (g->model == BBX_BR && g->tab_on);
     if (!want) return BBX_OK;
-    if (!g->d_tab) {
-        if (dmalloc(&g->d_tab, sizeof(float4) * 4 * (size_t)kTabN) != cudaSuccess) {
+    if (!g->d_tab) {  // room for both tables of BBX_BR_MRL
+        if (dmalloc(&g->d_tab, sizeof(float4) * 8 * (size_t)kTabN) != cudaSuccess) {
             cudaGetLastError();
             return BBX_ERR_NOMEM;
         }
         g->tab_model = 0;
     }
     if (!(g->dt > 0.0) || (g->tab_dt == g->dt && g->tab_model == g->model)) return BBX_OK;
-    BBX_CUDA(g->model == BBX_BR_MRL ? mrl_build_table(g->d_tab, g->dt, g->stream)
-                                    : br_build_rl_table(g->d_tab, g->dt, g->stream));
+    BBX_CUDA(br_build_rl_table(g->d_tab, g->dt, g->stream));
+    if (g->model == BBX_BR_MRL) BBX_CUDA(mrl_build_table(g->d_tab + 4 * (size_t)kTabN, g->dt, g->stream));
     g->tab_dt = g->dt;
     g->tab_model = g->model;
     return BBX_OK;
