@@ -199,28 +199,25 @@ def run_reference(args):
 
 
 def run_e2e(G, w, st0, S, args, dist, dev, ws, n_tissue):
-    """Steps through the C ABI with host buffers: write u and v from pinned
-    host memory, one step, read u and v back into pinned host memory."""
+    """Steps through the C ABI with host buffers: every step writes all
+    variables from pinned host memory (bbx_write_all), steps once and reads
+    all variables back into pinned host memory (bbx_read_all)."""
     import torch
-    pin_in = [torch.from_numpy(st0[v].copy()).pin_memory() for v in range(S)]
-    pin_out = [torch.empty(st0[v].shape, dtype=torch.float32).pin_memory() for v in range(S)]
+    pin_in = torch.from_numpy(st0[:S].copy()).pin_memory()
+    pin_out = torch.empty(pin_in.shape, dtype=torch.float32).pin_memory()
     e2e_steps = max(3, min(args.steps, 20))
     for _ in range(2):
-        for v in range(S):
-            G.write_state(v, pin_in[v])
+        G.write_all(pin_in)
         G.step(w.dt, 1)
-        for v in range(S):
-            G.read_state(v, out=pin_out[v])
+        G.read_all(out=pin_out)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     e0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for v in range(S):
-            G.write_state(v, pin_in[v])
+        G.write_all(pin_in)
         G.step(w.dt, 1)
-        for v in range(S):
-            G.read_state(v, out=pin_out[v])
+        G.read_all(out=pin_out)
     torch.cuda.synchronize()
     e_wall = time.perf_counter() - e0
     e_wall = max_over_ranks(e_wall, dist, dev)

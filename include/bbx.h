@@ -144,6 +144,11 @@ int bbx_set_ionic_model(bbx_grid* g, int model, const double* params, int n_para
  * BBX_ERR_ARG (var out of range, n wrong, null). */
 int bbx_write_state(bbx_grid* g, int var, const float* host, size_t n);
 
+/* All state variables at once, [var][z][y][x] (n = nvars*nx*ny*nz floats),
+ * into both ping-pong buffers with one synchronisation (one host copy when
+ * the rows are not padded).  Errors as bbx_write_state. */
+int bbx_write_all(bbx_grid* g, const float* host, size_t n);
+
 /* Let the caller (e.g. PyTorch) own the state: dev_a and dev_b each hold
  * bytes >= nvars*nz*ny*px*4 bytes laid out [var][z][y][x] with row pitch px,
  * 16-byte aligned.  The library never frees them.  Must follow
@@ -249,6 +254,11 @@ int bbx_step(bbx_grid* g, double dt, int n_steps);
 
 /* Copy one state variable to the host (n = nx*ny*nz floats).  Synchronises. */
 int bbx_read_state(bbx_grid* g, int var, float* host_out, size_t n);
+
+/* All state variables at once, [var][z][y][x] (n = nvars*nx*ny*nz floats;
+ * one device-to-host copy when the rows are not padded).  Synchronises;
+ * returns sticky device errors as bbx_read_state. */
+int bbx_read_all(bbx_grid* g, float* host_out, size_t n);
 
 /* Activation steps (BBX_ACT_NONE where not activated), n int32.  Synchronises. */
 int bbx_read_activation(bbx_grid* g, int32_t* host_out, size_t n);

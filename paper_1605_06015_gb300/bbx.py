@@ -58,6 +58,8 @@ def _load():
         "bbx_set_fibres": [P, P, D, D],
         "bbx_set_ionic_model": [P, I, P, I],
         "bbx_write_state": [P, I, P, Z],
+        "bbx_write_all": [P, P, Z],
+        "bbx_read_all": [P, P, Z],
         "bbx_bind_state": [P, P, P, Z],
         "bbx_set_stimulus": [P, P, D, D, D],
         "bbx_set_threshold": [P, D],
@@ -208,6 +210,29 @@ def bbx_write_state(g, var, values):
     n, _ = _ncell(g)
     vp, keep = _hostptr(values, np.float32, n)
     _check(_lib.bbx_write_state(g, int(var), vp, n), "bbx_write_state")
+
+
+def bbx_write_all(g, state):
+    """All variables at once: state [nvars][nz][ny][nx] float32 (NumPy or a
+    CPU torch tensor, pinned or not)."""
+    n, _ = _ncell(g)
+    S = bbx_get_info(g)["nvars"]
+    vp, keep = _hostptr(state, np.float32, S * n)
+    _check(_lib.bbx_write_all(g, vp, S * n), "bbx_write_all")
+
+
+def bbx_read_all(g, out=None):
+    """All variables at once into out [nvars][nz][ny][nx] float32 (new
+    NumPy array if None)."""
+    n, shape = _ncell(g)
+    S = bbx_get_info(g)["nvars"]
+    if out is None:
+        out = np.empty((S,) + tuple(shape), dtype=np.float32)
+    op, keep = _hostptr(out, np.float32, S * n)
+    if isinstance(keep, np.ndarray) and keep is not out and not np.shares_memory(keep, out):
+        raise ValueError("out must be a contiguous float32 array")
+    _check(_lib.bbx_read_all(g, op, S * n), "bbx_read_all")
+    return out
 
 
 def bbx_bind_state(g, dev_a, dev_b, nbytes=None):
@@ -516,10 +541,8 @@ class Grid:
             raise AttributeError(name)
         return lambda *a, **k: fn(self.g, *a, **k)
 
-    def read_all(self):
-        S = bbx_get_info(self.g)["nvars"]
-        return np.stack([bbx_read_state(self.g, v) for v in range(S)])
+    def read_all(self, out=None):
+        return bbx_read_all(self.g, out)
 
     def write_all(self, state):
-        for v in range(state.shape[0]):
-            bbx_write_state(self.g, v, np.asarray(state[v], dtype=np.float32))
+        bbx_write_all(self.g, state)

@@ -1306,6 +1306,27 @@ int bbx_write_state(bbx_grid* g, int var, const float* host, size_t n) {
     return BBX_OK;
 }
 
+int bbx_write_all(bbx_grid* g, const float* host, size_t n) {
+    if (!g) return BBX_ERR_ARG;
+    if (!g->model) return BBX_ERR_STATE;
+    if (!host || n != (size_t)g->S * (size_t)g->ncell) return BBX_ERR_ARG;
+    // every variable into buffer 0, then buffer 0 into buffer 1 in one
+    // device copy (both hold the state, as bbx_write_state leaves them); one
+    // synchronisation at the end
+    if (g->px == g->nx) {
+        BBX_CUDA(cudaMemcpyAsync(g->d_state[0], host, sizeof(float) * n, cudaMemcpyHostToDevice, g->stream));
+    } else {
+        for (int v = 0; v < g->S; ++v) {
+            int rc = copy_in(g, g->d_state[0] + (size_t)v * g->vol, host + (size_t)v * g->ncell, sizeof(float));
+            if (rc) return rc;
+        }
+    }
+    BBX_CUDA(cudaMemcpyAsync(g->d_state[1], g->d_state[0], sizeof(float) * (size_t)g->S * g->vol,
+                             cudaMemcpyDeviceToDevice, g->stream));
+    BBX_CUDA(cudaStreamSynchronize(g->stream));
+    return BBX_OK;
+}
+
 int bbx_set_stimulus(bbx_grid* g, const uint8_t* region, double amp, double t_on, double t_off) {
     if (!g || !std::isfinite(amp) || std::isnan(t_on) || std::isnan(t_off)) return BBX_ERR_ARG;
     if (!region) {
@@ -1470,6 +1491,23 @@ int bbx_read_state(bbx_grid* g, int var, float* host, size_t n) {
     if (rc) return rc;
     rc = copy_out(g, host, g->d_state[d.cur] + (size_t)var * g->vol, sizeof(float));
     if (rc) return rc;
+    return check_sticky(g);
+}
+
+int bbx_read_all(bbx_grid* g, float* host, size_t n) {
+    if (!g) return BBX_ERR_ARG;
+    if (!g->model) return BBX_ERR_STATE;
+    if (!host || n != (size_t)g->S * (size_t)g->ncell) return BBX_ERR_ARG;
+    TissueDyn d;
+    int rc = read_dyn(g, &d);
+    if (rc) return rc;
+    const float* src = g->d_state[d.cur];
+    if (g->px == g->nx) {
+        BBX_CUDA(cudaMemcpyAsync(host, src, sizeof(float) * n, cudaMemcpyDeviceToHost, g->stream));
+    } else {
+        for (int v = 0; v < g->S; ++v)
+            if ((rc = copy_out(g, host + (size_t)v * g->ncell, src + (size_t)v * g->vol, sizeof(float)))) return rc;
+    }
     return check_sticky(g);
 }
 
