@@ -243,8 +243,9 @@ int bbx_set_scheme(bbx_grid* g, int scheme);
 int bbx_set_solver(bbx_grid* g, int solver);
 
 /* Advance n_steps explicit steps of size dt (asynchronous on the grid's
- * stream).  Each step also writes the double-precision sum of the new V over
- * tissue nodes (read with bbx_step_total).  Errors: BBX_ERR_STATE (no
+ * stream).  Each step also reduces the new V over tissue nodes into one
+ * double-precision partial per piece of its schedule (the total is summed
+ * from them, in a fixed order, by bbx_step_total).  Errors: BBX_ERR_STATE (no
  * model), BBX_ERR_ARG (dt <= 0, n_steps < 0), BBX_ERR_CUDA (launch),
  * BBX_ERR_UNSTABLE when dt (4 tr D + 2 |D_par - D_perp|) > 2 h^2, tr D =
  * D_par + 2 D_perp (3 D_par when isotropic): a Gershgorin bound on the
@@ -270,8 +271,10 @@ int bbx_write_activation(bbx_grid* g, const int32_t* host, size_t n);
  * double precision.  Synchronises. */
 int bbx_total(bbx_grid* g, int var, double* out);
 
-/* The tissue sum of V after the most recent step, computed inside that step.
- * Synchronises.  BBX_ERR_STATE if no step was taken. */
+/* The tissue sum of V after the most recent step: the fixed-order sum of the
+ * per-piece partials that step computed (a small kernel on the grid's stream
+ * adds them up the first time it is asked for; deterministic).  Synchronises.
+ * BBX_ERR_STATE if no step was taken; BBX_ERR_NAN if V is not finite. */
 int bbx_step_total(bbx_grid* g, double* out);
 
 /* Model time and step counter (checkpoint/resume). */
