@@ -35,7 +35,7 @@ namespace bbx {
 // launch arguments
 // ---------------------------------------------------------------------------
 
-enum : int { ERRBIT_TIMEOUT = 1, ERRBIT_NAN = 2 };
+enum : int { ERRBIT_TIMEOUT = 1, ERRBIT_NAN = 2, ERRBIT_HINT = 4 };
 
 // Device-updated state of one grid: written once per step, by the CTA that
 // takes the last start ticket (single-grid launch) or by the last CTA to
@@ -103,6 +103,14 @@ struct LaunchArgs {
     int* err;                  // sticky error bits
     long long wait_limit;      // clock64 cycles a wait may spin before giving up
     int poison_first_load;     // fault injection: CTA 0's first plane never completes
+    // Single-grid launch: the buffer parity the host expects (-1: read it),
+    // and for an unmasked 3D grid the schedule's shape, from which a CTA finds
+    // its first piece without a memory read (reg_len = 0: read the list).  A
+    // CTA then issues its first plane copies before any global load returns;
+    // both are checked against device memory (ERRBIT_HINT on a mismatch).
+    int cur_hint;
+    int reg_len, reg_nbx, reg_ty, reg_ctas;  // column length (nz), columns in x, tile rows, CTAs
+    long long reg_planes;                    // column-planes of the schedule
 };
 
 struct Coef {
@@ -128,6 +136,12 @@ __device__ __forceinline__ void mbar_init_fence() {
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Expect bytes on the barrier without arriving (the arrival comes later).
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
@@ -1022,12 +1036,49 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                 d0.n = D->n;
                 d0.cur = D->cur;
             }
+            // Single-grid launch of an unmasked 3D grid with a known parity:
+            // the first piece from the schedule's shape and its first three
+            // plane copies issued now, expected on their barriers but not yet
+            // arrived on (the arrival follows the piece context, below).
+            bool early = false;
+            int4 pc_early = make_int4(0, 0, 0, 0);
+            if (!PLANAR && L.single && L.cur_hint >= 0 && L.reg_len > 0 && !L.poison_first_load) {
+                const long long p0 = (long long)blockIdx.x * L.reg_planes / L.reg_ctas;
+                const long long p1 = ((long long)blockIdx.x + 1) * L.reg_planes / L.reg_ctas;
+                if (p1 > p0) {
+                    const int col = (int)(p0 / L.reg_len), z0 = (int)(p0 % L.reg_len);
+                    const int z1 = (int)min((long long)L.reg_len, z0 + (p1 - p0));
+                    pc_early = make_int4((col % L.reg_nbx) * TX, (col / L.reg_nbx) * L.reg_ty, z0, z1);
+                    early = true;
+                    const TissueArgs* T = &L.t0;
+                    const int src = L.cur_hint;
+                    const int nl = z1 - z0 + 2;
+#pragma unroll 1
+                    for (int off = 0; off < 3; ++off) {
+                        const int z = z0 - 1 + off;
+                        if (z < 0 || z >= T->nz) continue;
+                        uint64_t* bar = &full[off];
+                        unsigned char* st = smem + off * P::STAGE;
+                        const bool halo = (off == 0) || (off == nl - 1);
+                        mbar_expect_tx(bar, (halo || S == 1) ? P::TX_BYTES_HALO : P::TX_BYTES);
+                        tma_load_3d(st + P::U_OFF, &T->tm_u[src], pc_early.x - 4, pc_early.y - 1, z, bar);
+                        if (ANISO) tma_load_4d(st + P::F_OFF, &T->tm_f, pc_early.x, pc_early.y - 1, z, 0, bar);
+                        if (MASKED) tma_load_3d(st + P::M_OFF, &T->tm_m, pc_early.x - 16, pc_early.y - 1, z, bar);
+                        if (S > 1 && !halo) tma_load_4d(st + P::S_OFF, &T->tm_s[src], pc_early.x, pc_early.y, z, 1, bar);
+                    }
+                }
+            }
+            if (L.single && L.cur_hint >= 0 &&
+                (d0.cur != L.cur_hint ||
+                 (early && (pc_early.x != pc_next.x || pc_early.y != pc_next.y || pc_early.z != pc_next.z ||
+                            pc_early.w != pc_next.w))))
+                atomicOr(L.err, ERRBIT_HINT);
             for (int pi = piece_begin; pi < piece_end && !stop; ++pi, ++lp) {
                 const int4 pc = pc_next;
                 if (pi + 1 < piece_end) pc_next = L.pieces[pi + 1];
                 const TissueArgs* T = L.single ? &L.t0 : L.tissues + L.piece_tissue[pi];
                 const TissueDyn* D = T->dyn;
-                const int src = L.single ? d0.cur : D->cur;
+                const int src = L.single ? (L.cur_hint >= 0 ? L.cur_hint : d0.cur) : D->cur;
                 const int nz = T->nz;
                 const int nload = PLANAR ? pc.w - pc.z : pc.w - pc.z + 2;
                 for (int off = 0; off < nload; ++off) {
@@ -1077,7 +1128,9 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                     const bool halo = !PLANAR && ((off == 0) || (off == nload - 1));
                     uint64_t* bar = &full[slot];
                     unsigned char* st = smem + slot * P::STAGE;
-                    if (z < 0 || z >= nz) {
+                    if (early && lp == 0 && off < 3) {
+                        mbar_arrive(bar);  // its copies were issued at the start
+                    } else if (z < 0 || z >= nz) {
                         mbar_arrive(bar);  // plane outside the array: nothing to load
                     } else {
                         mbar_arrive_expect_tx(bar, (halo || S == 1) ? P::TX_BYTES_HALO : P::TX_BYTES);

@@ -585,6 +585,7 @@ LaunchArgs launch_args(const LaunchPlan& lp, const TissueArgs* d_tissues, int* d
     L.ticket = lp.d_ticket;
     L.err = d_err;
     L.poison_first_load = poison;
+    L.cur_hint = -1;
     L.wait_limit = poison ? kPoisonWaitLimit : kWaitLimitCycles;
     return L;
 }
@@ -653,6 +654,7 @@ struct bbx_grid {
     float* d_rest = nullptr;  // 16 floats
     float4* d_tab = nullptr;  // V-table: chain matrices (BBX_BR_MRL) or Rush-Larsen coefficients (BBX_BR)
     double tab_dt = 0.0;      // the time step d_tab was built for
+    int h_cur = 0;            // buffer parity as the enqueued work leaves it (mirror of d_dyn->cur)
     int tab_model = 0;        // the model d_tab was built for
     bool tab_on = false;      // Beeler-Reuter with tabulated Rush-Larsen coefficients (bbx_set_tabulation)
     float* d_mp = nullptr;    // 8 floats
@@ -938,12 +940,14 @@ int refresh_targs(bbx_grid* g) {
 int read_dyn(bbx_grid* g, TissueDyn* d) {
     BBX_CUDA(cudaMemcpyAsync(d, g->d_dyn, sizeof(TissueDyn), cudaMemcpyDeviceToHost, g->stream));
     BBX_CUDA(cudaStreamSynchronize(g->stream));
+    g->h_cur = d->cur;  // nothing is in flight: the device value is the parity
     return BBX_OK;
 }
 
 int write_dyn(bbx_grid* g, const TissueDyn& d) {
     BBX_CUDA(cudaMemcpyAsync(g->d_dyn, &d, sizeof(TissueDyn), cudaMemcpyHostToDevice, g->stream));
     BBX_CUDA(cudaStreamSynchronize(g->stream));
+    g->h_cur = d.cur;
     return BBX_OK;
 }
 
@@ -963,6 +967,7 @@ int check_sticky_ptr(cudaStream_t s, int* d_err) {
     BBX_CUDA(cudaStreamSynchronize(s));
     if (err & ERRBIT_TIMEOUT) return BBX_ERR_TIMEOUT;
     if (err & ERRBIT_NAN) return BBX_ERR_NAN;
+    if (err & ERRBIT_HINT) return BBX_ERR_STATE;  // host and device disagreed on the schedule or parity
     return BBX_OK;
 }
 
@@ -1260,6 +1265,7 @@ int bbx_set_ionic_model(bbx_grid* g, int model, const double* params, int n_para
     BBX_CUDA(cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream));
     BBX_CUDA(cudaMemsetAsync(g->d_dyn, 0, sizeof(TissueDyn), g->stream));
     BBX_CUDA(cudaStreamSynchronize(g->stream));
+    g->h_cur = 0;
     g->stepped = false;
     return prepare(g);
 }
@@ -1468,15 +1474,26 @@ int bbx_step(bbx_grid* g, double dt, int n_steps) {
             if (e != cudaSuccess) return fail_cuda(e);
             if (!ok) break;  // not launchable after all: the tiled kernel takes the rest
             done += chunk;
+            g->h_cur ^= chunk & 1;
         }
         if (done > 0) g->stepped = true;
         n_steps -= done;
         if (n_steps == 0) return BBX_OK;
     }
-    const LaunchArgs L = launch_args(g->lp, g->d_t, g->d_err, g->poison, &g->h_t);
+    LaunchArgs L = launch_args(g->lp, g->d_t, g->d_err, g->poison, &g->h_t);
+    if (!g->d_mask && g->nz > 1) {
+        // unmasked 3D grid: whole columns in order, equal shares (build_plan)
+        L.reg_len = g->nz;
+        L.reg_nbx = g->nbx;
+        L.reg_ty = g->ty;
+        L.reg_ctas = g->lp.ctas;
+        L.reg_planes = g->lp.n_planes;
+    }
     for (int s = 0; s < n_steps; ++s) {
+        L.cur_hint = g->h_cur;
         const cudaError_t e = launch(g->lp, L, g->stream);
         if (e != cudaSuccess) return fail_cuda(e);
+        g->h_cur ^= 1;
     }
     g->stepped = true;
     return BBX_OK;
@@ -2047,7 +2064,10 @@ int bbx_batch_step(bbx_batch* b, int n_steps) {
         if ((rc = batch_launch_step(b))) return rc;
     BBX_CUDA(cudaEventRecord(b->leave, b->ps));
     BBX_CUDA(cudaStreamWaitEvent(b->stream, b->leave, 0));
-    for (bbx_grid* g : b->grids) g->stepped = true;
+    for (bbx_grid* g : b->grids) {
+        g->stepped = true;
+        g->h_cur ^= n_steps & 1;  // every batch step flips every member's parity
+    }
     return BBX_OK;
 }
 
@@ -2128,6 +2148,7 @@ int bbx_batch_autotune(bbx_batch* b, double* best_ms) {
         TissueDyn d = saved[i].dyn;
         d.cur = 0;
         cudaMemcpyAsync(g->d_dyn, &d, sizeof(TissueDyn), cudaMemcpyHostToDevice, b->stream);
+        g->h_cur = 0;
         cudaStreamSynchronize(b->stream);
         cudaFree(saved[i].st);
         cudaFree(saved[i].act);

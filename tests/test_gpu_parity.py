@@ -492,3 +492,39 @@ def test_full_size_slab_one_step_sampled(bbx):
     for v in range(2):
         e = np.abs(flat[v, cells] - ref[:, v]).max() / max(np.abs(ref[:, v]).max(), 1e-30)
         assert e <= 1e-5, (v, e)
+
+
+def test_host_parity_mirror_through_every_stepping_path(bbx):
+    # Single-grid launches of unmasked 3D grids issue their first copies from
+    # the parity the host expects; any disagreement with the device would be
+    # reported (BBX_ERR_STATE) by the next synchronising call.  Step one grid
+    # through every path that moves the parity and compare with a grid that
+    # only steps alone.
+    w = wl.barkley_slab(70, 30, 10)
+    rest = oracle.rest_state(w.model, w.params)
+    st0 = w.initial_state(rest).astype(np.float32)
+    G = _gpu_grid(bbx, w, 14, 4)
+    H = _gpu_grid(bbx, w, 14, 4)
+    for X in (G, H):
+        X.set_timestep(w.dt)
+        X.write_all(st0)
+    F = _gpu_grid(bbx, wl.fhn_sheet(40, 20))
+    F.set_timestep(0.01)
+    G.step(w.dt, 3)
+    B = bbx.Batch([G, F])
+    B.step(3)
+    B.sync()
+    G.step(w.dt, 2)
+    t, n = G.get_time()
+    G.set_time(t, n)
+    G.step(w.dt, 1)
+    G.read_state(0)
+    G.step(w.dt, 1)
+    H.step(w.dt, 10)
+    got, ref = G.read_all(), H.read_all()
+    assert G.get_time()[1] == H.get_time()[1] == 10
+    assert _rel_linf(got[0], ref[0], np.ones(w.shape, bool)) < 1e-5
+    G.autotune(w.dt)  # leaves the state as it was
+    G.step(w.dt, 3)
+    H.step(w.dt, 3)
+    assert _rel_linf(G.read_all()[0], H.read_all()[0], np.ones(w.shape, bool)) < 1e-5
