@@ -294,10 +294,11 @@ __device__ __forceinline__ void step_finalize(const LaunchArgs& L, double* scrat
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // Fixed-order sums (deterministic).  One grid: every thread of the CTA
-    // strides over its pieces, then a shuffle tree per warp and the warps in
-    // order.  Several grids: one warp per grid, lanes striding its pieces.
-    // The partials are loaded several at a time so their L2 latencies overlap.
+    // Fixed-order sums (deterministic).  One grid in the launch: every
+    // thread of the CTA strides over its pieces, then a shuffle tree per warp
+    // and the warps in order.  Several grids: one warp per grid, lanes
+    // striding its pieces.  The partials are loaded several at a time so
+    // their L2 latencies overlap.
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
     auto finish = [&](int ti, double s) {
         const TissueArgs* T = L.tissues + ti;
@@ -309,15 +310,15 @@ __device__ __forceinline__ void step_finalize(const LaunchArgs& L, double* scrat
         d->cur = d->cur ^ 1;
         d->total_pending = 0;
     };
-    // direct: slots k0..k1 of partials; otherwise through tissue_pieces
-    auto strided_sum = [&](int k0, int k1, int first, int stride, bool direct) {
+    // the partials of the grid's pieces tissue_pieces[k0 .. k1)
+    auto strided_sum = [&](int k0, int k1, int first, int stride) {
         double s = 0.0;
         for (int k = k0 + first; k < k1; k += 4 * stride) {
             double v[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int kk = k + u * stride;
-                v[u] = kk < k1 ? __ldcg(&L.partials[direct ? kk : __ldcg(&L.tissue_pieces[kk])]) : 0.0;
+                v[u] = kk < k1 ? __ldcg(&L.partials[__ldcg(&L.tissue_pieces[kk])]) : 0.0;
             }
             s += (v[0] + v[1]) + (v[2] + v[3]);
         }
@@ -325,8 +326,7 @@ __device__ __forceinline__ void step_finalize(const LaunchArgs& L, double* scrat
         return s;
     };
     if (L.n_tissues == 1) {
-        const double s = strided_sum(__ldcg(&L.tissue_off[0]), __ldcg(&L.tissue_off[1]), threadIdx.x, blockDim.x,
-                                     false);
+        const double s = strided_sum(__ldcg(&L.tissue_off[0]), __ldcg(&L.tissue_off[1]), threadIdx.x, blockDim.x);
         if (lane == 0) scratch32[warp] = s;
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -336,7 +336,7 @@ __device__ __forceinline__ void step_finalize(const LaunchArgs& L, double* scrat
         }
     } else {
         for (int ti = warp; ti < L.n_tissues; ti += nwarps) {
-            const double s = strided_sum(__ldcg(&L.tissue_off[ti]), __ldcg(&L.tissue_off[ti + 1]), lane, 32, false);
+            const double s = strided_sum(__ldcg(&L.tissue_off[ti]), __ldcg(&L.tissue_off[ti + 1]), lane, 32);
             if (lane == 0) finish(ti, s);
         }
     }
