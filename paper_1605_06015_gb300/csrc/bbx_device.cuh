@@ -967,6 +967,13 @@ __device__ __forceinline__ void consumers_sync(int nthreads) {
     asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
+// First row of the tile of load off of a piece: a 3D piece keeps its tile
+// (pc.y); a sheet's piece is a run of tile rows pc.z .. pc.w of a column.
+template <bool PLANAR, int TY>
+__device__ __forceinline__ int tile_row_of(int4 pc, int off) {
+    return PLANAR ? (pc.z + off) * TY : pc.y;
+}
+
 // Warp-specialised step kernel: warps 0..RY-1 compute (2 x CY nodes per
 // thread), warp RY is the producer.
 //
@@ -1036,13 +1043,15 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                 d0.n = D->n;
                 d0.cur = D->cur;
             }
-            // Single-grid launch of an unmasked 3D grid with a known parity:
-            // the first piece from the schedule's shape and its first three
-            // plane copies issued now, expected on their barriers but not yet
-            // arrived on (the arrival follows the piece context, below).
+            // Single-grid launch of an unmasked grid with a known parity: the
+            // first piece from the schedule's shape and its first plane copies
+            // (three planes; two tile rows of a sheet) issued now, expected on
+            // their barriers but not yet arrived on (the arrival follows the
+            // piece context, below).
             bool early = false;
+            int n_early = 0;
             int4 pc_early = make_int4(0, 0, 0, 0);
-            if (!PLANAR && L.single && L.cur_hint >= 0 && L.reg_len > 0 && !L.poison_first_load) {
+            if (L.single && L.cur_hint >= 0 && L.reg_len > 0 && !L.poison_first_load) {
                 const long long p0 = (long long)blockIdx.x * L.reg_planes / L.reg_ctas;
                 const long long p1 = ((long long)blockIdx.x + 1) * L.reg_planes / L.reg_ctas;
                 if (p1 > p0) {
@@ -1052,19 +1061,21 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                     early = true;
                     const TissueArgs* T = &L.t0;
                     const int src = L.cur_hint;
-                    const int nl = z1 - z0 + 2;
+                    const int nl = PLANAR ? z1 - z0 : z1 - z0 + 2;
+                    n_early = PLANAR ? min(nl, 2) : 3;
 #pragma unroll 1
-                    for (int off = 0; off < 3; ++off) {
-                        const int z = z0 - 1 + off;
+                    for (int off = 0; off < n_early; ++off) {
+                        const int z = PLANAR ? 0 : z0 - 1 + off;
                         if (z < 0 || z >= T->nz) continue;
+                        const int y0 = tile_row_of<PLANAR, TY>(pc_early, off);
                         uint64_t* bar = &full[off];
                         unsigned char* st = smem + off * P::STAGE;
-                        const bool halo = (off == 0) || (off == nl - 1);
+                        const bool halo = !PLANAR && ((off == 0) || (off == nl - 1));
                         mbar_expect_tx(bar, (halo || S == 1) ? P::TX_BYTES_HALO : P::TX_BYTES);
-                        tma_load_3d(st + P::U_OFF, &T->tm_u[src], pc_early.x - 4, pc_early.y - 1, z, bar);
-                        if (ANISO) tma_load_4d(st + P::F_OFF, &T->tm_f, pc_early.x, pc_early.y - 1, z, 0, bar);
-                        if (MASKED) tma_load_3d(st + P::M_OFF, &T->tm_m, pc_early.x - 16, pc_early.y - 1, z, bar);
-                        if (S > 1 && !halo) tma_load_4d(st + P::S_OFF, &T->tm_s[src], pc_early.x, pc_early.y, z, 1, bar);
+                        tma_load_3d(st + P::U_OFF, &T->tm_u[src], pc_early.x - 4, y0 - 1, z, bar);
+                        if (ANISO) tma_load_4d(st + P::F_OFF, &T->tm_f, pc_early.x, y0 - 1, z, 0, bar);
+                        if (MASKED) tma_load_3d(st + P::M_OFF, &T->tm_m, pc_early.x - 16, y0 - 1, z, bar);
+                        if (S > 1 && !halo) tma_load_4d(st + P::S_OFF, &T->tm_s[src], pc_early.x, y0, z, 1, bar);
                     }
                 }
             }
@@ -1124,11 +1135,11 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                         for (int i = 0; i < 8; ++i) r.mp[i] = T->mp[i];
                     }
                     const int z = PLANAR ? 0 : pc.z - 1 + off;
-                    const int y0 = PLANAR ? (pc.z + off) * TY : pc.y;  // first row of the tile
+                    const int y0 = tile_row_of<PLANAR, TY>(pc, off);  // first row of the tile
                     const bool halo = !PLANAR && ((off == 0) || (off == nload - 1));
                     uint64_t* bar = &full[slot];
                     unsigned char* st = smem + slot * P::STAGE;
-                    if (early && lp == 0 && off < 3) {
+                    if (early && lp == 0 && off < n_early) {
                         mbar_arrive(bar);  // its copies were issued at the start
                     } else if (z < 0 || z >= nz) {
                         mbar_arrive(bar);  // plane outside the array: nothing to load

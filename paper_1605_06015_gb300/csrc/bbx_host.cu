@@ -1481,9 +1481,10 @@ int bbx_step(bbx_grid* g, double dt, int n_steps) {
         if (n_steps == 0) return BBX_OK;
     }
     LaunchArgs L = launch_args(g->lp, g->d_t, g->d_err, g->poison, &g->h_t);
-    if (!g->d_mask && g->nz > 1) {
-        // unmasked 3D grid: whole columns in order, equal shares (build_plan)
-        L.reg_len = g->nz;
+    if (!g->d_mask) {
+        // unmasked grid: whole columns in order (nz planes, or a sheet's nby
+        // tile rows), equal shares (build_plan)
+        L.reg_len = g->nz > 1 ? g->nz : g->nby;
         L.reg_nbx = g->nbx;
         L.reg_ty = g->ty;
         L.reg_ctas = g->lp.ctas;
