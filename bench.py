@@ -399,6 +399,8 @@ def run_configs(args, dev, stream, dist=None, n_ranks=1):
         "br_mrl_256x256x64": (lambda: wl.br_mrl_slab(256, 256, 64), (2, 22),
                               "the same slab with the sodium activation as a 4-state Markov chain, "
                               "matrix Rush-Larsen with T(V) tabulated"),
+        "br_shell_256": (lambda: wl.br_shell(256), (2, 22),
+                         "Beeler-Reuter shell in 256^3 (profiling size, not in the default list)"),
         "br_256x256x64_tab": (lambda: wl.br_slab(256, 256, 64), (2, 22),
                               "Beeler-Reuter slab 256x256x64, Rush-Larsen coefficients tabulated in V"),
         "br_shell_512_tab": (lambda: wl.br_shell(512), (2, 22),
