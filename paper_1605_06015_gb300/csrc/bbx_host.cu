@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <map>
 #include <vector>
 
 #include "bbx_device.cuh"
@@ -41,6 +42,7 @@ constexpr long long kWaitLimitCycles = 4000000000LL;  // about 2 s of SM clock
 constexpr long long kPoisonWaitLimit = 2000000LL;     // about 1 ms
 constexpr int kMaxPartials = 152 * 32;
 constexpr int kErrFibre = 4;
+constexpr int kChunkX = 16;  // x granularity of a masked grid's piece origins (the mask copy's 16-byte rule)
 
 int model_nvars(int model) {
     switch (model) {
@@ -215,6 +217,25 @@ __global__ void k_brick_flags(const uint8_t* __restrict__ mask, int nx, int ny, 
         const int x = x0 + c % kTileX;
         const int y = y0 + (c / kTileX) % ty;
         const int z = z0 + c / (kTileX * ty);
+        if (x < nx && y < ny && z < nz) any = mask[z * plane + (long long)y * px + x] != 0;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) flags[id] = any ? 1 : 0;
+}
+
+// One block per 16-node-wide chunk of a brick row band: does the chunk
+// (16 x ty x zb nodes) hold any tissue node?  Block id = cx + ncx (by + nby bz).
+__global__ void k_chunk_flags(const uint8_t* __restrict__ mask, int nx, int ny, int nz, int px, long long plane,
+                              int ty, int zb, int ncx, int nby, uint8_t* flags) {
+    const long long id = blockIdx.x;
+    const int cx = (int)(id % ncx), by = (int)((id / ncx) % nby), bz = (int)(id / ((long long)ncx * nby));
+    const int x0 = cx * kChunkX, y0 = by * ty, z0 = bz * zb;
+    const int cells = kChunkX * ty * zb;
+    int any = 0;
+    for (int c = threadIdx.x; c < cells && !any; c += blockDim.x) {
+        const int x = x0 + c % kChunkX;
+        const int y = y0 + (c / kChunkX) % ty;
+        const int z = z0 + c / (kChunkX * ty);
         if (x < nx && y < ny && z < nz) any = mask[z * plane + (long long)y * px + x] != 0;
     }
     any = __syncthreads_or(any);
@@ -668,6 +689,7 @@ struct bbx_grid {
     int* d_bricks = nullptr;
     long long n_bricks = 0;
     std::vector<int> h_bricks;  // host copy of the active brick ids (masked grids)
+    std::vector<uint8_t> h_chunks;  // masked 3D grids: tissue flag of each 16-wide chunk of each brick band
 
     TissueArgs h_t;                // host copy of the kernel's view of this grid
     TissueArgs* d_t = nullptr;     // device copy
@@ -750,6 +772,26 @@ int build_bricks(bbx_grid* g) {
     g->n_bricks = cnt;
     g->h_bricks.resize((size_t)cnt);
     if (cnt > 0) BBX_CUDA(cudaMemcpy(g->h_bricks.data(), g->d_bricks, sizeof(int) * cnt, cudaMemcpyDeviceToHost));
+    g->h_chunks.clear();
+    if (g->nz > 1) {
+        // 16-wide chunk flags, from which the pieces of a masked 3D grid are cut
+        const int ncx = (g->nx + kChunkX - 1) / kChunkX;
+        const long long nc = (long long)ncx * g->nby * g->nbz;
+        uint8_t* cflags = nullptr;
+        if (nc > 0x7fffffffLL || dmalloc(&cflags, nc) != cudaSuccess) {
+            cudaGetLastError();
+            return BBX_ERR_NOMEM;
+        }
+        k_chunk_flags<<<(unsigned)nc, 256, 0, g->stream>>>(g->d_mask, g->nx, g->ny, g->nz, g->px, g->plane, g->ty,
+                                                            g->zb, ncx, g->nby, cflags);
+        g->h_chunks.resize((size_t)nc);
+        cudaError_t e2 = cudaGetLastError();
+        if (e2 == cudaSuccess)
+            e2 = cudaMemcpyAsync(g->h_chunks.data(), cflags, nc, cudaMemcpyDeviceToHost, g->stream);
+        if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(g->stream);
+        cudaFree(cflags);
+        if (e2 != cudaSuccess) return fail_cuda(e2);
+    }
     return BBX_OK;
 }
 
@@ -781,18 +823,35 @@ void grid_segments(const bbx_grid* g, int tissue, std::vector<Seg>* segs) {
             for (int bx = 0; bx < g->nbx; ++bx) segs->push_back({tissue, bx * kTileX, by * g->ty, 0, g->nz});
         return;
     }
-    const long long ncol = (long long)g->nbx * g->nby;
-    std::vector<std::vector<int>> col((size_t)ncol);
-    for (int id : g->h_bricks) col[(size_t)(id % ncol)].push_back((int)(id / ncol));
-    for (long long c = 0; c < ncol; ++c) {
-        const std::vector<int>& zs = col[(size_t)c];
-        const int bx = (int)(c % g->nbx), by = (int)(c / g->nbx);
-        size_t i = 0;
-        while (i < zs.size()) {
-            size_t j = i;
-            while (j + 1 < zs.size() && zs[j + 1] == zs[j] + 1) ++j;
-            segs->push_back({tissue, bx * kTileX, by * g->ty, zs[i] * g->zb, std::min((zs[j] + 1) * g->zb, g->nz)});
-            i = j + 1;
+    // Masked 3D grid: in each band of ty rows by zb planes, the 16-wide chunks
+    // that hold tissue are covered from the left by 64-wide pieces starting
+    // at a chunk (so a wall that crosses a 64-column boundary costs one piece,
+    // not two); pieces with the same origin in consecutive bands of a row band
+    // merge into one z-run.  Every tissue node lies in exactly one piece.
+    const int ncx = (g->nx + kChunkX - 1) / kChunkX;
+    const int per = kTileX / kChunkX;
+    for (int by = 0; by < g->nby; ++by) {
+        std::map<int, std::vector<int>> runs;  // piece origin x0 -> bands bz holding a piece there
+        for (int bz = 0; bz < g->nbz; ++bz) {
+            const uint8_t* f = g->h_chunks.data() + ((size_t)bz * g->nby + by) * ncx;
+            for (int c = 0; c < ncx;) {
+                if (!f[c]) {
+                    ++c;
+                    continue;
+                }
+                runs[c * kChunkX].push_back(bz);
+                c += per;
+            }
+        }
+        for (const auto& kv : runs) {
+            const std::vector<int>& zs = kv.second;
+            size_t i = 0;
+            while (i < zs.size()) {
+                size_t j = i;
+                while (j + 1 < zs.size() && zs[j + 1] == zs[j] + 1) ++j;
+                segs->push_back({tissue, kv.first, by * g->ty, zs[i] * g->zb, std::min((zs[j] + 1) * g->zb, g->nz)});
+                i = j + 1;
+            }
         }
     }
 }
