@@ -261,6 +261,15 @@ int bbx_read_state(bbx_grid* g, int var, float* host_out, size_t n);
  * returns sticky device errors as bbx_read_state. */
 int bbx_read_all(bbx_grid* g, float* host_out, size_t n);
 
+/* Exchange the whole state with the host in one call: host_out receives the
+ * current state ([var][z][y][x], n = nvars*nx*ny*nz floats) while host_in is
+ * copied in as the new one, the two copies running at the same time (a
+ * second stream; both host buffers should be pinned for the copies to
+ * overlap).  Equal to bbx_read_all(host_out) followed by bbx_write_all(host_in),
+ * for a loop that feeds new inputs and takes results every step.
+ * Synchronises.  Errors as bbx_read_all / bbx_write_all, BBX_ERR_CUDA. */
+int bbx_exchange_state(bbx_grid* g, const float* host_in, float* host_out, size_t n);
+
 /* Activation steps (BBX_ACT_NONE where not activated), n int32.  Synchronises. */
 int bbx_read_activation(bbx_grid* g, int32_t* host_out, size_t n);
 

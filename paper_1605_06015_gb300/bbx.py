@@ -60,6 +60,7 @@ def _load():
         "bbx_write_state": [P, I, P, Z],
         "bbx_write_all": [P, P, Z],
         "bbx_read_all": [P, P, Z],
+        "bbx_exchange_state": [P, P, P, Z],
         "bbx_bind_state": [P, P, P, Z],
         "bbx_set_stimulus": [P, P, D, D, D],
         "bbx_set_threshold": [P, D],
@@ -232,6 +233,20 @@ def bbx_read_all(g, out=None):
     if isinstance(keep, np.ndarray) and keep is not out and not np.shares_memory(keep, out):
         raise ValueError("out must be a contiguous float32 array")
     _check(_lib.bbx_read_all(g, op, S * n), "bbx_read_all")
+    return out
+
+
+def bbx_exchange_state(g, state_in, out):
+    """out <- the current state, state_in -> the new state, both
+    [nvars][nz][ny][nx] float32, the copies overlapping (pinned CPU tensors or
+    arrays)."""
+    n, _ = _ncell(g)
+    S = bbx_get_info(g)["nvars"]
+    ip, keep_in = _hostptr(state_in, np.float32, S * n)
+    op, keep_out = _hostptr(out, np.float32, S * n)
+    if isinstance(keep_out, np.ndarray) and keep_out is not out and not np.shares_memory(keep_out, out):
+        raise ValueError("out must be a contiguous float32 array")
+    _check(_lib.bbx_exchange_state(g, ip, op, S * n), "bbx_exchange_state")
     return out
 
 

@@ -323,6 +323,10 @@ __global__ void k_fill_state(float* __restrict__ st, int S, long long vol, const
         st[i] = rest[i / vol];
 }
 
+__global__ void k_set_parity(TissueDyn* dyn, int cur) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) dyn->cur = cur;
+}
+
 __global__ void k_fill_int(int32_t* __restrict__ p, long long n, int32_t v) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
@@ -676,6 +680,8 @@ struct bbx_grid {
     float4* d_tab = nullptr;  // V-table: chain matrices (BBX_BR_MRL) or Rush-Larsen coefficients (BBX_BR)
     double tab_dt = 0.0;      // the time step d_tab was built for
     int h_cur = 0;            // buffer parity as the enqueued work leaves it (mirror of d_dyn->cur)
+    cudaStream_t copy_stream = nullptr;          // bbx_exchange_state: device-to-host copies
+    cudaEvent_t ev_enter = nullptr, ev_out = nullptr;
     int tab_model = 0;        // the model d_tab was built for
     bool tab_on = false;      // Beeler-Reuter with tabulated Rush-Larsen coefficients (bbx_set_tabulation)
     float* d_mp = nullptr;    // 8 floats
@@ -1099,6 +1105,12 @@ const char* bbx_status_string(int s) {
 void bbx_destroy_grid(bbx_grid* g) {
     if (!g) return;
     cudaStreamSynchronize(g->stream);
+    if (g->copy_stream) {
+        cudaStreamSynchronize(g->copy_stream);
+        cudaStreamDestroy(g->copy_stream);
+    }
+    if (g->ev_enter) cudaEventDestroy(g->ev_enter);
+    if (g->ev_out) cudaEventDestroy(g->ev_out);
     cudaFree(g->d_mask);
     cudaFree(g->d_fib);
     if (!g->bound) {
@@ -1585,6 +1597,41 @@ int bbx_read_all(bbx_grid* g, float* host, size_t n) {
         for (int v = 0; v < g->S; ++v)
             if ((rc = copy_out(g, host + (size_t)v * g->ncell, src + (size_t)v * g->vol, sizeof(float)))) return rc;
     }
+    return check_sticky(g);
+}
+
+int bbx_exchange_state(bbx_grid* g, const float* host_in, float* host_out, size_t n) {
+    if (!g) return BBX_ERR_ARG;
+    if (!g->model) return BBX_ERR_STATE;
+    if (!host_in || !host_out || n != (size_t)g->S * (size_t)g->ncell) return BBX_ERR_ARG;
+    if (g->px != g->nx) {  // padded rows: one direction after the other
+        int rc = bbx_read_all(g, host_out, n);
+        return rc ? rc : bbx_write_all(g, host_in, n);
+    }
+    if (!g->copy_stream) {
+        if (cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&g->ev_enter, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&g->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return BBX_ERR_CUDA;
+        }
+    }
+    const int cur = g->h_cur, oth = cur ^ 1;
+    const size_t bytes = sizeof(float) * n;
+    // the current state out on the copy stream, after everything enqueued so far ...
+    BBX_CUDA(cudaEventRecord(g->ev_enter, g->stream));
+    BBX_CUDA(cudaStreamWaitEvent(g->copy_stream, g->ev_enter, 0));
+    BBX_CUDA(cudaMemcpyAsync(host_out, g->d_state[cur], bytes, cudaMemcpyDeviceToHost, g->copy_stream));
+    // ... while the new one comes into the other buffer on the grid's stream
+    BBX_CUDA(cudaMemcpyAsync(g->d_state[oth], host_in, bytes, cudaMemcpyHostToDevice, g->stream));
+    BBX_CUDA(cudaEventRecord(g->ev_out, g->copy_stream));
+    BBX_CUDA(cudaStreamWaitEvent(g->stream, g->ev_out, 0));  // nothing overwrites the old buffer before it is out
+    if (g->d_mask)  // void nodes hold the same values in both buffers
+        BBX_CUDA(cudaMemcpyAsync(g->d_state[cur], g->d_state[oth], bytes, cudaMemcpyDeviceToDevice, g->stream));
+    k_set_parity<<<1, 1, 0, g->stream>>>(g->d_dyn, oth);
+    BBX_CUDA(cudaGetLastError());
+    g->h_cur = oth;
+    BBX_CUDA(cudaStreamSynchronize(g->stream));
     return check_sticky(g);
 }
 

@@ -528,3 +528,34 @@ def test_host_parity_mirror_through_every_stepping_path(bbx):
     G.step(w.dt, 3)
     H.step(w.dt, 3)
     assert _rel_linf(G.read_all()[0], H.read_all()[0], np.ones(w.shape, bool)) < 1e-5
+
+
+@pytest.mark.parametrize("nx,masked", [(64, False), (64, True), (70, False)])
+def test_exchange_state_is_read_all_then_write_all(bbx, nx, masked):
+    # bbx_exchange_state returns the current state while taking a new one
+    # (overlapping copies on two streams; one after the other for padded rows)
+    w = wl.barkley_slab(nx, 24, 8)
+    if masked:
+        w.mask, w.fibres = wl.random_geometry(nx, 24, 8, seed=9, tissue_frac=0.8)
+    rest = oracle.rest_state(w.model, w.params)
+    s0 = w.initial_state(rest).astype(np.float32)
+    s1 = (s0 + np.float32(0.01) * np.random.default_rng(3).random(s0.shape, dtype=np.float32)).astype(np.float32)
+    G = _gpu_grid(bbx, w, 14, 4)
+    H = _gpu_grid(bbx, w, 14, 4)
+    G.write_all(s0)
+    out = np.empty_like(s0)
+    G.exchange_state(s1, out)
+    assert np.array_equal(out, s0)
+    assert np.array_equal(G.read_all(), s1)
+    H.write_all(s1)
+    G.step(w.dt, 3)
+    H.step(w.dt, 3)
+    ref = H.read_all()
+    assert np.array_equal(G.read_all(), ref)
+    out2 = np.empty_like(s0)
+    G.exchange_state(s0, out2)
+    assert np.array_equal(out2, ref)
+    G.step(w.dt, 2)
+    H.write_all(s0)
+    H.step(w.dt, 2)
+    assert np.array_equal(G.read_all(), H.read_all())
