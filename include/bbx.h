@@ -442,6 +442,20 @@ int bbx_total_noalloc(const float* field_dev, const uint8_t* mask_dev, int nx, i
 /* Release every resource of the grid (NULL is ignored). */
 void bbx_destroy_grid(bbx_grid* g);
 
+/* Host-only test hooks (no device work, usable without a GPU).
+ * bbx_debug_cover_chunks: the pieces a masked 3D grid is cut into, from the
+ *   tissue flags of its 16-wide chunks, flags[bz][by][cx] (ncx x nby x nbz
+ *   bytes, nonzero = the 16 x ty x zb chunk holds tissue): *count pieces
+ *   (x0, y0, z0, z1) into out (4 ints each, at most cap pieces; BBX_ERR_ARG
+ *   with *count set if cap is too small).
+ * bbx_debug_plan_first_pieces: the first piece (x0, y0, z0, z1) of each CTA
+ *   when the segments segs4 (nsegs x (x0, y0, z0, z1), in order) are shared
+ *   among ctas CTAs; *used = CTAs used (at most the total plane count; at
+ *   most cap written, else BBX_ERR_ARG). */
+int bbx_debug_cover_chunks(const uint8_t* flags, int ncx, int nby, int nbz, int ty, int zb, int nz, int* out,
+                           int cap, int* count);
+int bbx_debug_plan_first_pieces(const int* segs4, int nsegs, int ctas, int* out, int cap, int* used);
+
 /* Static text for a status code. */
 const char* bbx_status_string(int status);
 

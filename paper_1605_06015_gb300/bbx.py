@@ -61,6 +61,8 @@ def _load():
         "bbx_write_all": [P, P, Z],
         "bbx_read_all": [P, P, Z],
         "bbx_exchange_state": [P, P, P, Z],
+        "bbx_debug_cover_chunks": [P, I, I, I, I, I, I, P, I, P],
+        "bbx_debug_plan_first_pieces": [P, I, I, P, I, P],
         "bbx_bind_state": [P, P, P, Z],
         "bbx_set_stimulus": [P, P, D, D, D],
         "bbx_set_threshold": [P, D],
@@ -248,6 +250,30 @@ def bbx_exchange_state(g, state_in, out):
         raise ValueError("out must be a contiguous float32 array")
     _check(_lib.bbx_exchange_state(g, ip, op, S * n), "bbx_exchange_state")
     return out
+
+
+def bbx_debug_cover_chunks(flags, ty, zb, nz):
+    """Host-only hook: the pieces (x0, y0, z0, z1) a masked 3D grid is cut
+    into, from its chunk flags [nbz][nby][ncx] (no GPU needed)."""
+    f = np.ascontiguousarray(flags, dtype=np.uint8)
+    nbz, nby, ncx = f.shape
+    cap = nbz * nby * ncx + 1
+    out = np.zeros(4 * cap, np.int32)
+    cnt = ctypes.c_int(0)
+    _check(_lib.bbx_debug_cover_chunks(f.ctypes.data, ncx, nby, nbz, int(ty), int(zb), int(nz), out.ctypes.data,
+                                       cap, ctypes.byref(cnt)), "bbx_debug_cover_chunks")
+    return out[: 4 * cnt.value].reshape(-1, 4)
+
+
+def bbx_debug_plan_first_pieces(segs, ctas):
+    """Host-only hook: the first piece of each CTA when the segments
+    (x0, y0, z0, z1) are shared among ctas CTAs; returns (pieces, CTAs used)."""
+    s = np.ascontiguousarray(np.asarray(segs, dtype=np.int32).reshape(-1))
+    out = np.zeros(4 * int(ctas), np.int32)
+    used = ctypes.c_int(0)
+    _check(_lib.bbx_debug_plan_first_pieces(s.ctypes.data, s.size // 4, int(ctas), out.ctypes.data, int(ctas),
+                                            ctypes.byref(used)), "bbx_debug_plan_first_pieces")
+    return out[: 4 * used.value].reshape(-1, 4), used.value
 
 
 def bbx_bind_state(g, dev_a, dev_b, nbytes=None):

@@ -509,15 +509,18 @@ int upload(T** d, size_t* cap, const std::vector<T>& h) {
 
 // Each CTA receives an equal share of the column-planes of all segments (in
 // segment order) as contiguous pieces, so that no CTA idles while others
-// finish; per grid, the pieces are listed for the fixed-order totals.
-int build_plan(LaunchPlan* lp, const std::vector<Seg>& segs, int n_tissues, int ctas) {
+// finish: CTA c takes column-planes [c T / ctas, (c+1) T / ctas) of the T in
+// all segments.  Returns the CTA count used (at most T); per[c] and per_t[c]
+// get CTA c's pieces and their grids.  Host-only.
+int plan_shares(const std::vector<Seg>& segs, int ctas, std::vector<std::vector<int4>>* per_out,
+                std::vector<std::vector<int>>* per_t_out, int* stride_out) {
     long long T = 0;
     for (const Seg& sg : segs) T += sg.z1 - sg.z0;
-    lp->n_planes = T;
-    lp->n_tissues = n_tissues;
     if (ctas > T) ctas = (int)std::max<long long>(T, 1);
-    std::vector<std::vector<int4>> per((size_t)ctas);
-    std::vector<std::vector<int>> per_t((size_t)ctas);
+    std::vector<std::vector<int4>>& per = *per_out;
+    std::vector<std::vector<int>>& per_t = *per_t_out;
+    per.assign((size_t)ctas, {});
+    per_t.assign((size_t)ctas, {});
     size_t si = 0;
     long long consumed = 0;
     int stride = 1;
@@ -539,6 +542,21 @@ int build_plan(LaunchPlan* lp, const std::vector<Seg>& segs, int n_tissues, int 
         }
         stride = std::max(stride, (int)per[(size_t)c].size());
     }
+    *stride_out = stride;
+    return ctas;
+}
+
+// The launch plan of a list of segments (plan_shares), uploaded; per grid,
+// the pieces are listed for the fixed-order totals.
+int build_plan(LaunchPlan* lp, const std::vector<Seg>& segs, int n_tissues, int ctas) {
+    long long T = 0;
+    for (const Seg& sg : segs) T += sg.z1 - sg.z0;
+    lp->n_planes = T;
+    lp->n_tissues = n_tissues;
+    std::vector<std::vector<int4>> per;
+    std::vector<std::vector<int>> per_t;
+    int stride = 1;
+    ctas = plan_shares(segs, ctas, &per, &per_t, &stride);
     // slot c*stride + i holds piece i of CTA c; unused slots stay zero
     const size_t nslot = (size_t)ctas * (size_t)stride;
     std::vector<int4> pieces(nslot, make_int4(0, 0, 0, 0));
@@ -801,6 +819,41 @@ int build_bricks(bbx_grid* g) {
     return BBX_OK;
 }
 
+// Masked 3D grid: in each band of ty rows by zb planes, the 16-wide chunks
+// that hold tissue (flags [bz][by][cx]) are covered from the left by 64-wide
+// pieces starting at a chunk (so a wall that crosses a 64-column boundary
+// costs one piece, not two); pieces with the same origin in consecutive bands
+// of a row band merge into one z-run.  Every tissue node lies in exactly one
+// piece.  Host-only.
+void cover_chunks(const uint8_t* flags, int ncx, int nby, int nbz, int ty, int zb, int nz, int tissue,
+                  std::vector<Seg>* segs) {
+    const int per = kTileX / kChunkX;
+    for (int by = 0; by < nby; ++by) {
+        std::map<int, std::vector<int>> runs;  // piece origin x0 -> bands bz holding a piece there
+        for (int bz = 0; bz < nbz; ++bz) {
+            const uint8_t* f = flags + ((size_t)bz * nby + by) * ncx;
+            for (int c = 0; c < ncx;) {
+                if (!f[c]) {
+                    ++c;
+                    continue;
+                }
+                runs[c * kChunkX].push_back(bz);
+                c += per;
+            }
+        }
+        for (const auto& kv : runs) {
+            const std::vector<int>& zs = kv.second;
+            size_t i = 0;
+            while (i < zs.size()) {
+                size_t j = i;
+                while (j + 1 < zs.size() && zs[j + 1] == zs[j] + 1) ++j;
+                segs->push_back({tissue, kv.first, by * ty, zs[i] * zb, std::min((zs[j] + 1) * zb, nz)});
+                i = j + 1;
+            }
+        }
+    }
+}
+
 // Active columns (64 x ty nodes) of a grid with their active z-runs, for the
 // given tile rows (the brick list must have been built for g->ty).
 void grid_segments(const bbx_grid* g, int tissue, std::vector<Seg>* segs) {
@@ -829,37 +882,8 @@ void grid_segments(const bbx_grid* g, int tissue, std::vector<Seg>* segs) {
             for (int bx = 0; bx < g->nbx; ++bx) segs->push_back({tissue, bx * kTileX, by * g->ty, 0, g->nz});
         return;
     }
-    // Masked 3D grid: in each band of ty rows by zb planes, the 16-wide chunks
-    // that hold tissue are covered from the left by 64-wide pieces starting
-    // at a chunk (so a wall that crosses a 64-column boundary costs one piece,
-    // not two); pieces with the same origin in consecutive bands of a row band
-    // merge into one z-run.  Every tissue node lies in exactly one piece.
-    const int ncx = (g->nx + kChunkX - 1) / kChunkX;
-    const int per = kTileX / kChunkX;
-    for (int by = 0; by < g->nby; ++by) {
-        std::map<int, std::vector<int>> runs;  // piece origin x0 -> bands bz holding a piece there
-        for (int bz = 0; bz < g->nbz; ++bz) {
-            const uint8_t* f = g->h_chunks.data() + ((size_t)bz * g->nby + by) * ncx;
-            for (int c = 0; c < ncx;) {
-                if (!f[c]) {
-                    ++c;
-                    continue;
-                }
-                runs[c * kChunkX].push_back(bz);
-                c += per;
-            }
-        }
-        for (const auto& kv : runs) {
-            const std::vector<int>& zs = kv.second;
-            size_t i = 0;
-            while (i < zs.size()) {
-                size_t j = i;
-                while (j + 1 < zs.size() && zs[j + 1] == zs[j] + 1) ++j;
-                segs->push_back({tissue, kv.first, by * g->ty, zs[i] * g->zb, std::min((zs[j] + 1) * g->zb, g->nz)});
-                i = j + 1;
-            }
-        }
-    }
+    cover_chunks(g->h_chunks.data(), (g->nx + kChunkX - 1) / kChunkX, g->nby, g->nbz, g->ty, g->zb, g->nz, tissue,
+                 segs);
 }
 
 // The kernel's view of a grid for tile rows `ty` (tensor maps depend on it).
@@ -2274,3 +2298,44 @@ int bbx_batch_info(bbx_batch* b, int* n_groups, int* tile_y, int cap) {
 }
 
 }  // extern "C"
+
+// Host-only test hooks (no device work): the piece covering of a masked 3D
+// grid and the CTA shares of a launch plan, as the library computes them.
+extern "C" int bbx_debug_cover_chunks(const uint8_t* flags, int ncx, int nby, int nbz, int ty, int zb, int nz,
+                                      int* out, int cap, int* count) {
+    if (!flags || !count || ncx <= 0 || nby <= 0 || nbz <= 0 || ty <= 0 || zb <= 0 || nz <= 0 || cap < 0 ||
+        (cap > 0 && !out))
+        return BBX_ERR_ARG;
+    std::vector<Seg> segs;
+    cover_chunks(flags, ncx, nby, nbz, ty, zb, nz, 0, &segs);
+    *count = (int)segs.size();
+    if ((int)segs.size() > cap) return BBX_ERR_ARG;
+    for (size_t i = 0; i < segs.size(); ++i) {
+        out[4 * i] = segs[i].x0;
+        out[4 * i + 1] = segs[i].y0;
+        out[4 * i + 2] = segs[i].z0;
+        out[4 * i + 3] = segs[i].z1;
+    }
+    return BBX_OK;
+}
+
+extern "C" int bbx_debug_plan_first_pieces(const int* segs4, int nsegs, int ctas, int* out, int cap, int* used) {
+    if (!segs4 || nsegs <= 0 || ctas <= 0 || !out || !used) return BBX_ERR_ARG;
+    std::vector<Seg> segs((size_t)nsegs);
+    for (int i = 0; i < nsegs; ++i)
+        segs[(size_t)i] = {0, segs4[4 * i], segs4[4 * i + 1], segs4[4 * i + 2], segs4[4 * i + 3]};
+    std::vector<std::vector<int4>> per;
+    std::vector<std::vector<int>> per_t;
+    int stride = 1;
+    const int n = plan_shares(segs, ctas, &per, &per_t, &stride);
+    *used = n;
+    if (n > cap) return BBX_ERR_ARG;
+    for (int c = 0; c < n; ++c) {
+        const int4 p = per[(size_t)c].empty() ? make_int4(0, 0, 0, 0) : per[(size_t)c][0];
+        out[4 * c] = p.x;
+        out[4 * c + 1] = p.y;
+        out[4 * c + 2] = p.z;
+        out[4 * c + 3] = p.w;
+    }
+    return BBX_OK;
+}
