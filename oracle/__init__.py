@@ -12,8 +12,12 @@ Parity status per function (see ``bbx_oracle.c`` for the passages):
   tests/test_oracle_output.py.
   Matrix Rush-Larsen (transition matrix of the Markov form of the BR sodium
   activation, the BR_MRL model): pinned by tests/test_oracle_markov.py.
-  Beeler-Reuter constants: PARITY UNPINNED (the paper does not print them;
-  transcribed from Beeler & Reuter 1977, checked only qualitatively).
+  Beeler-Reuter rates and currents: the paper does not print them
+  (transcribed from Beeler & Reuter 1977); pinned by physics and physiology
+  in tests/test_oracle_br.py (directions, windows, hierarchy, reversal
+  potentials, the whole-cell action potential), which catch gross slips of
+  one constant but not a small change: PARITY PARTIAL for the exact values
+  of the constants.
 """
 from __future__ import annotations
 

@@ -25,8 +25,10 @@
  *   - Beeler-Reuter                     named in section "Cell models"
  *                                       (ionic format); the equations and
  *                                       constants are Beeler & Reuter (1977).
- *                                       PARITY UNPINNED for the BR constants:
- *                                       the paper does not print them.
+ *                                       The paper does not print them;
+ *                                       physics/physiology pins catch gross
+ *                                       slips, not small ones: PARITY
+ *                                       PARTIAL for the constants' values.
  *   - matrix Rush-Larsen                Eq. (markov-generic) and the scheme
  *                                       u_{n+1} = T(V_n) u_n, T = exp(dt A(V_n))
  *                                       that follows it (section "Exponential

@@ -158,7 +158,11 @@ def _disc_run(h, off, T=0.2):
 @pytest.mark.slow
 def test_disc_convergence_slopes_like_the_paper():
     """Fig. discerror: errors converge faster than h^1, slower than h^2; the
-    paper's fitted slopes are 1.564 (Linf) and 1.719 (L2)."""
+    paper's fitted slopes are 1.564 (Linf) and 1.719 (L2).  The paper does
+    not print its h values, and with the staircase boundary the error is
+    not a smooth function of h (the four centre offsets scatter by 20-40 %
+    at one h), so the fitted slope depends on the h set: on h = 1/6 .. 1/16
+    the oracle fits 1.37 / 1.53, on 1/4 .. 1/32 1.28 / 1.55."""
     gd = _golden("disc_convergence.json")
     hs = [1 / 6, 1 / 8, 1 / 11, 1 / 16]
     offs = [(0, 0), (0.2, 0.2), (0.2, 0.6), (0.6, 0.6)]
@@ -171,6 +175,22 @@ def test_disc_convergence_slopes_like_the_paper():
     s2 = np.polyfit(np.log(H), np.log(E2), 1)[0]
     assert 1.0 < si < 2.0 and 1.0 < s2 < 2.2, (si, s2)
     assert abs(si - gd["slope_Linf"]) < 0.35 and abs(s2 - gd["slope_L2"]) < 0.35, (si, s2)
+    # The L2 norm converges faster than the Linf norm (the error is
+    # localised at the boundary), as the section states.
+    assert s2 > si
+
+
+@pytest.mark.slow
+def test_disc_error_halves_to_quarters_on_a_finer_grid():
+    """Fig. discerror's statement at finer grids than the slope fit: going
+    from h = 1/16 to 1/32 divides both error norms (mean over the four centre
+    offsets) by more than 2 (better than first order) and less than 4
+    (worse than second order)."""
+    offs = [(0, 0), (0.2, 0.2), (0.2, 0.6), (0.6, 0.6)]
+    e16 = np.mean([_disc_run(1 / 16, o) for o in offs], axis=0)
+    e32 = np.mean([_disc_run(1 / 32, o) for o in offs], axis=0)
+    r = e16 / e32
+    assert np.all(r > 2.0) and np.all(r < 4.0), r
 
 
 def _zfk_run(h, L=10.0, T=10.0, alpha=0.13, Dpar=2.0, Dperp=0.2, fib_deg=30.0, wave_deg=0.0,
