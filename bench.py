@@ -14,9 +14,14 @@ value:  cell-updates/s with the state resident in HBM, device-timed with CUDA
         left for the step to write back), outside the events.
 e2e:    the same metric through the C ABI with host buffers: every step
         writes u and v from pinned host memory, steps, and reads u and v back.
-Under torchrun each rank steps its own slab (independent replicas, no
-collective on the data path): weak scaling, value summed over ranks.
---impl reference times the FP64 CPU oracle on the host cores instead.
+Under torchrun the slab is N times as high (64 N planes) and cut into N
+z-slabs, one per rank (the paper's domain decomposition): every step each
+rank exchanges its one-plane V halo with its neighbours (NCCL send/recv)
+and steps its slab; weak scaling, value = all ranks' cells / slowest rank.
+The batch of tissues is split over the ranks (independent units).
+--impl reference times the FP64 CPU oracle on all host cores instead.
+cpu_baseline: the same oracle on all host cores (OpenMP over the node loops)
+and on one thread, on bounded samples of the slab.
 """
 from __future__ import annotations
 
@@ -124,21 +129,33 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_rate(w, steps, nz_sample=None):
-    """Oracle (FP64 CPU, single thread) cell-updates/s on a bounded sample:
-    `steps` steps in one call on the first nz_sample planes of the slab."""
-    import numpy as np
+def host_cores():
+    """Host cores this process may run on (the GPU machine's Grace cores)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_rate(w, steps, nz_sample=None, threads=1):
+    """Oracle (FP64 CPU) cell-updates/s on a bounded sample: `steps` steps in
+    one call on the first nz_sample planes of the slab, its node loops on
+    `threads` OpenMP threads (bit-identical results for any count)."""
     import oracle
     from paper_1605_06015_gb300 import workloads as wl
     if nz_sample is not None and nz_sample < w.nz:
         w = wl.barkley_slab(w.nx, w.ny, nz_sample)
-    og = oracle.Grid(w.nx, w.ny, w.nz, w.h, w.mask, w.fibres, w.D_par, w.D_perp)
-    st = w.initial_state(oracle.rest_state(w.model, w.params))
-    sim = oracle.Sim(og, w.model, par=w.params, state=st)
-    t0 = time.perf_counter()
-    sim.step(w.dt, steps)
-    dt = time.perf_counter() - t0
-    return w.n_active() * steps / dt, dt, w
+    used = oracle.set_threads(threads)
+    try:
+        og = oracle.Grid(w.nx, w.ny, w.nz, w.h, w.mask, w.fibres, w.D_par, w.D_perp)
+        st = w.initial_state(oracle.rest_state(w.model, w.params))
+        sim = oracle.Sim(og, w.model, par=w.params, state=st)
+        t0 = time.perf_counter()
+        sim.step(w.dt, steps)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(1)
+    return w.n_active() * steps / dt, dt, w, used
 
 
 def dist_setup():
@@ -173,51 +190,57 @@ def whole_job_rate(units_per_rank, steps, ws, seconds):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, on all host cores
+    (OpenMP node loops), one oracle call of one step of the full slab per
+    benchmark step (the call builds the stencil weights, then steps)."""
     rank, ws, local, dist = dist_setup()
     if rank != 0:
         return 0
     from paper_1605_06015_gb300 import workloads as wl
     w = wl.barkley_slab()
+    cores = host_cores()
     times = []
+    used = 1
     for i in range(args.warmup + args.steps):
-        rate, dt, ws_ = oracle_rate(w, 1, nz_sample=8)
+        rate, dt, _, used = oracle_rate(w, 1, threads=cores)
         if i >= args.warmup:
             times.append(dt)
-    cells = 256 * 256 * 8
     T = sum(times)
-    value = cells * args.steps / T
+    value = w.n_active() * args.steps / T
+    sample = "one oracle call of 1 step of the full 256x256x64 slab per benchmark step, %d threads" % used
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded)",
-            "config": {"workload": WORKLOAD_DESC, "sample": "first 8 z-planes (256x256x8) per step"},
-            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-                             "sample": "one oracle call of 1 step on the 256x256x8 sub-slab per benchmark step"},
+            "config": {"workload": WORKLOAD_DESC, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": used, "kind": "oracle",
+                             "sample": sample, "nproc": cores},
             "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_e2e(G, w, st0, S, args, dist, dev, ws, n_tissue):
+def run_e2e(G, w, st0, S, args, dist, dev, ws, n_tissue, step_fn=None):
     """Steps through the C ABI with host buffers: every step takes a new
     whole state from pinned host memory while the previous step's result goes
     back to pinned host memory (bbx_exchange_state: the two copies overlap),
     then steps once; the last step's result is read after the loop, inside
     the timed region."""
     import torch
+    step = step_fn or (lambda: G.step(w.dt, 1))
     pin_in = torch.from_numpy(st0[:S].copy()).pin_memory()
     pin_out = torch.empty(pin_in.shape, dtype=torch.float32).pin_memory()
     e2e_steps = max(3, min(args.steps, 20))
     for _ in range(2):
         G.exchange_state(pin_in, pin_out)
-        G.step(w.dt, 1)
+        step()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     e0 = time.perf_counter()
     for _ in range(e2e_steps):
         G.exchange_state(pin_in, pin_out)
-        G.step(w.dt, 1)
+        step()
     G.read_all(out=pin_out)
     torch.cuda.synchronize()
     e_wall = time.perf_counter() - e0
@@ -235,6 +258,19 @@ def initial_state(G, w):
     return w.initial_state(rest).astype(np.float32)
 
 
+def partition_tissues(cells, n_ranks):
+    """Split independent tissues (their node counts) over ranks, largest
+    first to the least loaded rank; returns each rank's tissue indices.  The
+    tissues are independent units of work, so no data crosses ranks."""
+    load = [0] * n_ranks
+    out = [[] for _ in range(n_ranks)]
+    for i in sorted(range(len(cells)), key=lambda k: (-cells[k], k)):
+        r = min(range(n_ranks), key=lambda q: (load[q], q))
+        out[r].append(i)
+        load[r] += cells[i]
+    return [sorted(o) for o in out]
+
+
 def run_batched(args, dev, stream, dist=None, n_ranks=1):
     """The batch of 256 independent tissues (192 FHN sheets with sides in
     64..512, 64 Barkley blocks with sides in 64..128, parameters swept by
@@ -244,7 +280,11 @@ def run_batched(args, dev, stream, dist=None, n_ranks=1):
     import torch
     from paper_1605_06015_gb300 import bbx
     from paper_1605_06015_gb300 import workloads as wl
-    ws = wl.tissue_batch(n2d=args.batch_2d, n3d=args.batch_3d)
+    ws_all = wl.tissue_batch(n2d=args.batch_2d, n3d=args.batch_3d)
+    rank = dist.get_rank() if dist else 0
+    share = partition_tissues([w.n_cells for w in ws_all], n_ranks)[rank]
+    ws = [ws_all[i] for i in share]  # this rank's tissues
+    cells_all = sum(w.n_cells for w in ws_all)
     grids = []
     for w in ws:
         G = bbx.Grid(w.nx, w.ny, w.nz, w.h, w.mask, stream=stream)
@@ -283,8 +323,10 @@ def run_batched(args, dev, stream, dist=None, n_ranks=1):
         G.close()
     return {"workload": "%d 2D FHN sheets (sides 64..512) + %d 3D Barkley blocks (sides 64..128), D and model "
                         "parameters swept +-20%%, isotropic" % (args.batch_2d, args.batch_3d),
-            "cells": cells, "steps": K, "value": whole_job_rate(cells, K, n_ranks, t_batch), "unit": "cell-updates/s",
-            "one_launch_per_grid_value": whole_job_rate(cells, K, n_ranks, t_solo),
+            "cells": cells_all, "cells_this_rank": cells, "tissues_this_rank": len(ws),
+            "partition": "tissues split over %d rank(s), largest first to the least loaded" % n_ranks,
+            "steps": K, "value": cells_all * K / t_batch, "unit": "cell-updates/s",
+            "one_launch_per_grid_value": cells_all * K / t_solo,
             "speedup_vs_one_launch_per_grid": t_solo / t_batch,
             "groups": info["n_groups"], "tile_y": info["tile_y"], "graph_steps_per_replay": 16}
 
@@ -406,6 +448,12 @@ def run_configs(args, dev, stream, dist=None, n_ranks=1):
                               "Beeler-Reuter slab 256x256x64, Rush-Larsen coefficients tabulated in V"),
         "br_shell_512_tab": (lambda: wl.br_shell(512), (2, 22),
                              "Beeler-Reuter shell in 512^3, Rush-Larsen coefficients tabulated in V"),
+        "br_shell_512_u16": (lambda: wl.br_shell(512), (2, 22),
+                             "Beeler-Reuter shell in 512^3, the six gates stored as 16-bit fixed point"),
+        "br_shell_512_f16": (lambda: wl.br_shell(512), (2, 22),
+                             "Beeler-Reuter shell in 512^3, the six gates stored as binary16"),
+        "br_256x256x64_u16": (lambda: wl.br_slab(256, 256, 64), (2, 22),
+                              "Beeler-Reuter slab 256x256x64, the six gates stored as 16-bit fixed point"),
     }
     out = {}
     for name in args.configs.split(","):
@@ -421,6 +469,9 @@ def run_configs(args, dev, stream, dist=None, n_ranks=1):
         if name.endswith("_tab"):
             G.set_tabulation(True)
         st = initial_state(G, w)
+        gates = {"_u16": bbx.BBX_GATES_UNORM16, "_f16": bbx.BBX_GATES_FP16}.get(name[-4:], bbx.BBX_GATES_FP32)
+        if gates != bbx.BBX_GATES_FP32:
+            G.set_gate_storage(gates)
         G.autotune(w.dt)
         G.write_all(st)
         del st
@@ -431,7 +482,8 @@ def run_configs(args, dev, stream, dist=None, n_ranks=1):
         info = G.get_info()
         cells = info["n_tissue"]
         S = info["nvars"]
-        b_alg = 2 * S * 4 + (12 if info["anisotropic"] else 0) + (1 if info["masked"] else 0)
+        state_bytes = S * 4 if gates == bbx.BBX_GATES_FP32 else 2 * 4 + 6 * 2  # V, Ca + six 16-bit gates
+        b_alg = 2 * state_bytes + (12 if info["anisotropic"] else 0) + (1 if info["masked"] else 0)
         G.step(w.dt, 2)
         secs = []
         for n in (n1, n2):
@@ -499,14 +551,29 @@ def run_bbx(args):
     from paper_1605_06015_gb300 import bbx
     from paper_1605_06015_gb300 import workloads as wl
 
-    w = wl.barkley_slab()
     stream = torch.cuda.current_stream()
-    G = bbx.Grid(w.nx, w.ny, w.nz, w.h, w.mask, stream=stream)
-    G.set_fibres(w.fibres, w.D_par, w.D_perp)
-    G.set_ionic_model(w.model, w.params)
-    G.set_threshold(w.theta)
-    st0 = initial_state(G, w)
-    G.write_all(st0)
+    slab = None
+    if ws == 1:
+        w = wl.barkley_slab()
+        G = bbx.Grid(w.nx, w.ny, w.nz, w.h, w.mask, stream=stream)
+        G.set_fibres(w.fibres, w.D_par, w.D_perp)
+        G.set_ionic_model(w.model, w.params)
+        G.set_threshold(w.theta)
+        st0 = initial_state(G, w)
+        G.write_all(st0)
+    else:
+        # N ranks: the slab 64 N planes high, cut into N z-slabs of 64 planes
+        # (the paper's domain decomposition), each rank's halo planes
+        # refreshed from its neighbours by NCCL sends and receives every step
+        from paper_1605_06015_gb300 import slabs
+        w = wl.barkley_slab(256, 256, 64 * ws)
+        slab = slabs.SlabGrid(w, ws, rank, stream=stream, device=dev)
+        G = slab.G
+        rest = [float(G.read_state(v).reshape(-1)[0]) for v in range(G.get_info()["nvars"])]
+        st_global = w.initial_state(rest).astype(np.float32)
+        slab.write_global_state(st_global)
+        st0 = np.ascontiguousarray(st_global[:, slab.a:slab.b])
+        del st_global
     if args.tile:
         ty, tz = (int(v) for v in args.tile.split(","))
         G.set_tiling(ty, tz)
@@ -529,9 +596,14 @@ def run_bbx(args):
         flush.fill_(val)
         torch.sum(flush_rd, dim=0, out=sink)
 
+    def one_step():
+        if slab is not None:
+            slab.exchange(dist, rank, ws)
+        G.step(w.dt, 1)
+
     for _ in range(args.warmup):
         flush_l2(1.0)
-        G.step(w.dt, 1)
+        one_step()
     torch.cuda.synchronize()
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -546,7 +618,7 @@ def run_bbx(args):
     for i in range(args.steps):
         flush_l2(float(i))
         starts[i].record(stream)
-        G.step(w.dt, 1)
+        one_step()
         ends[i].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
@@ -559,7 +631,7 @@ def run_bbx(args):
     ms_step = dev_ms / args.steps
     value = whole_job_rate(n_tissue, args.steps, ws, dev_ms * 1e-3)
 
-    e2e = None if args.no_e2e else run_e2e(G, w, st0, S, args, dist, dev, ws, n_tissue)
+    e2e = None if args.no_e2e else run_e2e(G, w, st0, S, args, dist, dev, ws, n_tissue, one_step)
 
 
     batched = None
@@ -576,17 +648,24 @@ def run_bbx(args):
     achieved = B_alg * n_tissue / (ms_step * 1e-3) / 1e9
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, secs, _ = oracle_rate(w, args.cpu_steps)
-        cpu = {"value": rate, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-               "sample": "%d steps of the full 256x256x64 slab in one oracle call (%.1f s, weights built once "
-                         "per call)" % (args.cpu_steps, secs)}
+        cores = host_cores()
+        rate1, secs1, _, _ = oracle_rate(w, args.cpu_steps, threads=1)
+        ratep, secsp, _, used = oracle_rate(w, args.cpu_steps_parallel, threads=cores)
+        cpu = {"value": ratep, "unit": "cell-updates/s", "cores": used, "kind": "oracle", "nproc": cores,
+               "sample": "%d steps of the full 256x256x64 slab in one oracle call on %d threads (%.1f s, "
+                         "weights built once per call)" % (args.cpu_steps_parallel, used, secsp),
+               "single_thread": {"value": rate1, "unit": "cell-updates/s", "cores": 1,
+                                 "sample": "%d steps of the full slab in one oracle call on 1 thread (%.1f s)"
+                                           % (args.cpu_steps, secs1)}}
     line = {
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
         "config": {"workload": WORKLOAD_DESC, "active_cells": n_tissue, "l2": "flushed between timed steps "
                    "(256 MiB write then 256 MiB read, outside the events)", "tile": [info["tile_x"], info["tile_y"], info["tile_z"]],
-                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+                   "parallelism": ("z-slabs of a 256x256x%d slab, one per rank, one-plane V halo exchanged by NCCL "
+                                   "send/recv every step (inside the timed region)" % (64 * ws)) if ws > 1
+                                  else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": load_traffic("barkley_slab_256x256x64"), "peak_kind": peak_kind,
                      "bytes_per_cell": B_alg},
@@ -604,7 +683,10 @@ def run_bbx(args):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    G.close()
+    if slab is not None:
+        slab.close()
+    else:
+        G.close()
     if dist:
         dist.destroy_process_group()
     return 0
@@ -617,6 +699,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="bbx", choices=["bbx", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=20)
+    ap.add_argument("--cpu-steps-parallel", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
@@ -626,7 +709,7 @@ def main():
     ap.add_argument("--tile", default=None, help="TY,TZ brick shape instead of autotuning")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--configs", default="fhn_200,fhn_16384,barkley_512x512x256,br_shell_512,br_256x256x64,br_mrl_256x256x64,"
-                            "br_256x256x64_tab,br_shell_512_tab",
+                            "br_256x256x64_tab,br_shell_512_tab,br_shell_512_u16,br_shell_512_f16,br_256x256x64_u16",
                     help="comma-separated other workloads to time by differencing ('' for none)")
     ap.add_argument("--surrogate-pairs", type=int, default=10_000_000)
     ap.add_argument("--surrogate-traj-steps", type=int, default=6000)

@@ -40,11 +40,12 @@ INT32_MAX = np.iinfo(np.int32).max
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain IEEE double: no fast-math, no FMA
-    contraction).  Returns the library path."""
+    contraction; OpenMP for the optional threaded node loops).  Returns the
+    library path."""
     os.makedirs(_LIBDIR, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -89,6 +90,8 @@ def lib():
         L.orc_mrl_transition.argtypes = [D, D, P]
         L.orc_run.argtypes = [P, P, P, D, I, P, P, P]
         L.orc_run.restype = I
+        L.orc_set_threads.argtypes = [I]
+        L.orc_set_threads.restype = I
         L.orc_step_cells.argtypes = [P, P, P, D, D, P, I, P]
         L.orc_step_cells.restype = I
         L.orc_total.argtypes = [P, P]
@@ -97,6 +100,13 @@ def lib():
         L.orc_active_bricks.restype = ctypes.c_longlong
         _lib = L
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads for the whole-grid loops of Sim.step (1 = serial, the
+    default).  Results are bit-identical for any count.  Returns the count in
+    use."""
+    return lib().orc_set_threads(int(n))
 
 
 def _ptr(a):

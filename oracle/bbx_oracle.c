@@ -6,7 +6,12 @@
  * leg of bench.py use it.  It shares no code, header, table or constant with
  * the CUDA library in paper_1605_06015_gb300/csrc.
  *
- * Plain, slow, single-threaded C in double precision.  Every function follows
+ * Plain, slow C in double precision, single-threaded unless orc_set_threads
+ * asks for more: then the two node loops of orc_run (diffusion terms, then
+ * updates) are shared among OpenMP threads.  Each node's arithmetic is the
+ * same in either case, so results are bit-identical for any thread count;
+ * the threads only serve timing on the host cores and long parity runs.
+ * Every function follows
  * one passage of the paper (arXiv:1605.06015, "BeatBox - HPC simulation
  * environment ...") and names it:
  *
@@ -591,6 +596,20 @@ static void node_update(const orc_run_cfg* c, const double* y, double L, double 
  * not yet), may be NULL.  The weights are built once per call (they depend
  * only on geometry), then every step first evaluates L on all tissue nodes
  * from the old state and then updates every tissue node. */
+static int orc_threads = 1;
+
+/* Threads for the node loops of orc_run (1 = serial, the default); returns
+ * the count in use (1 when the oracle was built without OpenMP). */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    orc_threads = n < 1 ? 1 : n;
+#else
+    (void)n;
+    orc_threads = 1;
+#endif
+    return orc_threads;
+}
+
 int orc_run(const orc_geom* g, const orc_run_cfg* c, double* state, double dt, int n_steps,
             double* t, long long* n, int32_t* act) {
     const size_t N = (size_t)g->nx * g->ny * g->nz;
@@ -612,15 +631,23 @@ int orc_run(const orc_geom* g, const orc_run_cfg* c, double* state, double dt, i
             for (int x = 0; x < g->nx; x++)
                 if (psi_at(g, x, y, z)) {
                     cx[3 * m] = x; cx[3 * m + 1] = y; cx[3 * m + 2] = z;
-                    orc_cell_weights(g, x, y, z, W + 27 * m);
                     m++;
                 }
-    double y[ORC_MAXS], yn[ORC_MAXS];
+    const int nth = orc_threads;
+    const long long ntl = (long long)nt;
+    (void)nth;
+#pragma omp parallel for schedule(static) num_threads(nth) if (nth > 1)
+    for (long long i = 0; i < ntl; i++) orc_cell_weights(g, cx[3 * i], cx[3 * i + 1], cx[3 * i + 2], W + 27 * i);
     for (int s = 0; s < n_steps; s++) {
         int on = c->amp != 0.0 && *t >= c->t_on && *t < c->t_off;
-        for (size_t i = 0; i < nt; i++)
+        /* every diffusion term from the old state first ... */
+#pragma omp parallel for schedule(static) num_threads(nth) if (nth > 1)
+        for (long long i = 0; i < ntl; i++)
             L[i] = apply_weights(g, W + 27 * i, state, cx[3 * i], cx[3 * i + 1], cx[3 * i + 2]);
-        for (size_t i = 0; i < nt; i++) {
+        /* ... then every node's update, each touching only its own node */
+#pragma omp parallel for schedule(static) num_threads(nth) if (nth > 1)
+        for (long long i = 0; i < ntl; i++) {
+            double y[ORC_MAXS], yn[ORC_MAXS];
             size_t p = gidx(g, cx[3 * i], cx[3 * i + 1], cx[3 * i + 2]);
             for (int v = 0; v < S; v++) y[v] = state[(size_t)v * N + p];
             double Is = (on && c->stim && c->stim[p]) ? c->amp : 0.0;

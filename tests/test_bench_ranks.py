@@ -63,3 +63,16 @@ def test_two_gloo_ranks_combine_by_the_slowest_rank(tmp_path):
     assert line["impl"] == "reference" and line["value"] > 0 and line["n_gpus"] == 2
     assert line["cpu_baseline"]["kind"] == "oracle"
     assert res[1]["ref_out"] == ""
+
+
+def test_tissue_partition_balances_and_covers_every_tissue():
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1605_06015_gb300 import workloads as wl
+    cells = [w.n_cells for w in wl.tissue_batch()]
+    for n in (1, 2, 3, 8):
+        parts = bench.partition_tissues(cells, n)
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(len(cells)))  # every tissue on exactly one rank
+        loads = [sum(cells[i] for i in p) for p in parts]
+        assert max(loads) - min(loads) <= max(cells)  # greedy bound: within one tissue
