@@ -312,6 +312,72 @@ int bbx_autotune(bbx_grid* g, double dt, double* best_ms);
  * BBX_ERR_STATE (no model), BBX_ERR_ARG (dt <= 0), BBX_ERR_UNSTABLE. */
 int bbx_set_timestep(bbx_grid* g, double dt);
 
+/* Storage of the Beeler-Reuter gates between steps (bbx_set_gate_storage). */
+#define BBX_GATES_FP32 0    /* 32-bit floats (default) */
+#define BBX_GATES_FP16 1    /* IEEE binary16, round to nearest */
+#define BBX_GATES_UNORM16 2 /* 16-bit unsigned fixed point y = u / 65535, round to nearest */
+
+/* Store the six gates of a Beeler-Reuter grid (x1, m, h, j, d, f; variables
+ * 2..7) in 16 bits instead of 32 between steps: the precision path of a
+ * state whose gates are fractions in [0, 1].  V and Ca stay 32-bit, every
+ * operation of the step stays FP32 (the gates are decoded when the tile is
+ * read, and the new values rounded to nearest when stored), so a node-update
+ * moves 2 (4 + 4 + 6 x 2) bytes of state instead of 2 (8 x 4).
+ * BBX_GATES_FP16 has steps of 2^-11 just below 1: a slow gate (f, j, x1)
+ * whose Rush-Larsen increment per step is below half a step there stops
+ * moving (at dt = 0.02 ms the cell then never repolarises);
+ * BBX_GATES_UNORM16 has uniform steps of 1/65535 over [0, 1] and keeps the
+ * step within the parity bars.  The current state is converted (read and
+ * written back in the new layout).  Device layout with 16 bits: V and Ca
+ * planes of floats, then six planes of uint16, [var][z][y][px]; buffers bound
+ * by bbx_bind_state need 5 nz ny px floats.  bbx_read_state / bbx_write_state
+ * and the whole-state copies convert to and from float; bbx_state_device_ptr
+ * returns a uint16 plane for a gate.  With 16-bit gates the grid is stepped
+ * alone (no batch), on 7- or 14-row tiles, without surrogate (the Lie scheme
+ * and tabulated coefficients are kept), and bbx_total, bbx_ppm_frame and
+ * bbx_phase_singularities refuse gate variables (BBX_ERR_UNSUPPORTED).  Setting a model resets the storage
+ * to FP32.  Errors: BBX_ERR_ARG (mode), BBX_ERR_STATE (no model, or bound
+ * buffers too small), BBX_ERR_UNSUPPORTED (not BBX_BR, or the settings
+ * above), BBX_ERR_NOMEM. */
+int bbx_set_gate_storage(bbx_grid* g, int mode);
+
+/* ---- z-slab decomposition (section "Domain partitioning") --------------- */
+/* The paper's parallel layer cuts the grid into subdomains that exchange a
+ * one-node layer of the diffusing variable with their neighbours before
+ * every step (the exchange buffers around each subdomain, figure domdec).
+ * Here a grid of nz_global planes is cut along z into slabs; each slab is its
+ * own bbx_grid holding its planes plus one halo plane on every side that
+ * has a neighbour slab, with the mask and fibres of those planes (from the
+ * global grid).  Only V diffuses, so only V's halo plane is refreshed.
+ *
+ * bbx_set_halo_planes: lo, hi in {0, 1}: the first lo and last hi planes of g
+ * are halo planes: the stencil reads them as the neighbours they are, the
+ * step never computes them (no update, activation, stimulus or tissue sum
+ * there); bbx_total and bbx_get_info's n_tissue count only the slab's own
+ * planes.  Default 0, 0.  Errors: BBX_ERR_ARG (values, or nz <= lo + hi).
+ *
+ * bbx_halo_exchange: refresh the halo planes between two slabs of one
+ * device, lower directly below upper (lower has hi = 1, upper lo = 1, same
+ * nx and ny): upper's lowest own V plane goes into lower's top halo plane
+ * and lower's highest own V plane into upper's bottom halo plane, both in
+ * the buffers the next steps read (2 nx ny floats, row-pitched).
+ * Asynchronous, on lower's stream (after upper's enqueued work, and
+ * upper's later work waits for it when the streams differ).  Call it
+ * between the steps of the two slabs, once per step.  Errors: BBX_ERR_ARG,
+ * BBX_ERR_STATE (no model, no halo plane on the facing sides), BBX_ERR_CUDA.
+ *
+ * bbx_halo_plane: for slabs on different GPUs, the device address of one V
+ * plane of the buffer the next step reads: side 0 = low z, 1 = high z; halo
+ * = 1: the halo plane to receive into, 0: the slab's own boundary plane to
+ * send.  *bytes (may be NULL) = the plane's size (ny rows of px floats).
+ * The caller moves the planes (NCCL send/recv, peer copies) on the grid's
+ * stream before the next step; the address changes with every step.
+ * Errors: BBX_ERR_ARG, BBX_ERR_STATE (no model, no halo plane on that
+ * side). */
+int bbx_set_halo_planes(bbx_grid* g, int lo, int hi);
+int bbx_halo_exchange(bbx_grid* lower, bbx_grid* upper);
+int bbx_halo_plane(bbx_grid* g, int side, int halo, void** dev_ptr, size_t* bytes);
+
 /* ---- batches of independent grids ------------------------------------- */
 /* Many independent grids of uneven sizes and parameters (parameter sweeps)
  * advanced together.  Grids of one kernel type (model, masked, anisotropic)
@@ -433,9 +499,13 @@ int bbx_clear_device_error(bbx_grid* g);
  * double on the device, written when the work enqueued on cuda_stream runs.
  * No device memory is allocated or freed.  Limits: nx*ny*nz <= 2^28 nodes,
  * else BBX_ERR_ARG.  The first call on a device looks up the scratch array's
- * device address (make that first call before any stream capture).  All
- * calls share the scratch, so calls that overlap on the GPU (concurrent
- * streams) race; serialise them.  Errors: BBX_ERR_ARG, BBX_ERR_CUDA. */
+ * device address (make that first call before any stream capture); it is
+ * looked up again when the device's context changes (after cudaDeviceReset).
+ * All calls share the scratch, so calls that overlap on the GPU (concurrent
+ * streams) race; serialise them.  An error already pending from the
+ * caller's earlier CUDA work makes the call return BBX_ERR_CUDA and is left
+ * in place, not cleared.  Errors: BBX_ERR_ARG (checked before any CUDA
+ * call), BBX_ERR_CUDA. */
 int bbx_total_noalloc(const float* field_dev, const uint8_t* mask_dev, int nx, int ny, int nz, int pitch,
                       double* out_dev, void* cuda_stream);
 

@@ -32,6 +32,7 @@ NVARS = {BBX_FHN: 2, BBX_BARKLEY: 2, BBX_BR: 8, BBX_ZFK: 1, BBX_DIFFUSION: 1, BB
 BBX_ACT_NONE = 2147483647
 BBX_SCHEME_UNSPLIT, BBX_SCHEME_LIE = 0, 1
 BBX_SOLVER_EULER, BBX_SOLVER_RK4 = 0, 1
+BBX_GATES_FP32, BBX_GATES_FP16, BBX_GATES_UNORM16 = 0, 1, 2
 
 
 class BbxError(RuntimeError):
@@ -93,6 +94,10 @@ def _load():
         "bbx_batch_sync": [P],
         "bbx_batch_autotune": [P, ctypes.POINTER(D)],
         "bbx_batch_info": [P, ctypes.POINTER(I), ctypes.POINTER(I), I],
+        "bbx_set_gate_storage": [P, I],
+        "bbx_set_halo_planes": [P, I, I],
+        "bbx_halo_exchange": [P, P],
+        "bbx_halo_plane": [P, I, I, ctypes.POINTER(P), ctypes.POINTER(Z)],
         "bbx_total_noalloc": [P, P, I, I, I, I, P, P],
         "bbx_mlp_create": [ctypes.POINTER(P), ctypes.c_ulonglong, P],
         "bbx_mlp_set_params": [P, P, Z],
@@ -449,6 +454,26 @@ def bbx_batch_info(b):
 
 def bbx_batch_destroy(b):
     _lib.bbx_batch_destroy(b)
+
+
+def bbx_set_gate_storage(g, mode):
+    _check(_lib.bbx_set_gate_storage(g, int(mode)), "bbx_set_gate_storage")
+
+
+def bbx_set_halo_planes(g, lo, hi):
+    _check(_lib.bbx_set_halo_planes(g, int(lo), int(hi)), "bbx_set_halo_planes")
+
+
+def bbx_halo_exchange(lower, upper):
+    _check(_lib.bbx_halo_exchange(lower, upper), "bbx_halo_exchange")
+
+
+def bbx_halo_plane(g, side, halo):
+    """(device address, bytes) of one V plane of the buffer the next step reads."""
+    p = ctypes.c_void_p()
+    n = ctypes.c_size_t()
+    _check(_lib.bbx_halo_plane(g, int(side), int(halo), ctypes.byref(p), ctypes.byref(n)), "bbx_halo_plane")
+    return p.value, n.value
 
 
 def bbx_total_noalloc(field_dev, mask_dev, nx, ny, nz, pitch, out_dev, stream=None):

@@ -25,6 +25,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include "../../include/bbx.h"
@@ -53,10 +54,12 @@ struct TissueDyn {
 // so that one launch, or one graph node, can serve any number of grids).
 struct TissueArgs {  // (CUtensorMap members impose its alignment)
     CUtensorMap tm_u[2];  // V of buffer b with halo (box TX+8 x TY+2)
-    CUtensorMap tm_s[2];  // non-diffusing variables of buffer b (box TX x TY x S-1)
+    CUtensorMap tm_s[2];  // non-diffusing variables of buffer b (box TX x TY x S-1; with 16-bit gates: Ca only)
+    CUtensorMap tm_g[2];  // 16-bit gates of buffer b (box TX x TY x 6 uint16), when stored so
     CUtensorMap tm_f;     // unit fibres, x stored from -4 with clamped padding
     CUtensorMap tm_m;     // tissue mask bytes
-    float* state[2];      // the ping-pong buffers, var v at state[b] + v*vol
+    float* state[2];      // the ping-pong buffers, var v at state[b] + v*vol (32-bit variables)
+    uint16_t* gate16[2];  // 16-bit gates: gate g (variable 2 + g) at gate16[b] + g*vol, or nullptr
     int32_t* act;         // activation steps
     const uint8_t* stim;  // stimulus region (nullptr: none)
     TissueDyn* dyn;
@@ -111,6 +114,7 @@ struct LaunchArgs {
     int cur_hint;
     int reg_len, reg_nbx, reg_ty, reg_ctas;  // column length (nz), columns in x, tile rows, CTAs
     long long reg_planes;                    // column-planes of the schedule
+    int reg_z0;                              // first computed plane of every column (0; 1 below a halo plane)
 };
 
 struct Coef {
@@ -639,9 +643,44 @@ constexpr int align128(int b) { return (b + 127) & ~127; }
 // 18 stencil neighbours are all tissue inside the array ("interior").
 enum : uint8_t { MASK_TISSUE = 1, MASK_INTERIOR = 2 };
 
-template <int MODEL, bool MASKED, bool ANISO, int TY, bool SURR = false>
+// Storage of the Beeler-Reuter gates (variables 2..7) between steps: FP32
+// (default), IEEE binary16, or 16-bit unsigned fixed point y = u / 65535
+// (uniform steps of 1.5e-5 over [0, 1]); arithmetic is FP32 in every case,
+// the new values rounded to nearest when stored.
+enum : int { GATES_F32 = 0, GATES_F16 = 1, GATES_U16 = 2 };
+
+template <int GATES>
+__device__ __forceinline__ float2 gate_decode2(uint32_t w) {
+    if (GATES == GATES_F16) {
+        __half2 h = *reinterpret_cast<__half2*>(&w);
+        return __half22float2(h);
+    }
+    constexpr float k = 1.0f / 65535.0f;
+    return make_float2((float)(w & 0xffffu) * k, (float)(w >> 16) * k);
+}
+
+template <int GATES>
+__device__ __forceinline__ uint16_t gate_encode(float y) {
+    if (GATES == GATES_F16) return __half_as_ushort(__float2half_rn(y));
+    return (uint16_t)__float2uint_rn(__saturatef(y) * 65535.0f);
+}
+
+template <int GATES>
+__device__ __forceinline__ uint32_t gate_encode2(float lo, float hi) {
+    return (uint32_t)gate_encode<GATES>(lo) | ((uint32_t)gate_encode<GATES>(hi) << 16);
+}
+
+__device__ __forceinline__ void st_global_u32(uint16_t* p, uint32_t v) {
+    asm volatile("st.global.u32 [%0], %1;" ::"l"(p), "r"(v));
+}
+__device__ __forceinline__ void st_global_u16(uint16_t* p, uint16_t v) {
+    asm volatile("st.global.u16 [%0], %1;" ::"l"(p), "h"(v));
+}
+
+template <int MODEL, bool MASKED, bool ANISO, int TY, bool SURR = false, int GATES = GATES_F32>
 struct Plan {
     static constexpr int S = Model<MODEL>::S;
+    static constexpr int NG = GATES ? 6 : 0;  // variables stored in 16 bits (the gates, last in the state)
     static constexpr int TX = kTileX;
     static constexpr int RY = rows_of_threads(TY);
     static constexpr int CTAS = ctas_per_sm(MASKED, ANISO, TY, SURR);
@@ -653,11 +692,14 @@ struct Plan {
     static constexpr int U_RAW = UW * UH * 4;
     static constexpr int F_RAW = ANISO ? 3 * UW * UH * 4 : 0;
     static constexpr int M_RAW = MASKED ? MW * UH : 0;
-    static constexpr int S_RAW = (S > 1) ? (S - 1) * TX * TY * 4 : 0;
+    static constexpr int S32_RAW = (S > 1) ? (S - 1 - NG) * TX * TY * 4 : 0;  // 32-bit non-diffusing variables
+    static constexpr int G_RAW = NG * TX * TY * 2;                              // 16-bit gates
+    static constexpr int S_RAW = S32_RAW + G_RAW;
     static constexpr int U_OFF = 0;
     static constexpr int F_OFF = U_OFF + align128(U_RAW);
     static constexpr int M_OFF = F_OFF + align128(F_RAW);
     static constexpr int S_OFF = M_OFF + align128(M_RAW);
+    static constexpr int G_OFF = S_OFF + S32_RAW;  // (S32_RAW is a multiple of 128)
     static constexpr int STAGE = S_OFF + align128(S_RAW);
     static constexpr uint32_t TX_BYTES = U_RAW + F_RAW + M_RAW + S_RAW;  // plane computed in this piece
     static constexpr uint32_t TX_BYTES_HALO = U_RAW + F_RAW + M_RAW;     // z-halo plane: no other vars
@@ -936,6 +978,7 @@ struct PieceSlot : Coef {
     int nx, ny, nz, px;
     long long plane, vol;
     float* dst;
+    uint16_t* dst16;  // the 16-bit gates of the buffer written (nullptr: all variables 32-bit)
     int32_t* act;
     const uint8_t* stim;
     float stim_amp, dt, theta;
@@ -991,10 +1034,13 @@ __device__ __forceinline__ int tile_row_of(int4 pc, int off) {
 // rings: full[s] completes when the plane's bulk copies have landed, empty[s]
 // when all RY consumer warps are done with the plane.  No CTA-wide barrier is
 // taken per plane.
-template <int MODEL, bool MASKED, bool ANISO, int TY, bool SURR = false, bool PLANAR = false, bool GEN = false>
+template <int MODEL, bool MASKED, bool ANISO, int TY, bool SURR = false, bool PLANAR = false, bool GEN = false,
+          int GATES = GATES_F32>
 __global__ void __launch_bounds__(32 * rows_of_threads(TY) + 32, ctas_per_sm(MASKED, ANISO, TY, SURR))
 step_kernel(const __grid_constant__ LaunchArgs L) {
-    using P = Plan<MODEL, MASKED, ANISO, TY, SURR>;
+    using P = Plan<MODEL, MASKED, ANISO, TY, SURR, GATES>;
+    static_assert(GATES == GATES_F32 || (MODEL == BBX_BR && !SURR), "16-bit gates: Beeler-Reuter without surrogate");
+    constexpr int NG = P::NG, S32 = P::S - NG;  // 16-bit variables last
     constexpr int S = P::S, TX = P::TX, UW = P::UW, MW = P::MW, NS = P::NS, CY = P::CY;
     constexpr int NCW = P::RY;  // consumer warps
     constexpr int NCT = 32 * NCW;        // consumer threads
@@ -1055,8 +1101,8 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                 const long long p0 = (long long)blockIdx.x * L.reg_planes / L.reg_ctas;
                 const long long p1 = ((long long)blockIdx.x + 1) * L.reg_planes / L.reg_ctas;
                 if (p1 > p0) {
-                    const int col = (int)(p0 / L.reg_len), z0 = (int)(p0 % L.reg_len);
-                    const int z1 = (int)min((long long)L.reg_len, z0 + (p1 - p0));
+                    const int col = (int)(p0 / L.reg_len), z0 = L.reg_z0 + (int)(p0 % L.reg_len);
+                    const int z1 = (int)min((long long)(L.reg_z0 + L.reg_len), z0 + (p1 - p0));
                     pc_early = make_int4((col % L.reg_nbx) * TX, (col / L.reg_nbx) * L.reg_ty, z0, z1);
                     early = true;
                     const TissueArgs* T = &L.t0;
@@ -1076,6 +1122,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                         if (ANISO) tma_load_4d(st + P::F_OFF, &T->tm_f, pc_early.x, y0 - 1, z, 0, bar);
                         if (MASKED) tma_load_3d(st + P::M_OFF, &T->tm_m, pc_early.x - 16, y0 - 1, z, bar);
                         if (S > 1 && !halo) tma_load_4d(st + P::S_OFF, &T->tm_s[src], pc_early.x, y0, z, 1, bar);
+                        if (NG && !halo) tma_load_4d(st + P::G_OFF, &T->tm_g[src], pc_early.x, y0, z, 0, bar);
                     }
                 }
             }
@@ -1119,6 +1166,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                         r.nx = T->nx; r.ny = T->ny; r.nz = nz; r.px = T->px;
                         r.plane = T->plane; r.vol = T->vol;
                         r.dst = T->state[src ^ 1];
+                        r.dst16 = T->gate16[src ^ 1];
                         r.act = T->act;
                         r.stim = T->stim;
                         r.stim_amp = (T->stim && T->stim_amp != 0.0f && tn >= T->t_on && tn < T->t_off) ? T->stim_amp
@@ -1149,6 +1197,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                         if (ANISO) tma_load_4d(st + P::F_OFF, &T->tm_f, pc.x, y0 - 1, z, 0, bar);  // fibre x offset 4
                         if (MASKED) tma_load_3d(st + P::M_OFF, &T->tm_m, pc.x - 16, y0 - 1, z, bar);
                         if (S > 1 && !halo) tma_load_4d(st + P::S_OFF, &T->tm_s[src], pc.x, y0, z, 1, bar);
+                        if (NG && !halo) tma_load_4d(st + P::G_OFF, &T->tm_g[src], pc.x, y0, z, 0, bar);
                     }
                     ++issued;
                 }
@@ -1364,10 +1413,18 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
     #pragma unroll
                         for (int e = 0; e < 2; ++e) yv[e][0] = u0r[r][e];
     #pragma unroll
-                        for (int v = 1; v < S; ++v) {
+                        for (int v = 1; v < S32; ++v) {
                             const float2 sv = *reinterpret_cast<const float2*>(Sv + (v - 1) * TX * TY + (row0 + r) * TX + 2 * tx);
                             yv[0][v] = sv.x;
                             yv[1][v] = sv.y;
+                        }
+    #pragma unroll
+                        for (int v = S32; v < S; ++v) {  // 16-bit gates, decoded to FP32
+                            const uint32_t w = *reinterpret_cast<const uint32_t*>(
+                                stc + P::G_OFF + 2 * ((v - S32) * TX * TY + (row0 + r) * TX + 2 * tx));
+                            const float2 gv = gate_decode2<GATES>(w);
+                            yv[0][v] = gv.x;
+                            yv[1][v] = gv.y;
                         }
                             float Isr[2];
 #pragma unroll
@@ -1446,14 +1503,23 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                         }
                         if (live[r][0] && live[r][1]) {
     #pragma unroll
-                            for (int v = 0; v < S; ++v)
+                            for (int v = 0; v < S32; ++v)
                                 st_global(a.dst + (long long)v * a.vol + gi, make_float2(yv[0][v], yv[1][v]));
+    #pragma unroll
+                            for (int v = S32; v < S; ++v)
+                                st_global_u32(a.dst16 + (long long)(v - S32) * a.vol + gi,
+                                              gate_encode2<GATES>(yv[0][v], yv[1][v]));
                         } else if (live[r][0] || live[r][1]) {
     #pragma unroll
                             for (int e = 0; e < 2; ++e)
-                                if (live[r][e])
+                                if (live[r][e]) {
     #pragma unroll
-                                    for (int v = 0; v < S; ++v) st_global(a.dst + (long long)v * a.vol + gi + e, yv[e][v]);
+                                    for (int v = 0; v < S32; ++v) st_global(a.dst + (long long)v * a.vol + gi + e, yv[e][v]);
+    #pragma unroll
+                                    for (int v = S32; v < S; ++v)
+                                        st_global_u16(a.dst16 + (long long)(v - S32) * a.vol + gi + e,
+                                                      gate_encode<GATES>(yv[e][v]));
+                                }
                         }
     #pragma unroll
                         for (int e = 0; e < 2; ++e) {

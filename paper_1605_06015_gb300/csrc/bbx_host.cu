@@ -24,6 +24,7 @@ StepKernel step_kernel_br_mrl(bool masked, bool aniso, int ty, bool planar, bool
 cudaError_t mrl_build_table(float4* tab, double dt, cudaStream_t s);
 cudaError_t br_build_rl_table(float4* tab, double dt, cudaStream_t s);
 StepKernel step_kernel_br_surrogate(bool masked, bool aniso, int ty);
+StepKernel step_kernel_br16(bool masked, bool aniso, int ty, bool planar, bool general, int gates);
 cudaError_t launch_ppm(const float* s0, const float* s1, const int* cur, const uint8_t* mask, long long vol, int nx,
                        int ny, int nz, int px, long long plane, const int layer[3], const float lo[3],
                        const float hi[3], uint8_t* out, int num_sms, cudaStream_t s);
@@ -94,7 +95,11 @@ void model_kernel_params(int model, const double* p, float* mp) {
 // planar: a grid with nz = 1 (sheet kernels, tiles marched along y).  The
 // surrogate kernels exist for 3D grids only.  general: the grid uses the Lie
 // scheme or the RK4 solver (kernels for 7- and 14-row tiles).
-StepKernel lookup_kernel(int model, bool masked, bool aniso, int ty, bool surrogate, bool planar, bool general) {
+StepKernel lookup_kernel(int model, bool masked, bool aniso, int ty, bool surrogate, bool planar, bool general,
+                         int gates = GATES_F32) {
+    if (gates != GATES_F32)  // 16-bit gates: Beeler-Reuter without surrogate
+        return model == BBX_BR && !surrogate ? step_kernel_br16(masked, aniso, ty, planar, general, gates)
+                                             : StepKernel{nullptr, 0, 0, 0};
     if (surrogate)
         return model == BBX_BR && !planar ? step_kernel_br_surrogate(masked, aniso, ty) : StepKernel{nullptr, 0, 0, 0};
     switch (model) {
@@ -171,6 +176,54 @@ __global__ void k_fibres(const float* __restrict__ in, int nx, int ny, int nz, i
         out[o] = ox;
         out[fvol + o] = oy;
         out[2 * fvol + o] = oz;
+    }
+}
+
+// The W-tilde ingredient of the weights (section "Monodomain diffusion and
+// boundary conditions"): per tissue node p, S_k = sum_j (f_j f_k at p + q_j
+// minus at p - q_j), f the unit fibre, with a void or out-of-array neighbour's
+// fibre replaced by f at p (D^p in place of its tensor; the D_perp parts of
+// D cancel in the difference).  The fibre field is fixed, so the three sums
+// are computed once, in double precision, and read by every step.  Layout
+// [3][nz][ny][px]; 0 at void nodes.
+__global__ void k_divergence(const float* __restrict__ fib, int nx, int ny, int nz, int pxf, long long fplane,
+                             long long fvol, const uint8_t* __restrict__ mask, int px, long long plane,
+                             long long vol, float* __restrict__ div) {
+    const long long n = (long long)nx * ny * nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = int(i % nx);
+        const long long r = i / nx;
+        const int y = int(r % ny);
+        const int z = int(r / ny);
+        const long long o = z * plane + (long long)y * px + x;
+        auto tissue = [&](int xx, int yy, int zz) {
+            if (xx < 0 || yy < 0 || zz < 0 || xx >= nx || yy >= ny || zz >= nz) return false;
+            return mask ? (mask[zz * plane + (long long)yy * px + xx] & 1) != 0 : true;
+        };
+        auto fibre = [&](int xx, int yy, int zz, double* f) {
+            const long long q = zz * fplane + (long long)yy * pxf + (xx + 4);
+            f[0] = fib[q];
+            f[1] = fib[fvol + q];
+            f[2] = fib[2 * fvol + q];
+        };
+        double acc[3] = {0.0, 0.0, 0.0};
+        if (tissue(x, y, z)) {
+            double fp[3];
+            fibre(x, y, z, fp);
+            for (int j = 0; j < 3; ++j) {
+                for (int sgn = -1; sgn <= 1; sgn += 2) {
+                    int c[3] = {x, y, z};
+                    c[j] += sgn;
+                    double fn[3] = {fp[0], fp[1], fp[2]};
+                    if (tissue(c[0], c[1], c[2])) fibre(c[0], c[1], c[2], fn);
+                    for (int k = 0; k < 3; ++k) acc[k] += sgn * fn[j] * fn[k];
+                }
+            }
+        }
+        div[o] = (float)acc[0];
+        div[vol + o] = (float)acc[1];
+        div[2 * vol + o] = (float)acc[2];
     }
 }
 
@@ -321,6 +374,40 @@ __global__ void k_fill_state(float* __restrict__ st, int S, long long vol, const
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
         st[i] = rest[i / vol];
+}
+
+// 16-bit gate storage (Beeler-Reuter): V and Ca as float planes, then the
+// six gates as uint16 planes (binary16 or fixed point u / 65535).
+__device__ __forceinline__ uint16_t enc16(float y, int mode) {
+    if (mode == GATES_F16) return __half_as_ushort(__float2half_rn(y));
+    return (uint16_t)__float2uint_rn(__saturatef(y) * 65535.0f);
+}
+__device__ __forceinline__ float dec16(uint16_t u, int mode) {
+    if (mode == GATES_F16) return __half2float(__ushort_as_half(u));
+    return (float)u * (1.0f / 65535.0f);
+}
+
+// Every node of a buffer to the rest state (in the buffer's layout).
+__global__ void k_fill_state16(float* __restrict__ st, long long vol, const float* __restrict__ rest, int mode) {
+    uint16_t* g16 = reinterpret_cast<uint16_t*>(st + 2 * vol);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < vol;
+         i += (long long)gridDim.x * blockDim.x) {
+        st[i] = rest[0];
+        st[vol + i] = rest[1];
+        for (int g = 0; g < 6; ++g) g16[g * vol + i] = enc16(rest[2 + g], mode);
+    }
+}
+
+// One 16-bit plane of variable-sized data to and from floats.
+__global__ void k_pack16(const float* __restrict__ src, uint16_t* __restrict__ dst, long long n, int mode) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = enc16(src[i], mode);
+}
+__global__ void k_unpack16(const uint16_t* __restrict__ src, float* __restrict__ dst, long long n, int mode) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = dec16(src[i], mode);
 }
 
 __global__ void k_set_parity(TissueDyn* dyn, int cur) {
@@ -642,8 +729,8 @@ cudaError_t launch(const LaunchPlan& lp, const LaunchArgs& L, cudaStream_t s) {
 // Select the kernel for a configuration, check it fits, and return the CTA
 // budget (resident CTAs on the whole GPU).
 int select_kernel(int model, bool masked, bool aniso, int ty, int device, int num_sms, StepKernel* out,
-                  int* ctas, bool surrogate, bool planar, bool general) {
-    StepKernel k = lookup_kernel(model, masked, aniso, ty, surrogate, planar, general);
+                  int* ctas, bool surrogate, bool planar, bool general, int gates = GATES_F32) {
+    StepKernel k = lookup_kernel(model, masked, aniso, ty, surrogate, planar, general, gates);
     if (!k.fn) return BBX_ERR_UNSUPPORTED;
     int smem_optin = 0;
     if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
@@ -682,6 +769,7 @@ struct bbx_grid {
     uint8_t* d_mask = nullptr;
     long long n_tissue = 0;
     float* d_fib = nullptr;  // [3][nz][ny][pxf], x stored from -4 (clamped padding)
+    float* d_div = nullptr;  // [3][nz][ny][px]: the fixed W-tilde sums of every node (k_divergence)
     int pxf = 0;
     long long fplane = 0, fvol = 0;
     bool aniso = false;
@@ -693,6 +781,7 @@ struct bbx_grid {
     double dt = 0.0;
     float* d_state[2] = {nullptr, nullptr};
     bool bound = false;
+    size_t bound_bytes = 0;
     int32_t* d_act = nullptr;
     float* d_rest = nullptr;  // 16 floats
     float4* d_tab = nullptr;  // V-table: chain matrices (BBX_BR_MRL) or Rush-Larsen coefficients (BBX_BR)
@@ -728,6 +817,18 @@ struct bbx_grid {
     int rk4 = 0;    // kinetics solver (bbx_set_solver)
     int resident = 0;  // multi-step resident kernel requested (bbx_set_resident)
 
+    // z-slab of a decomposed grid: the first halo_lo and last halo_hi planes
+    // are halo planes (a neighbour slab's boundary V, read by the stencil,
+    // never computed); plane_tissue: tissue nodes per plane
+    int halo_lo = 0, halo_hi = 0;
+    // storage of the Beeler-Reuter gates (GATES_F32, GATES_F16, GATES_U16);
+    // with 16 bits the buffers hold V and Ca as float planes, then the six
+    // gates as uint16 planes.  d_stage: float staging plane for host copies.
+    int gates = GATES_F32;
+    float* d_stage = nullptr;
+    std::vector<long long> plane_tissue;
+    cudaEvent_t ev_halo = nullptr;
+
     double* d_partials = nullptr;  // bbx_total scratch
     unsigned int* d_ticket = nullptr;
     double* d_total2 = nullptr;
@@ -749,6 +850,24 @@ int fail_cuda(cudaError_t e) {
         cudaError_t e_ = (call);                             \
         if (e_ != cudaSuccess) return fail_cuda(e_);         \
     } while (0)
+
+// Float-sized words of one state buffer: S planes, or with 16-bit gates two
+// float planes and six half-size planes.
+size_t state_words(const bbx_grid* g) {
+    return (size_t)(g->gates != GATES_F32 ? 5 : g->S) * (size_t)g->vol;
+}
+bool var_is16(const bbx_grid* g, int var) { return g->gates != GATES_F32 && var >= 2; }
+int ensure_stage(bbx_grid* g) {  // the float staging plane of 16-bit host copies
+    if (g->d_stage) return BBX_OK;
+    if (dmalloc(&g->d_stage, sizeof(float) * (size_t)g->vol) != cudaSuccess) {
+        cudaGetLastError();
+        return BBX_ERR_NOMEM;
+    }
+    return BBX_OK;
+}
+uint16_t* gate_plane(const bbx_grid* g, int b, int var) {
+    return reinterpret_cast<uint16_t*>(g->d_state[b] + 2 * (size_t)g->vol) + (size_t)(var - 2) * g->vol;
+}
 
 int n_blocks_for(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
@@ -877,13 +996,21 @@ void grid_segments(const bbx_grid* g, int tissue, std::vector<Seg>* segs) {
         }
         return;
     }
+    // a z-slab computes only the planes between its halo planes
+    const int zlo = g->halo_lo, zhi = g->nz - g->halo_hi;
     if (!g->d_mask) {
         for (int by = 0; by < g->nby; ++by)
-            for (int bx = 0; bx < g->nbx; ++bx) segs->push_back({tissue, bx * kTileX, by * g->ty, 0, g->nz});
+            for (int bx = 0; bx < g->nbx; ++bx) segs->push_back({tissue, bx * kTileX, by * g->ty, zlo, zhi});
         return;
     }
+    std::vector<Seg> all;
     cover_chunks(g->h_chunks.data(), (g->nx + kChunkX - 1) / kChunkX, g->nby, g->nbz, g->ty, g->zb, g->nz, tissue,
-                 segs);
+                 &all);
+    for (Seg sg : all) {
+        sg.z0 = std::max(sg.z0, zlo);
+        sg.z1 = std::min(sg.z1, zhi);
+        if (sg.z1 > sg.z0) segs->push_back(sg);
+    }
 }
 
 // The kernel's view of a grid for tile rows `ty` (tensor maps depend on it).
@@ -893,9 +1020,14 @@ int encode_targs(const bbx_grid* g, int ty, TissueArgs* t) {
     const cuuint64_t dims3[3] = {(cuuint64_t)g->nx, (cuuint64_t)g->ny, (cuuint64_t)g->nz};
     const cuuint64_t str3[2] = {(cuuint64_t)g->px * 4, (cuuint64_t)g->plane * 4};
     const cuuint32_t ubox[3] = {(cuuint32_t)(kTileX + 8), (cuuint32_t)(ty + 2), 1};
-    const cuuint64_t sdims4[4] = {(cuuint64_t)g->nx, (cuuint64_t)g->ny, (cuuint64_t)g->nz, (cuuint64_t)g->S};
+    const bool g16 = g->gates != GATES_F32;
+    const int s32 = g16 ? 2 : g->S;  // 32-bit variables (V first)
+    const cuuint64_t sdims4[4] = {(cuuint64_t)g->nx, (cuuint64_t)g->ny, (cuuint64_t)g->nz, (cuuint64_t)s32};
     const cuuint64_t str4[3] = {(cuuint64_t)g->px * 4, (cuuint64_t)g->plane * 4, (cuuint64_t)g->vol * 4};
-    const cuuint32_t sbox[4] = {(cuuint32_t)kTileX, (cuuint32_t)ty, 1, (cuuint32_t)(g->S > 1 ? g->S - 1 : 1)};
+    const cuuint32_t sbox[4] = {(cuuint32_t)kTileX, (cuuint32_t)ty, 1, (cuuint32_t)(s32 > 1 ? s32 - 1 : 1)};
+    const cuuint64_t gdims4[4] = {(cuuint64_t)g->nx, (cuuint64_t)g->ny, (cuuint64_t)g->nz, 6};
+    const cuuint64_t gstr4[3] = {(cuuint64_t)g->px * 2, (cuuint64_t)g->plane * 2, (cuuint64_t)g->vol * 2};
+    const cuuint32_t gbox[4] = {(cuuint32_t)kTileX, (cuuint32_t)ty, 1, 6};
     for (int b = 0; b < 2; ++b) {
         if (!encode(&t->tm_u[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, g->d_state[b], dims3, str3, ubox))
             return BBX_ERR_CUDA;
@@ -904,6 +1036,14 @@ int encode_targs(const bbx_grid* g, int ty, TissueArgs* t) {
                 return BBX_ERR_CUDA;
         } else {
             t->tm_s[b] = t->tm_u[b];
+        }
+        if (g16) {
+            if (!encode(&t->tm_g[b], CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, gate_plane(g, b, 2), gdims4, gstr4, gbox))
+                return BBX_ERR_CUDA;
+            t->gate16[b] = gate_plane(g, b, 2);
+        } else {
+            t->tm_g[b] = t->tm_u[b];
+            t->gate16[b] = nullptr;
         }
     }
     if (g->aniso) {
@@ -992,7 +1132,7 @@ int prepare(bbx_grid* g) {
     StepKernel k;
     int ctas = 0;
     int rc = select_kernel(g->model, g->d_mask != nullptr, g->aniso, g->ty, g->device, g->num_sms, &k, &ctas,
-                           g->surr_on && g->model == BBX_BR, g->nz == 1, wants_general(g));
+                           g->surr_on && g->model == BBX_BR, g->nz == 1, wants_general(g), g->gates);
     if (rc) return rc;
     if ((rc = encode_targs(g, g->ty, &g->h_t))) return rc;
     BBX_CUDA(cudaMemcpyAsync(g->d_t, &g->h_t, sizeof(TissueArgs), cudaMemcpyHostToDevice, g->stream));
@@ -1135,8 +1275,11 @@ void bbx_destroy_grid(bbx_grid* g) {
     }
     if (g->ev_enter) cudaEventDestroy(g->ev_enter);
     if (g->ev_out) cudaEventDestroy(g->ev_out);
+    if (g->ev_halo) cudaEventDestroy(g->ev_halo);
+    cudaFree(g->d_stage);
     cudaFree(g->d_mask);
     cudaFree(g->d_fib);
+    cudaFree(g->d_div);
     if (!g->bound) {
         cudaFree(g->d_state[0]);
         cudaFree(g->d_state[1]);
@@ -1206,9 +1349,16 @@ int bbx_create_grid(bbx_grid** out, int nx, int ny, int nz, double h, const uint
             rc = BBX_ERR_CUDA;
             break;
         }
+        g->plane_tissue.assign((size_t)nz, (long long)nx * ny);
         if (mask_host) {
             long long nt = 0;
-            for (long long i = 0; i < ncell; ++i) nt += mask_host[i] != 0;
+            for (int z = 0; z < nz; ++z) {
+                long long c = 0;
+                const uint8_t* m = mask_host + (size_t)z * nx * ny;
+                for (long long i = 0; i < (long long)nx * ny; ++i) c += m[i] != 0;
+                g->plane_tissue[(size_t)z] = c;
+                nt += c;
+            }
             g->n_tissue = nt;
             if (dmalloc(&g->d_mask, (size_t)g->vol) != cudaSuccess) {
                 cudaGetLastError();
@@ -1262,8 +1412,11 @@ int bbx_set_fibres(bbx_grid* g, const float* f, double D_par, double D_perp) {
     if (!g || !(D_par >= 0.0) || !(D_perp >= 0.0) || !std::isfinite(D_par) || !std::isfinite(D_perp))
         return BBX_ERR_ARG;
     if (!f) {
+        cudaStreamSynchronize(g->stream);
         cudaFree(g->d_fib);
+        cudaFree(g->d_div);
         g->d_fib = nullptr;
+        g->d_div = nullptr;
         g->aniso = false;
         g->Dpar = g->Dperp = D_par;
     } else {
@@ -1294,12 +1447,32 @@ int bbx_set_fibres(bbx_grid* g, const float* f, double D_par, double D_perp) {
         cudaFree(tmp);
         if (e != cudaSuccess) rc = fail_cuda(e);
         else if (err & kErrFibre) rc = BBX_ERR_FIBRE;
+        float* div = nullptr;
+        if (rc == BBX_OK) {
+            if (dmalloc(&div, sizeof(float) * 3 * (size_t)g->vol) != cudaSuccess) {
+                cudaGetLastError();
+                rc = BBX_ERR_NOMEM;
+            } else {
+                e = cudaMemsetAsync(div, 0, sizeof(float) * 3 * (size_t)g->vol, g->stream);
+                if (e == cudaSuccess) {
+                    k_divergence<<<n_blocks_for(g->ncell, 256), 256, 0, g->stream>>>(
+                        fib, g->nx, g->ny, g->nz, pxf, fplane, fvol, g->d_mask, g->px, g->plane, g->vol, div);
+                    e = cudaGetLastError();
+                }
+                if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+                if (e != cudaSuccess) rc = fail_cuda(e);
+            }
+        }
         if (rc != BBX_OK) {
             cudaFree(fib);
+            cudaFree(div);
             return rc;
         }
+        cudaStreamSynchronize(g->stream);
         cudaFree(g->d_fib);
+        cudaFree(g->d_div);
         g->d_fib = fib;
+        g->d_div = div;
         g->pxf = pxf;
         g->fplane = fplane;
         g->fvol = fvol;
@@ -1322,11 +1495,13 @@ int bbx_set_ionic_model(bbx_grid* g, int model, const double* params, int n_para
     for (int i = 0; i < nd; ++i)
         if (!std::isfinite(p[i])) return BBX_ERR_ARG;
     cudaStreamSynchronize(g->stream);
+    const size_t old_words = g->d_state[0] ? state_words(g) : 0;
+    g->gates = GATES_F32;  // a new model starts with 32-bit storage
     if (g->bound && S != g->S) {
         g->bound = false;  // the caller's buffers no longer fit: back to library buffers
         g->d_state[0] = g->d_state[1] = nullptr;
     }
-    if (!g->bound && (S != g->S || !g->d_state[0])) {
+    if (!g->bound && ((size_t)S * g->vol != old_words || !g->d_state[0])) {
         cudaFree(g->d_state[0]);
         cudaFree(g->d_state[1]);
         g->d_state[0] = g->d_state[1] = nullptr;
@@ -1369,7 +1544,7 @@ int bbx_bind_state(bbx_grid* g, void* a, void* b, size_t bytes) {
     if (!g) return BBX_ERR_ARG;
     if (!g->model) return BBX_ERR_STATE;
     if (!a || !b || a == b || (reinterpret_cast<uintptr_t>(a) & 15) || (reinterpret_cast<uintptr_t>(b) & 15) ||
-        bytes < sizeof(float) * g->S * (size_t)g->vol)
+        bytes < sizeof(float) * state_words(g))
         return BBX_ERR_ARG;
     cudaStreamSynchronize(g->stream);
     if (!g->bound) {
@@ -1379,9 +1554,15 @@ int bbx_bind_state(bbx_grid* g, void* a, void* b, size_t bytes) {
     g->d_state[0] = static_cast<float*>(a);
     g->d_state[1] = static_cast<float*>(b);
     g->bound = true;
-    for (int k = 0; k < 2; ++k)
-        k_fill_state<<<n_blocks_for((long long)g->S * g->vol, 256), 256, 0, g->stream>>>(g->d_state[k], g->S,
-                                                                                            g->vol, g->d_rest);
+    g->bound_bytes = bytes;
+    for (int k = 0; k < 2; ++k) {
+        if (g->gates != GATES_F32)
+            k_fill_state16<<<n_blocks_for(g->vol, 256), 256, 0, g->stream>>>(g->d_state[k], g->vol, g->d_rest,
+                                                                              g->gates);
+        else
+            k_fill_state<<<n_blocks_for((long long)g->S * g->vol, 256), 256, 0, g->stream>>>(g->d_state[k], g->S,
+                                                                                                g->vol, g->d_rest);
+    }
     BBX_CUDA(cudaGetLastError());
     TissueDyn d;
     int rc = read_dyn(g, &d);
@@ -1398,6 +1579,17 @@ int bbx_write_state(bbx_grid* g, int var, const float* host, size_t n) {
     // both ping-pong buffers get the values (void nodes are never rewritten
     // by a step, so the buffers must agree there): one copy from the host,
     // one on the device
+    if (var_is16(g, var)) {
+        int rc = ensure_stage(g);
+        if (rc || (rc = copy_in(g, g->d_stage, host, sizeof(float)))) return rc;
+        k_pack16<<<n_blocks_for(g->vol, 256), 256, 0, g->stream>>>(g->d_stage, gate_plane(g, 0, var), g->vol,
+                                                                     g->gates);
+        BBX_CUDA(cudaGetLastError());
+        BBX_CUDA(cudaMemcpyAsync(gate_plane(g, 1, var), gate_plane(g, 0, var), sizeof(uint16_t) * (size_t)g->vol,
+                                 cudaMemcpyDeviceToDevice, g->stream));
+        BBX_CUDA(cudaStreamSynchronize(g->stream));
+        return BBX_OK;
+    }
     float* b0 = g->d_state[0] + (size_t)var * g->vol;
     float* b1 = g->d_state[1] + (size_t)var * g->vol;
     int rc = copy_in(g, b0, host, sizeof(float));
@@ -1411,6 +1603,13 @@ int bbx_write_all(bbx_grid* g, const float* host, size_t n) {
     if (!g) return BBX_ERR_ARG;
     if (!g->model) return BBX_ERR_STATE;
     if (!host || n != (size_t)g->S * (size_t)g->ncell) return BBX_ERR_ARG;
+    if (g->gates != GATES_F32) {  // 16-bit gates: variable by variable, through the float staging plane
+        for (int v = 0; v < g->S; ++v) {
+            int rc = bbx_write_state(g, v, host + (size_t)v * g->ncell, (size_t)g->ncell);
+            if (rc) return rc;
+        }
+        return BBX_OK;
+    }
     // every variable into buffer 0, then buffer 0 into buffer 1 in one
     // device copy (both hold the state, as bbx_write_state leaves them); one
     // synchronisation at the end
@@ -1579,7 +1778,8 @@ int bbx_step(bbx_grid* g, double dt, int n_steps) {
     if (!g->d_mask) {
         // unmasked grid: whole columns in order (nz planes, or a sheet's nby
         // tile rows), equal shares (build_plan)
-        L.reg_len = g->nz > 1 ? g->nz : g->nby;
+        L.reg_len = g->nz > 1 ? g->nz - g->halo_lo - g->halo_hi : g->nby;
+        L.reg_z0 = g->nz > 1 ? g->halo_lo : 0;
         L.reg_nbx = g->nbx;
         L.reg_ty = g->ty;
         L.reg_ctas = g->lp.ctas;
@@ -1602,7 +1802,15 @@ int bbx_read_state(bbx_grid* g, int var, float* host, size_t n) {
     TissueDyn d;
     int rc = read_dyn(g, &d);
     if (rc) return rc;
-    rc = copy_out(g, host, g->d_state[d.cur] + (size_t)var * g->vol, sizeof(float));
+    if (var_is16(g, var)) {
+        if ((rc = ensure_stage(g))) return rc;
+        k_unpack16<<<n_blocks_for(g->vol, 256), 256, 0, g->stream>>>(gate_plane(g, d.cur, var), g->d_stage, g->vol,
+                                                                       g->gates);
+        BBX_CUDA(cudaGetLastError());
+        rc = copy_out(g, host, g->d_stage, sizeof(float));
+    } else {
+        rc = copy_out(g, host, g->d_state[d.cur] + (size_t)var * g->vol, sizeof(float));
+    }
     if (rc) return rc;
     return check_sticky(g);
 }
@@ -1611,6 +1819,13 @@ int bbx_read_all(bbx_grid* g, float* host, size_t n) {
     if (!g) return BBX_ERR_ARG;
     if (!g->model) return BBX_ERR_STATE;
     if (!host || n != (size_t)g->S * (size_t)g->ncell) return BBX_ERR_ARG;
+    if (g->gates != GATES_F32) {
+        for (int v = 0; v < g->S; ++v) {
+            int rc = bbx_read_state(g, v, host + (size_t)v * g->ncell, (size_t)g->ncell);
+            if (rc) return rc;
+        }
+        return BBX_OK;
+    }
     TissueDyn d;
     int rc = read_dyn(g, &d);
     if (rc) return rc;
@@ -1628,7 +1843,7 @@ int bbx_exchange_state(bbx_grid* g, const float* host_in, float* host_out, size_
     if (!g) return BBX_ERR_ARG;
     if (!g->model) return BBX_ERR_STATE;
     if (!host_in || !host_out || n != (size_t)g->S * (size_t)g->ncell) return BBX_ERR_ARG;
-    if (g->px != g->nx) {  // padded rows: one direction after the other
+    if (g->px != g->nx || g->gates != GATES_F32) {  // padded rows or 16-bit gates: one direction after the other
         int rc = bbx_read_all(g, host_out, n);
         return rc ? rc : bbx_write_all(g, host_in, n);
     }
@@ -1682,13 +1897,17 @@ int bbx_total(bbx_grid* g, int var, double* out) {
     if (!g) return BBX_ERR_ARG;
     if (!g->model) return BBX_ERR_STATE;
     if (var < 0 || var >= g->S || !out) return BBX_ERR_ARG;
+    if (var_is16(g, var)) return BBX_ERR_UNSUPPORTED;
     TissueDyn d;
     int rc = read_dyn(g, &d);
     if (rc) return rc;
     int blocks = g->num_sms * 4;
     if (blocks > kMaxPartials) blocks = kMaxPartials;
-    k_total<<<blocks, 256, 0, g->stream>>>(g->d_state[d.cur] + (size_t)var * g->vol, g->d_mask, g->nx, g->ny,
-                                           g->nz, g->px, g->plane, g->d_partials, g->d_ticket, g->d_total2, g->d_err);
+    const long long z0 = g->halo_lo;  // a z-slab sums its own planes, not its halo planes
+    k_total<<<blocks, 256, 0, g->stream>>>(g->d_state[d.cur] + (size_t)var * g->vol + z0 * g->plane,
+                                           g->d_mask ? g->d_mask + z0 * g->plane : nullptr, g->nx, g->ny,
+                                           g->nz - g->halo_lo - g->halo_hi, g->px, g->plane, g->d_partials,
+                                           g->d_ticket, g->d_total2, g->d_err);
     BBX_CUDA(cudaGetLastError());
     BBX_CUDA(cudaMemcpyAsync(out, g->d_total2, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
     return check_sticky(g);
@@ -1705,6 +1924,7 @@ int bbx_ppm_frame(bbx_grid* g, const int* layers, const double* lo, const double
         h[c] = (float)hi[c];
         if (ly[c] < -1 || ly[c] >= g->S) return BBX_ERR_ARG;
         if (ly[c] >= 0 && !(std::isfinite(l[c]) && std::isfinite(h[c]) && h[c] != l[c])) return BBX_ERR_ARG;
+        if (ly[c] >= 0 && var_is16(g, ly[c])) return BBX_ERR_UNSUPPORTED;  // 16-bit gate layers
     }
     BBX_CUDA(launch_ppm(g->d_state[0], g->d_state[1], &g->d_dyn->cur, g->d_mask, g->vol, g->nx, g->ny, g->nz, g->px,
                         g->plane, ly, l, h, out_dev, g->num_sms, g->stream));
@@ -1717,6 +1937,7 @@ int bbx_phase_singularities(bbx_grid* g, int var_a, double iso_a, int var_b, dou
     if (!g->model) return BBX_ERR_STATE;
     if (var_a < 0 || var_a >= g->S || var_b < 0 || var_b >= g->S || !std::isfinite(iso_a) || !std::isfinite(iso_b))
         return BBX_ERR_ARG;
+    if (var_is16(g, var_a) || var_is16(g, var_b)) return BBX_ERR_UNSUPPORTED;
     if (!g->d_count && dmalloc(&g->d_count, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return BBX_ERR_NOMEM;
@@ -1778,7 +1999,9 @@ int bbx_get_info(bbx_grid* g, bbx_info* o) {
     o->tile_y = g->ty;
     o->tile_z = g->zb;
     o->n_bricks = g->n_bricks;
-    o->n_tissue = g->n_tissue;
+    long long owned = 0;  // tissue nodes the step computes (a z-slab's halo planes excluded)
+    for (int z = g->halo_lo; z < g->nz - g->halo_hi; ++z) owned += g->plane_tissue[(size_t)z];
+    o->n_tissue = owned;
     o->step = d.n;
     o->t = d.t;
     return BBX_OK;
@@ -1819,7 +2042,115 @@ int bbx_state_device_ptr(bbx_grid* g, int var, void** p) {
     TissueDyn d;
     int rc = read_dyn(g, &d);
     if (rc) return rc;
-    *p = g->d_state[d.cur] + (size_t)var * g->vol;
+    *p = var_is16(g, var) ? (void*)gate_plane(g, d.cur, var) : (void*)(g->d_state[d.cur] + (size_t)var * g->vol);
+    return BBX_OK;
+}
+
+int bbx_set_gate_storage(bbx_grid* g, int mode) {
+    if (!g || (mode != BBX_GATES_FP32 && mode != BBX_GATES_FP16 && mode != BBX_GATES_UNORM16)) return BBX_ERR_ARG;
+    if (!g->model) return BBX_ERR_STATE;
+    if (mode == g->gates) return BBX_OK;
+    if (g->model != BBX_BR || (mode != BBX_GATES_FP32 && g->surr_on)) return BBX_ERR_UNSUPPORTED;
+    if (mode != BBX_GATES_FP32 && g->ty == 28) {  // 16-bit kernels have 7- and 14-row tiles
+        g->ty = 14;
+        int rc0 = build_bricks(g);
+        if (rc0) return rc0;
+    }
+    // the current state through the host, in the new layout
+    std::vector<float> host((size_t)g->S * g->ncell);
+    int rc = bbx_read_all(g, host.data(), host.size());
+    if (rc) return rc;
+    const int old = g->gates;
+    const size_t need = (size_t)(mode != BBX_GATES_FP32 ? 5 : g->S) * g->vol;
+    if (g->bound && sizeof(float) * need > g->bound_bytes) return BBX_ERR_STATE;  // the caller's buffers are too small
+    if (!g->bound) {
+        float* nb[2] = {nullptr, nullptr};
+        if (dmalloc(&nb[0], sizeof(float) * need) != cudaSuccess ||
+            dmalloc(&nb[1], sizeof(float) * need) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(nb[0]);
+            return BBX_ERR_NOMEM;
+        }
+        cudaStreamSynchronize(g->stream);
+        cudaFree(g->d_state[0]);
+        cudaFree(g->d_state[1]);
+        g->d_state[0] = nb[0];
+        g->d_state[1] = nb[1];
+    }
+    g->gates = mode;
+    // every node (void ones included) to rest in the new layout, then the state
+    for (int k = 0; k < 2; ++k) {
+        if (mode != BBX_GATES_FP32)
+            k_fill_state16<<<n_blocks_for(g->vol, 256), 256, 0, g->stream>>>(g->d_state[k], g->vol, g->d_rest, mode);
+        else
+            k_fill_state<<<n_blocks_for((long long)g->S * g->vol, 256), 256, 0, g->stream>>>(g->d_state[k], g->S,
+                                                                                                g->vol, g->d_rest);
+    }
+    BBX_CUDA(cudaGetLastError());
+    TissueDyn d;
+    if ((rc = read_dyn(g, &d))) return rc;
+    d.cur = 0;
+    if ((rc = write_dyn(g, d))) return rc;
+    g->ready = false;
+    if ((rc = prepare(g))) {
+        (void)old;
+        return rc;
+    }
+    return bbx_write_all(g, host.data(), host.size());
+}
+
+int bbx_set_halo_planes(bbx_grid* g, int lo, int hi) {
+    if (!g || lo < 0 || lo > 1 || hi < 0 || hi > 1) return BBX_ERR_ARG;
+    if ((lo || hi) && (g->nz < 2 || g->nz <= lo + hi)) return BBX_ERR_ARG;
+    if (lo == g->halo_lo && hi == g->halo_hi) return BBX_OK;
+    if (g->model) {
+        int rc = finish_total(g);  // the plan's partials are about to be replaced
+        if (rc) return rc;
+    }
+    g->halo_lo = lo;
+    g->halo_hi = hi;
+    g->ready = false;
+    return g->model ? prepare(g) : BBX_OK;
+}
+
+int bbx_halo_plane(bbx_grid* g, int side, int halo, void** dev_ptr, size_t* bytes) {
+    if (!g || !dev_ptr || (side != 0 && side != 1) || (halo != 0 && halo != 1)) return BBX_ERR_ARG;
+    if (!g->model || !g->d_state[0]) return BBX_ERR_STATE;
+    const int has = side == 0 ? g->halo_lo : g->halo_hi;
+    if (!has) return BBX_ERR_STATE;  // no halo plane on that side
+    int z;
+    if (side == 0) z = halo ? 0 : 1;
+    else z = halo ? g->nz - 1 : g->nz - 2;
+    *dev_ptr = g->d_state[g->h_cur] + (size_t)z * g->plane;  // V of the buffer the next step reads
+    if (bytes) *bytes = (size_t)g->plane * sizeof(float);
+    return BBX_OK;
+}
+
+int bbx_halo_exchange(bbx_grid* lower, bbx_grid* upper) {
+    if (!lower || !upper || lower == upper) return BBX_ERR_ARG;
+    if (!lower->model || !upper->model) return BBX_ERR_STATE;
+    if (!lower->halo_hi || !upper->halo_lo) return BBX_ERR_STATE;
+    if (lower->nx != upper->nx || lower->ny != upper->ny || lower->device != upper->device) return BBX_ERR_ARG;
+    const size_t bytes = (size_t)lower->plane * sizeof(float);
+    float* lo_send = lower->d_state[lower->h_cur] + (size_t)(lower->nz - 2) * lower->plane;
+    float* lo_recv = lower->d_state[lower->h_cur] + (size_t)(lower->nz - 1) * lower->plane;
+    float* up_send = upper->d_state[upper->h_cur] + (size_t)1 * upper->plane;
+    float* up_recv = upper->d_state[upper->h_cur];
+    const bool two = lower->stream != upper->stream;
+    if (two) {
+        // the copies run on the lower grid's stream after the upper grid's
+        // enqueued work, and the upper grid's later work waits for them
+        if (!upper->ev_halo) BBX_CUDA(cudaEventCreateWithFlags(&upper->ev_halo, cudaEventDisableTiming));
+        if (!lower->ev_halo) BBX_CUDA(cudaEventCreateWithFlags(&lower->ev_halo, cudaEventDisableTiming));
+        BBX_CUDA(cudaEventRecord(upper->ev_halo, upper->stream));
+        BBX_CUDA(cudaStreamWaitEvent(lower->stream, upper->ev_halo, 0));
+    }
+    BBX_CUDA(cudaMemcpyAsync(up_recv, lo_send, bytes, cudaMemcpyDeviceToDevice, lower->stream));
+    BBX_CUDA(cudaMemcpyAsync(lo_recv, up_send, bytes, cudaMemcpyDeviceToDevice, lower->stream));
+    if (two) {
+        BBX_CUDA(cudaEventRecord(lower->ev_halo, lower->stream));
+        BBX_CUDA(cudaStreamWaitEvent(upper->stream, lower->ev_halo, 0));
+    }
     return BBX_OK;
 }
 
@@ -1829,7 +2160,7 @@ int bbx_autotune(bbx_grid* g, double dt, double* best_ms) {
     int rc = set_dt(g, dt);
     if (rc) return rc;
     // save the state so the trial steps leave no trace
-    const size_t sbytes = sizeof(float) * g->S * (size_t)g->vol;
+    const size_t sbytes = sizeof(float) * state_words(g);
     float* save = nullptr;
     int32_t* save_act = nullptr;
     if (dmalloc(&save, sbytes) != cudaSuccess) {
@@ -1917,7 +2248,7 @@ extern "C" int bbx_set_surrogate(bbx_grid* g, const bbx_mlp* m, double v_upstrok
         return g->model ? prepare(g) : BBX_OK;
     }
     if (!g->model) return BBX_ERR_STATE;
-    if (g->model != BBX_BR) return BBX_ERR_UNSUPPORTED;
+    if (g->model != BBX_BR || g->gates != GATES_F32) return BBX_ERR_UNSUPPORTED;
     if (!g->d_surr && dmalloc(&g->d_surr, sizeof(SurrogateData)) != cudaSuccess) {
         cudaGetLastError();
         return BBX_ERR_NOMEM;
@@ -1940,7 +2271,7 @@ extern "C" int bbx_sample_reaction_pairs(bbx_grid* g, long long n, unsigned long
                                          float* t_dev) {
     if (!g || n <= 0 || !x_dev || !t_dev) return BBX_ERR_ARG;
     if (!g->model) return BBX_ERR_STATE;
-    if (g->model != BBX_BR) return BBX_ERR_UNSUPPORTED;
+    if (g->model != BBX_BR || g->gates != GATES_F32) return BBX_ERR_UNSUPPORTED;
     if (!(g->dt > 0.0)) return BBX_ERR_STATE;
     if (g->n_tissue == 0) return BBX_ERR_ARG;
     if (!g->ready) {
@@ -2130,6 +2461,7 @@ int bbx_batch_create(bbx_batch** out, bbx_grid* const* grids, int n) {
     for (int i = 0; i < n; ++i) {
         if (!grids[i]) return BBX_ERR_ARG;
         if (!grids[i]->model || !(grids[i]->dt > 0.0)) return BBX_ERR_STATE;
+        if (grids[i]->gates != GATES_F32) return BBX_ERR_UNSUPPORTED;  // 16-bit gates: stepped alone
         if (grids[i]->stream != grids[0]->stream || grids[i]->device != grids[0]->device) return BBX_ERR_ARG;
         for (int j = 0; j < i; ++j)
             if (grids[j] == grids[i]) return BBX_ERR_ARG;

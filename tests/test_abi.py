@@ -43,6 +43,21 @@ def test_argument_errors_without_gpu():
     L.bbx_destroy_grid(None)
 
 
+def test_noalloc_total_refuses_bad_arguments_without_gpu():
+    # every refusal of bbx_total_noalloc returns before any CUDA call; the
+    # pointers are dummies that are never dereferenced
+    L = bbx.lib()
+    f = ctypes.c_void_p(0x1000)
+    out = ctypes.c_void_p(0x2000)
+    T = L.bbx_total_noalloc
+    assert T(None, None, 8, 8, 8, 8, out, None) == bbx.BBX_ERR_ARG          # no field
+    assert T(f, None, 8, 8, 8, 8, None, None) == bbx.BBX_ERR_ARG            # no output
+    assert T(f, None, 8, 8, 8, 7, out, None) == bbx.BBX_ERR_ARG             # pitch < nx
+    assert T(f, None, 0, 8, 8, 8, out, None) == bbx.BBX_ERR_ARG             # empty
+    assert T(f, None, 8, -1, 8, 8, out, None) == bbx.BBX_ERR_ARG
+    assert T(f, None, 1 << 15, 1 << 14, 2, 1 << 15, out, None) == bbx.BBX_ERR_ARG  # 2^29 > 2^28 nodes
+
+
 def test_binding_names_match_the_c_abi():
     for n in _declared():
         assert callable(getattr(bbx, n)), n

@@ -37,6 +37,11 @@ def test_noalloc_total_matches_bbx_total_on_two_calls():
     bbx.bbx_total_noalloc(G.state_device_ptr(0), None, nx, ny, nz, px, out.data_ptr(), stream)
     torch.cuda.synchronize()
     assert out.item() == pytest.approx(float(np.sum(G.read_state(0).astype(np.float64))), rel=1e-12)
+    # few long rows (fewer rows than SMs): each block walks whole rows
+    u2 = torch.rand((1, 3, 70001), dtype=torch.float32, device="cuda")
+    bbx.bbx_total_noalloc(u2.data_ptr(), None, 70001, 3, 1, 70001, out.data_ptr(), stream)
+    torch.cuda.synchronize()
+    assert out.item() == pytest.approx(float(u2.double().sum().item()), rel=1e-12)
     # a field beyond the fixed scratch (2^28 nodes) is refused before any launch
     with pytest.raises(bbx.BbxError) as e:
         bbx.bbx_total_noalloc(G.state_device_ptr(0), None, 1 << 15, 1 << 14, 2, 1 << 15, out.data_ptr(), stream)
