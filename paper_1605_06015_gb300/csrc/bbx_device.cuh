@@ -56,7 +56,8 @@ struct TissueArgs {  // (CUtensorMap members impose its alignment)
     CUtensorMap tm_u[2];  // V of buffer b with halo (box TX+8 x TY+2)
     CUtensorMap tm_s[2];  // non-diffusing variables of buffer b (box TX x TY x S-1; with 16-bit gates: Ca only)
     CUtensorMap tm_g[2];  // 16-bit gates of buffer b (box TX x TY x 6 uint16), when stored so
-    CUtensorMap tm_f;     // unit fibres, x stored from -4 with clamped padding
+    CUtensorMap tm_f;     // unit fibres, x stored from -4 with clamped padding (box TX x TY x 3, no halo)
+    CUtensorMap tm_d;     // the W-tilde sums of every node (box TX x TY x 3)
     CUtensorMap tm_m;     // tissue mask bytes
     float* state[2];      // the ping-pong buffers, var v at state[b] + v*vol (32-bit variables)
     uint16_t* gate16[2];  // 16-bit gates: gate g (variable 2 + g) at gate16[b] + g*vol, or nullptr
@@ -689,25 +690,38 @@ struct Plan {
     static constexpr int UW = TX + 8;   // x from x0-4 to x0+TX+3 (16-byte aligned start)
     static constexpr int UH = TY + 2;   // y from y0-1 to y0+TY
     static constexpr int MW = TX + 32;  // mask bytes: x from x0-16 (16-byte aligned start)
+    // ring A, one stage per loaded plane (the computed planes and the z-halo
+    // planes): V with its one-node halo, the mask with its halo
     static constexpr int U_RAW = UW * UH * 4;
-    static constexpr int F_RAW = ANISO ? 3 * UW * UH * 4 : 0;
     static constexpr int M_RAW = MASKED ? MW * UH : 0;
+    static constexpr int U_OFF = 0;
+    static constexpr int M_OFF = U_OFF + align128(U_RAW);
+    static constexpr int A_STAGE = M_OFF + align128(M_RAW);
+    static constexpr uint32_t A_BYTES = U_RAW + M_RAW;
+    // ring B, one stage per computed plane: the node's own unit fibre and
+    // W-tilde sums (3 x TX x TY floats each), the other variables
+    static constexpr int F_RAW = ANISO ? 3 * TX * TY * 4 : 0;
+    static constexpr int D_RAW = ANISO ? 3 * TX * TY * 4 : 0;
     static constexpr int S32_RAW = (S > 1) ? (S - 1 - NG) * TX * TY * 4 : 0;  // 32-bit non-diffusing variables
     static constexpr int G_RAW = NG * TX * TY * 2;                              // 16-bit gates
     static constexpr int S_RAW = S32_RAW + G_RAW;
-    static constexpr int U_OFF = 0;
-    static constexpr int F_OFF = U_OFF + align128(U_RAW);
-    static constexpr int M_OFF = F_OFF + align128(F_RAW);
-    static constexpr int S_OFF = M_OFF + align128(M_RAW);
-    static constexpr int G_OFF = S_OFF + S32_RAW;  // (S32_RAW is a multiple of 128)
-    static constexpr int STAGE = S_OFF + align128(S_RAW);
-    static constexpr uint32_t TX_BYTES = U_RAW + F_RAW + M_RAW + S_RAW;  // plane computed in this piece
-    static constexpr uint32_t TX_BYTES_HALO = U_RAW + F_RAW + M_RAW;     // z-halo plane: no other vars
-    static constexpr int NS_FIT = ((CTAS == 1 ? 200 : 112) * 1024) / STAGE;  // stages that fit CTAS per SM
-    static constexpr int NS = NS_FIT > 8 ? 8 : (NS_FIT < 4 ? 4 : NS_FIT);
+    static constexpr int F_OFF = 0;
+    static constexpr int D_OFF = F_OFF + F_RAW;    // (each part a multiple of 128 bytes)
+    static constexpr int S_OFF = D_OFF + D_RAW;
+    static constexpr int G_OFF = S_OFF + S32_RAW;
+    static constexpr int B_STAGE = align128(F_RAW + D_RAW + S_RAW);
+    static constexpr uint32_t B_BYTES = F_RAW + D_RAW + S_RAW;
+    static constexpr bool HAS_B = B_BYTES > 0;
+    static constexpr int BUDGET = (CTAS == 1 ? 200 : 112) * 1024;  // dynamic shared memory per CTA
+    static constexpr int NB = !HAS_B ? 0 : (3 * B_STAGE + 5 * A_STAGE <= BUDGET ? 3 : 2);
+    static constexpr int NA_FIT = (BUDGET - NB * B_STAGE) / A_STAGE;
+    static constexpr int NA = NA_FIT > 8 ? 8 : (NA_FIT < 4 ? 4 : NA_FIT);
     static constexpr int WBUF = SURR ? RY * 2048 : 0;  // per consumer warp: 64 rows of 32 bytes
-    static constexpr int SMEM = 128 + NS * STAGE + WBUF + 2 * NS * 8 + NS * 176;  // stages, warp buffers, rings
+    static constexpr int BAR_OFF = NA * A_STAGE + NB * B_STAGE + WBUF;
+    // stages, warp buffers, full/empty barriers of both rings, piece contexts
+    static constexpr int SMEM = 128 + BAR_OFF + 2 * (NA + NB) * 8 + NA * 176;
     static_assert(TY % RY == 0 && CY >= 1, "tile rows must be a multiple of the thread rows");
+    static_assert(U_RAW % 16 == 0 && F_RAW % 128 == 0 && D_RAW % 128 == 0 && S32_RAW % 128 == 0, "stage layout");
 };
 
 struct F3 {
@@ -723,12 +737,16 @@ struct Nb {
     float ypzp, ymzm, ypzm, ymzp;  // (y,z) edges
 };
 
+// The precomputed ingredients of Eq. (Lu) at a node: the unit fibre f (D =
+// Dperp I + (Dpar - Dperp) f f^T, Eq. (sigma)) and the W-tilde sums sd_k =
+// sum_j (f_j f_k at p + q_j minus at p - q_j), with a void neighbour's fibre
+// replaced by f at p (computed once per grid, k_divergence).
+
 // (L u)_p for a node whose 18 neighbours are all tissue: the weights of
 // Eq. (Lu) with psi = 1 everywhere, in difference form.  c_perp = Dperp/h^2,
 // c_d = (Dpar-Dperp)/h^2, c_dh = c_d/2, c_s = c_d/4.
 template <bool ANISO>
-__device__ __forceinline__ float lap_interior(const Coef& a, const Nb& n, F3 f, F3 fxp, F3 fxm, F3 fyp,
-                                              F3 fym, F3 fzp, F3 fzm) {
+__device__ __forceinline__ float lap_interior(const Coef& a, const Nb& n, F3 f, F3 sd) {
     if (!ANISO) {
         return a.c_iso * (((n.xp + n.xm) + (n.yp + n.ym)) + (n.zp + n.zm) - 6.0f * n.u0);
     }
@@ -737,20 +755,13 @@ __device__ __forceinline__ float lap_interior(const Coef& a, const Nb& n, F3 f, 
     const float Dzz = fmaf(a.c_d, f.z * f.z, a.c_perp);
     const float hx = a.c_dh * f.x;
     const float Dxy = hx * f.y, Dxz = hx * f.z, Dyz = a.c_dh * f.y * f.z;
-    // S_k = sum_j (ff^T)_jk at p+q_j minus at p-q_j (the Dperp parts cancel)
-    float sx = fxp.x * fxp.x, sy = fxp.x * fxp.y, sz = fxp.x * fxp.z;
-    sx = fmaf(-fxm.x, fxm.x, sx); sy = fmaf(-fxm.x, fxm.y, sy); sz = fmaf(-fxm.x, fxm.z, sz);
-    sx = fmaf(fyp.y, fyp.x, sx); sy = fmaf(fyp.y, fyp.y, sy); sz = fmaf(fyp.y, fyp.z, sz);
-    sx = fmaf(-fym.y, fym.x, sx); sy = fmaf(-fym.y, fym.y, sy); sz = fmaf(-fym.y, fym.z, sz);
-    sx = fmaf(fzp.z, fzp.x, sx); sy = fmaf(fzp.z, fzp.y, sy); sz = fmaf(fzp.z, fzp.z, sz);
-    sx = fmaf(-fzm.z, fzm.x, sx); sy = fmaf(-fzm.z, fzm.y, sy); sz = fmaf(-fzm.z, fzm.z, sz);
     const float two_u = 2.0f * n.u0;
     float L = Dxx * ((n.xp + n.xm) - two_u);
     L = fmaf(Dyy, (n.yp + n.ym) - two_u, L);
     L = fmaf(Dzz, (n.zp + n.zm) - two_u, L);
-    float dv = sx * (n.xp - n.xm);
-    dv = fmaf(sy, n.yp - n.ym, dv);
-    dv = fmaf(sz, n.zp - n.zm, dv);
+    float dv = sd.x * (n.xp - n.xm);
+    dv = fmaf(sd.y, n.yp - n.ym, dv);
+    dv = fmaf(sd.z, n.zp - n.zm, dv);
     L = fmaf(a.c_s, dv, L);
     L = fmaf(Dxy, (n.pp + n.mm) - (n.pm + n.mp), L);
     L = fmaf(Dxz, (n.xpzp + n.xmzm) - (n.xpzm + n.xmzp), L);
@@ -760,12 +771,9 @@ __device__ __forceinline__ float lap_interior(const Coef& a, const Nb& n, F3 f, 
 
 // (L u)_p for a node of an unmasked grid whose y and z neighbours are inside
 // the array; px, mx in {0, 1} are psi of the x+1 and x-1 neighbours (0 only
-// at the array's x faces).  Out-of-array fibres read as the node's own (the
-// fibre field is stored with a clamped x-padding), which is the replacement
-// of a void neighbour's tensor by D^p.
+// at the array's x faces).
 template <bool ANISO>
-__device__ __forceinline__ float lap_xbound(const Coef& a, const Nb& n, float px, float mx, F3 f, F3 fxp,
-                                            F3 fxm, F3 fyp, F3 fym, F3 fzp, F3 fzm) {
+__device__ __forceinline__ float lap_xbound(const Coef& a, const Nb& n, float px, float mx, F3 f, F3 sd) {
     const float ex = px * (n.xp - n.u0) + mx * (n.xm - n.u0);
     if (!ANISO) {
         return a.c_iso * ((ex + (n.yp + n.ym)) + (n.zp + n.zm) - 4.0f * n.u0);
@@ -775,19 +783,13 @@ __device__ __forceinline__ float lap_xbound(const Coef& a, const Nb& n, float px
     const float Dzz = fmaf(a.c_d, f.z * f.z, a.c_perp);
     const float hx = a.c_dh * f.x;
     const float Dxy = hx * f.y, Dxz = hx * f.z, Dyz = a.c_dh * f.y * f.z;
-    float sx = fxp.x * fxp.x, sy = fxp.x * fxp.y, sz = fxp.x * fxp.z;
-    sx = fmaf(-fxm.x, fxm.x, sx); sy = fmaf(-fxm.x, fxm.y, sy); sz = fmaf(-fxm.x, fxm.z, sz);
-    sx = fmaf(fyp.y, fyp.x, sx); sy = fmaf(fyp.y, fyp.y, sy); sz = fmaf(fyp.y, fyp.z, sz);
-    sx = fmaf(-fym.y, fym.x, sx); sy = fmaf(-fym.y, fym.y, sy); sz = fmaf(-fym.y, fym.z, sz);
-    sx = fmaf(fzp.z, fzp.x, sx); sy = fmaf(fzp.z, fzp.y, sy); sz = fmaf(fzp.z, fzp.z, sz);
-    sx = fmaf(-fzm.z, fzm.x, sx); sy = fmaf(-fzm.z, fzm.y, sy); sz = fmaf(-fzm.z, fzm.z, sz);
     const float two_u = 2.0f * n.u0;
     float L = Dxx * ex;
     L = fmaf(Dyy, (n.yp + n.ym) - two_u, L);
     L = fmaf(Dzz, (n.zp + n.zm) - two_u, L);
-    float dv = (px * mx) * sx * (n.xp - n.xm);
-    dv = fmaf(sy, n.yp - n.ym, dv);
-    dv = fmaf(sz, n.zp - n.zm, dv);
+    float dv = (px * mx) * sd.x * (n.xp - n.xm);
+    dv = fmaf(sd.y, n.yp - n.ym, dv);
+    dv = fmaf(sd.z, n.zp - n.zm, dv);
     L = fmaf(a.c_s, dv, L);
     L = fmaf(Dxy, px * (n.pp - n.pm) + mx * (n.mm - n.mp), L);
     L = fmaf(Dxz, px * (n.xpzp - n.xpzm) + mx * (n.xmzm - n.xmzp), L);
@@ -805,11 +807,10 @@ struct Psi {
 };
 
 // (L u)_p for any tissue node: every weight carries its psi (a void or
-// out-of-array neighbour contributes nothing) and, in Wtilde, a void
-// neighbour's tensor is replaced by D^p.
+// out-of-array neighbour contributes nothing); the W-tilde sums already hold
+// a void neighbour's tensor replaced by D^p.
 template <bool ANISO>
-__device__ __forceinline__ float lap_general(const Coef& a, const Nb& n, const Psi& q, F3 f, F3 fxp, F3 fxm,
-                                             F3 fyp, F3 fym, F3 fzp, F3 fzm) {
+__device__ __forceinline__ float lap_general(const Coef& a, const Nb& n, const Psi& q, F3 f, F3 sd) {
     auto d = [&](bool ps, float uq) { return ps ? (uq - n.u0) : 0.0f; };
     const float exp_ = d(q.xp, n.xp), exm = d(q.xm, n.xm), eyp = d(q.yp, n.yp), eym = d(q.ym, n.ym);
     const float ezp = d(q.zp, n.zp), ezm = d(q.zm, n.zm);
@@ -821,24 +822,12 @@ __device__ __forceinline__ float lap_general(const Coef& a, const Nb& n, const P
     const float Dzz = fmaf(a.c_d, f.z * f.z, a.c_perp);
     const float hx = a.c_dh * f.x;
     const float Dxy = hx * f.y, Dxz = hx * f.z, Dyz = a.c_dh * f.y * f.z;
-    if (!q.xp) fxp = f;
-    if (!q.xm) fxm = f;
-    if (!q.yp) fyp = f;
-    if (!q.ym) fym = f;
-    if (!q.zp) fzp = f;
-    if (!q.zm) fzm = f;
-    float sx = fxp.x * fxp.x, sy = fxp.x * fxp.y, sz = fxp.x * fxp.z;
-    sx = fmaf(-fxm.x, fxm.x, sx); sy = fmaf(-fxm.x, fxm.y, sy); sz = fmaf(-fxm.x, fxm.z, sz);
-    sx = fmaf(fyp.y, fyp.x, sx); sy = fmaf(fyp.y, fyp.y, sy); sz = fmaf(fyp.y, fyp.z, sz);
-    sx = fmaf(-fym.y, fym.x, sx); sy = fmaf(-fym.y, fym.y, sy); sz = fmaf(-fym.y, fym.z, sz);
-    sx = fmaf(fzp.z, fzp.x, sx); sy = fmaf(fzp.z, fzp.y, sy); sz = fmaf(fzp.z, fzp.z, sz);
-    sx = fmaf(-fzm.z, fzm.x, sx); sy = fmaf(-fzm.z, fzm.y, sy); sz = fmaf(-fzm.z, fzm.z, sz);
     float L = Dxx * (exp_ + exm);
     L = fmaf(Dyy, eyp + eym, L);
     L = fmaf(Dzz, ezp + ezm, L);
-    float dv = (q.xp && q.xm) ? sx * (n.xp - n.xm) : 0.0f;
-    if (q.yp && q.ym) dv = fmaf(sy, n.yp - n.ym, dv);
-    if (q.zp && q.zm) dv = fmaf(sz, n.zp - n.zm, dv);
+    float dv = (q.xp && q.xm) ? sd.x * (n.xp - n.xm) : 0.0f;
+    if (q.yp && q.ym) dv = fmaf(sd.y, n.yp - n.ym, dv);
+    if (q.zp && q.zm) dv = fmaf(sd.z, n.zp - n.zm, dv);
     L = fmaf(a.c_s, dv, L);
     L = fmaf(Dxy, (d(q.pp, n.pp) + d(q.mm, n.mm)) - (d(q.pm, n.pm) + d(q.mp, n.mp)), L);
     L = fmaf(Dxz, (d(q.xpzp, n.xpzp) + d(q.xmzm, n.xmzm)) - (d(q.xpzm, n.xpzm) + d(q.xmzp, n.xmzp)), L);
@@ -1041,19 +1030,24 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
     using P = Plan<MODEL, MASKED, ANISO, TY, SURR, GATES>;
     static_assert(GATES == GATES_F32 || (MODEL == BBX_BR && !SURR), "16-bit gates: Beeler-Reuter without surrogate");
     constexpr int NG = P::NG, S32 = P::S - NG;  // 16-bit variables last
-    constexpr int S = P::S, TX = P::TX, UW = P::UW, MW = P::MW, NS = P::NS, CY = P::CY;
+    constexpr int S = P::S, TX = P::TX, UW = P::UW, MW = P::MW, CY = P::CY;
+    constexpr int NS = P::NA;            // ring A: loaded planes
+    constexpr int NB = P::NB;            // ring B: computed planes (0: nothing beyond V and the mask)
+    constexpr bool HB = P::HAS_B;
     constexpr int NCW = P::RY;  // consumer warps
     constexpr int NCT = 32 * NCW;        // consumer threads
     static_assert(TX == 64, "pair mapping assumes 64-node rows");
-    constexpr int FC = UW * P::UH;  // fibre component stride in a stage
+    constexpr int CB = TX * TY;  // component stride in a ring-B stage
 
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* smem =
-        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    unsigned char* wbufs = smem + NS * P::STAGE;  // surrogate buffers (SURR only)
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * P::STAGE + P::WBUF);
+    unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    unsigned char* bstages = smem + NS * P::A_STAGE;    // ring B
+    unsigned char* wbufs = bstages + NB * P::B_STAGE;   // surrogate buffers (SURR only)
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + P::BAR_OFF);
     uint64_t* empty = full + NS;
-    PieceSlot* ring = reinterpret_cast<PieceSlot*>(empty + NS);
+    uint64_t* fullb = empty + NS;
+    uint64_t* emptyb = fullb + NB;
+    PieceSlot* ring = reinterpret_cast<PieceSlot*>(emptyb + NB);
     __shared__ double red_scratch[32];
     __shared__ volatile int abort_flag;
 
@@ -1065,13 +1059,18 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], NCW);
         }
+        for (int s = 0; s < NB; ++s) {
+            mbar_init(&fullb[s], 1);
+            mbar_init(&emptyb[s], NCW);
+        }
         abort_flag = 0;
         mbar_init_fence();
     }
     __syncthreads();
 
     const int piece_begin = blockIdx.x * L.cta_stride, piece_end = piece_begin + L.cta_count[blockIdx.x];
-    int issued = 0;  // producer lane 0: plane loads issued
+    int issued = 0;   // producer lane 0: plane loads issued (ring A)
+    int issuedb = 0;  // producer lane 0: computed planes issued (ring B)
 
     if (warp == NCW) {
         // ---------------- producer warp ----------------
@@ -1094,6 +1093,16 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
             // (three planes; two tile rows of a sheet) issued now, expected on
             // their barriers but not yet arrived on (the arrival follows the
             // piece context, below).
+            // ring B copies of the computed plane z (tile rows from y0) of grid T
+            auto load_b = [&](const TissueArgs* T, int src, int x0, int y0, int z, int bslot, uint64_t* bar) {
+                unsigned char* sb = bstages + bslot * P::B_STAGE;
+                if (ANISO) {
+                    tma_load_4d(sb + P::F_OFF, &T->tm_f, x0 + 4, y0, z, 0, bar);  // fibres stored from x = -4
+                    tma_load_4d(sb + P::D_OFF, &T->tm_d, x0, y0, z, 0, bar);
+                }
+                if (S > 1 && S32 > 1) tma_load_4d(sb + P::S_OFF, &T->tm_s[src], x0, y0, z, 1, bar);
+                if (NG) tma_load_4d(sb + P::G_OFF, &T->tm_g[src], x0, y0, z, 0, bar);
+            };
             bool early = false;
             int n_early = 0;
             int4 pc_early = make_int4(0, 0, 0, 0);
@@ -1108,21 +1117,24 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                     const TissueArgs* T = &L.t0;
                     const int src = L.cur_hint;
                     const int nl = PLANAR ? z1 - z0 : z1 - z0 + 2;
-                    n_early = PLANAR ? min(nl, 2) : 3;
+                    n_early = PLANAR ? min(nl, 2) : 3;  // (3D: at most 2 computed planes; NB >= 2)
+                    if (HB && PLANAR && n_early > NB) n_early = NB;
 #pragma unroll 1
                     for (int off = 0; off < n_early; ++off) {
                         const int z = PLANAR ? 0 : z0 - 1 + off;
                         if (z < 0 || z >= T->nz) continue;
                         const int y0 = tile_row_of<PLANAR, TY>(pc_early, off);
                         uint64_t* bar = &full[off];
-                        unsigned char* st = smem + off * P::STAGE;
+                        unsigned char* st = smem + off * P::A_STAGE;
                         const bool halo = !PLANAR && ((off == 0) || (off == nl - 1));
-                        mbar_expect_tx(bar, (halo || S == 1) ? P::TX_BYTES_HALO : P::TX_BYTES);
+                        mbar_expect_tx(bar, P::A_BYTES);
                         tma_load_3d(st + P::U_OFF, &T->tm_u[src], pc_early.x - 4, y0 - 1, z, bar);
-                        if (ANISO) tma_load_4d(st + P::F_OFF, &T->tm_f, pc_early.x, y0 - 1, z, 0, bar);
                         if (MASKED) tma_load_3d(st + P::M_OFF, &T->tm_m, pc_early.x - 16, y0 - 1, z, bar);
-                        if (S > 1 && !halo) tma_load_4d(st + P::S_OFF, &T->tm_s[src], pc_early.x, y0, z, 1, bar);
-                        if (NG && !halo) tma_load_4d(st + P::G_OFF, &T->tm_g[src], pc_early.x, y0, z, 0, bar);
+                        if (HB && !halo) {  // computed plane b = off - 1 (3D) or off (sheet): slot b
+                            const int b = PLANAR ? off : off - 1;
+                            mbar_expect_tx(&fullb[b], P::B_BYTES);
+                            load_b(T, src, pc_early.x, y0, z, b, &fullb[b]);
+                        }
                     }
                 }
             }
@@ -1141,6 +1153,8 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                 const int nload = PLANAR ? pc.w - pc.z : pc.w - pc.z + 2;
                 for (int off = 0; off < nload; ++off) {
                     const int slot = issued % NS;
+                    const bool comp = PLANAR || (off >= 1 && off <= pc.w - pc.z);  // a computed plane: ring B too
+                    const int bslot = NB ? issuedb % NB : 0;
                     if (!ticketed && issued == NS) {
                         // the ring is full: the ticket's round trip overlaps the copies
                         start_ticket(L, d0);
@@ -1153,6 +1167,9 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                         stop = true;
                     } else if (issued >= NS &&
                                !mbar_wait_bounded(&empty[slot], ((issued / NS) - 1) & 1, L.wait_limit)) {
+                        stop = true;
+                    } else if (HB && comp && issuedb >= NB &&
+                               !mbar_wait_bounded(&emptyb[bslot], ((issuedb / NB) - 1) & 1, L.wait_limit)) {
                         stop = true;
                     }
                     if (stop || abort_flag) {
@@ -1184,22 +1201,24 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                     }
                     const int z = PLANAR ? 0 : pc.z - 1 + off;
                     const int y0 = tile_row_of<PLANAR, TY>(pc, off);  // first row of the tile
-                    const bool halo = !PLANAR && ((off == 0) || (off == nload - 1));
                     uint64_t* bar = &full[slot];
-                    unsigned char* st = smem + slot * P::STAGE;
+                    unsigned char* st = smem + slot * P::A_STAGE;
                     if (early && lp == 0 && off < n_early) {
                         mbar_arrive(bar);  // its copies were issued at the start
+                        if (HB && comp) mbar_arrive(&fullb[bslot]);
                     } else if (z < 0 || z >= nz) {
-                        mbar_arrive(bar);  // plane outside the array: nothing to load
+                        mbar_arrive(bar);  // plane outside the array: nothing to load (never a computed one)
                     } else {
-                        mbar_arrive_expect_tx(bar, (halo || S == 1) ? P::TX_BYTES_HALO : P::TX_BYTES);
+                        mbar_arrive_expect_tx(bar, P::A_BYTES);
                         tma_load_3d(st + P::U_OFF, &T->tm_u[src], pc.x - 4, y0 - 1, z, bar);
-                        if (ANISO) tma_load_4d(st + P::F_OFF, &T->tm_f, pc.x, y0 - 1, z, 0, bar);  // fibre x offset 4
                         if (MASKED) tma_load_3d(st + P::M_OFF, &T->tm_m, pc.x - 16, y0 - 1, z, bar);
-                        if (S > 1 && !halo) tma_load_4d(st + P::S_OFF, &T->tm_s[src], pc.x, y0, z, 1, bar);
-                        if (NG && !halo) tma_load_4d(st + P::G_OFF, &T->tm_g[src], pc.x, y0, z, 0, bar);
+                        if (HB && comp) {
+                            mbar_arrive_expect_tx(&fullb[bslot], P::B_BYTES);
+                            load_b(T, src, pc.x, y0, z, bslot, &fullb[bslot]);
+                        }
                     }
                     ++issued;
+                    if (HB && comp) ++issuedb;
                 }
             }
             if (!ticketed) start_ticket(L, d0);  // every CTA takes it, also on a short or aborted run
@@ -1212,16 +1231,18 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
         F2 vsum = {0.0f, 0.0f};
         bool timed_out = false;
         int jb = 0, lp = 0;  // load index of the first plane of the piece, local piece index
-        auto wait_slot = [&](int slot, int parity) {
+        int sb = 0, pb = 0;  // ring B: slot and phase parity of the next computed plane
+        auto wait_bar = [&](uint64_t* bar, int parity) {
             if (timed_out || abort_flag) {
                 timed_out = true;
                 return;
             }
-            if (!mbar_wait_bounded(&full[slot], parity, L.wait_limit)) {
+            if (!mbar_wait_bounded(bar, parity, L.wait_limit)) {
                 timed_out = true;
                 abort_flag = 1;
             }
         };
+        auto wait_slot = [&](int slot, int parity) { wait_bar(&full[slot], parity); };
         auto wait_full = [&](int j) { wait_slot(j % NS, (j / NS) & 1); };
         for (int pi = piece_begin; pi < piece_end; ++pi, ++lp) {
             wait_full(jb);  // the piece's first load carries its context
@@ -1250,21 +1271,22 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                         pw ^= 1;
                     }
                 }
+                if (HB) wait_bar(&fullb[sb], pb);  // the plane's own fibres, W-tilde sums, other variables
                 const int k = PLANAR ? 0 : pc.z + t;
                 const int yb = (PLANAR ? (pc.z + t) * TY : pc.y) + row0;  // y of this thread's first row
-                const unsigned char* stc = smem + (PLANAR ? sp : sc) * P::STAGE;
-                const unsigned char* stp = PLANAR ? stc : smem + sp * P::STAGE;
-                const unsigned char* stn = PLANAR ? stc : smem + sn * P::STAGE;
+                const unsigned char* stc = smem + (PLANAR ? sp : sc) * P::A_STAGE;
+                const unsigned char* stp = PLANAR ? stc : smem + sp * P::A_STAGE;
+                const unsigned char* stn = PLANAR ? stc : smem + sn * P::A_STAGE;
+                const unsigned char* stb = bstages + sb * P::B_STAGE;
                 const float* Up = reinterpret_cast<const float*>(stp + P::U_OFF);
                 const float* Uc = reinterpret_cast<const float*>(stc + P::U_OFF);
                 const float* Un = reinterpret_cast<const float*>(stn + P::U_OFF);
-                const float* Fp = reinterpret_cast<const float*>(stp + P::F_OFF);
-                const float* Fc = reinterpret_cast<const float*>(stc + P::F_OFF);
-                const float* Fn = reinterpret_cast<const float*>(stn + P::F_OFF);
+                const float* Fb = reinterpret_cast<const float*>(stb + P::F_OFF);  // [3][TY][TX]
+                const float* Db = reinterpret_cast<const float*>(stb + P::D_OFF);  // [3][TY][TX]
                 const unsigned char* Mp = stp + P::M_OFF;
                 const unsigned char* Mc = stc + P::M_OFF;
                 const unsigned char* Mn = stn + P::M_OFF;
-                const float* Sv = reinterpret_cast<const float*>(stc + P::S_OFF);
+                const float* Sv = reinterpret_cast<const float*>(stb + P::S_OFF);
                 const bool zn_ok = k + 1 < a.nz, zp_ok = k > 0;
                 const int c0 = (row0 + 1) * UW + (2 * tx + 4);   // stage index of node (x, yb), even
                 const int m0 = (row0 + 1) * MW + (2 * tx + 16);  // mask index of node (x, yb)
@@ -1282,13 +1304,11 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                     float Lr[CY][2], u0r[CY][2];
                     bool live[CY][2];
                     float2 wA[3], wB[3], wC[3], wN[3], wP[3];
-                    float2 wFx[3], wFy[3], wFz[3];
     #pragma unroll
                     for (int w = 0; w < 2; ++w) {
                         const int o = c0 + (w - 1) * UW;
                         wA[w] = ld2(Uc, o - 2); wB[w] = ld2(Uc, o); wC[w] = ld2(Uc, o + 2);
                         wN[w] = ld2(Un, o); wP[w] = ld2(Up, o);
-                        if (ANISO) { wFx[w] = ld2(Fc, o); wFy[w] = ld2(Fc + FC, o); wFz[w] = ld2(Fc + 2 * FC, o); }
                     }
     #pragma unroll
                     for (int r = 0; r < CY; ++r) {
@@ -1299,7 +1319,6 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                             const int o = c + UW;  // row r+1
                             wA[2] = ld2(Uc, o - 2); wB[2] = ld2(Uc, o); wC[2] = ld2(Uc, o + 2);
                             wN[2] = ld2(Un, o); wP[2] = ld2(Up, o);
-                            if (ANISO) { wFx[2] = ld2(Fc, o); wFy[2] = ld2(Fc + FC, o); wFz[2] = ld2(Fc + 2 * FC, o); }
                         }
                         bool tis[2] = {x_in && y < a.ny, x_in && y < a.ny && x1_in}, intr[2];
                         if (MASKED) {
@@ -1312,7 +1331,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                             intr[0] = intr[1] = (y > 0) && (y + 1 < a.ny) && (PLANAR || (zp_ok && zn_ok));  // warp-uniform
                         }
                         Nb n[2];
-                        F3 f[2], fxp[2], fxm[2], fyp[2], fym[2], fzp[2], fzm[2];
+                        F3 f[2], sd[2];
                         n[0].u0 = wB[1].x; n[0].xp = wB[1].y; n[0].xm = wA[1].y;
                         n[0].yp = wB[2].x; n[0].ym = wB[0].x; n[0].zp = wN[1].x; n[0].zm = wP[1].x;
                         n[1].u0 = wB[1].y; n[1].xp = wC[1].x; n[1].xm = wB[1].x;
@@ -1326,30 +1345,17 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                             n[1].pp = wC[2].x; n[1].mm = wB[0].x; n[1].pm = wC[0].x; n[1].mp = wB[2].x;
                             n[1].xpzp = nC.x; n[1].xmzm = wP[1].x; n[1].xpzm = pC.x; n[1].xmzp = wN[1].x;
                             n[1].ypzp = wN[2].y; n[1].ymzm = wP[0].y; n[1].ypzm = wP[2].y; n[1].ymzp = wN[0].y;
-                            const float2 fAx = ld2(Fc, c - 2), fAy = ld2(Fc + FC, c - 2), fAz = ld2(Fc + 2 * FC, c - 2);
-                            const float2 fCx = ld2(Fc, c + 2), fCy = ld2(Fc + FC, c + 2), fCz = ld2(Fc + 2 * FC, c + 2);
-                            const float2 fNx = ld2(Fn, c), fNy = ld2(Fn + FC, c), fNz = ld2(Fn + 2 * FC, c);
-                            const float2 fPx = ld2(Fp, c), fPy = ld2(Fp + FC, c), fPz = ld2(Fp + 2 * FC, c);
-                            f[0] = F3{wFx[1].x, wFy[1].x, wFz[1].x};
-                            f[1] = F3{wFx[1].y, wFy[1].y, wFz[1].y};
-                            fxp[0] = f[1];
-                            fxm[0] = F3{fAx.y, fAy.y, fAz.y};
-                            fxp[1] = F3{fCx.x, fCy.x, fCz.x};
-                            fxm[1] = f[0];
-                            fyp[0] = F3{wFx[2].x, wFy[2].x, wFz[2].x};
-                            fyp[1] = F3{wFx[2].y, wFy[2].y, wFz[2].y};
-                            fym[0] = F3{wFx[0].x, wFy[0].x, wFz[0].x};
-                            fym[1] = F3{wFx[0].y, wFy[0].y, wFz[0].y};
-                            fzp[0] = F3{fNx.x, fNy.x, fNz.x};
-                            fzp[1] = F3{fNx.y, fNy.y, fNz.y};
-                            fzm[0] = F3{fPx.x, fPy.x, fPz.x};
-                            fzm[1] = F3{fPx.y, fPy.y, fPz.y};
+                            // the pair's own fibres and W-tilde sums ([comp][row][x] in ring B)
+                            const int bo = (row0 + r) * TX + 2 * tx;
+                            const float2 fx = ld2(Fb, bo), fy = ld2(Fb + CB, bo), fz = ld2(Fb + 2 * CB, bo);
+                            const float2 dx = ld2(Db, bo), dy = ld2(Db + CB, bo), dz = ld2(Db + 2 * CB, bo);
+                            f[0] = F3{fx.x, fy.x, fz.x};
+                            f[1] = F3{fx.y, fy.y, fz.y};
+                            sd[0] = F3{dx.x, dy.x, dz.x};
+                            sd[1] = F3{dx.y, dy.y, dz.y};
                         } else {
     #pragma unroll
-                            for (int e = 0; e < 2; ++e) {
-                                f[e] = F3{0.f, 0.f, 0.f};
-                                fxp[e] = fxm[e] = fyp[e] = fym[e] = fzp[e] = fzm[e] = f[e];
-                            }
+                            for (int e = 0; e < 2; ++e) f[e] = sd[e] = F3{0.f, 0.f, 0.f};
                         }
     #pragma unroll
                         for (int e = 0; e < 2; ++e) {
@@ -1358,11 +1364,9 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                             // fast formula for every node (values of void or
                             // out-of-array nodes are finite and never stored) ...
                             if (MASKED)
-                                Lr[r][e] = lap_interior<ANISO>(a, n[e], f[e], fxp[e], fxm[e], fyp[e], fym[e], fzp[e],
-                                                               fzm[e]);
+                                Lr[r][e] = lap_interior<ANISO>(a, n[e], f[e], sd[e]);
                             else
-                                Lr[r][e] = lap_xbound<ANISO>(a, n[e], e ? px1 : px0, e ? mx1 : mx0, f[e], fxp[e],
-                                                             fxm[e], fyp[e], fym[e], fzp[e], fzm[e]);
+                                Lr[r][e] = lap_xbound<ANISO>(a, n[e], e ? px1 : px0, e ? mx1 : mx0, f[e], sd[e]);
                         }
                         // ... and the general one where a y/z neighbour (or, in a
                         // masked grid, any neighbour) may be void: rare, and
@@ -1390,17 +1394,12 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                                     q.xpzp = xp && zn_ok; q.xmzm = xm && zp_ok; q.xpzm = xp && zp_ok; q.xmzp = xm && zn_ok;
                                     q.ypzp = yp && zn_ok; q.ymzm = ym && zp_ok; q.ypzm = yp && zp_ok; q.ymzp = ym && zn_ok;
                                 }
-                                Lr[r][e] = lap_general<ANISO>(a, n[e], q, f[e], fxp[e], fxm[e], fyp[e], fym[e], fzp[e],
-                                                              fzm[e]);
+                                Lr[r][e] = lap_general<ANISO>(a, n[e], q, f[e], sd[e]);
                             }
                         }
                         // slide the window down one row
                         wA[0] = wA[1]; wA[1] = wA[2]; wB[0] = wB[1]; wB[1] = wB[2]; wC[0] = wC[1]; wC[1] = wC[2];
                         wN[0] = wN[1]; wN[1] = wN[2]; wP[0] = wP[1]; wP[1] = wP[2];
-                        if (ANISO) {
-                            wFx[0] = wFx[1]; wFx[1] = wFx[2]; wFy[0] = wFy[1]; wFy[1] = wFy[2];
-                            wFz[0] = wFz[1]; wFz[1] = wFz[2];
-                        }
                     }
     
                     // phase 2: reaction, stores, activation, tissue sum (predicated)
@@ -1421,7 +1420,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
     #pragma unroll
                         for (int v = S32; v < S; ++v) {  // 16-bit gates, decoded to FP32
                             const uint32_t w = *reinterpret_cast<const uint32_t*>(
-                                stc + P::G_OFF + 2 * ((v - S32) * TX * TY + (row0 + r) * TX + 2 * tx));
+                                stb + P::G_OFF + 2 * ((v - S32) * TX * TY + (row0 + r) * TX + 2 * tx));
                             const float2 gv = gate_decode2<GATES>(w);
                             yv[0][v] = gv.x;
                             yv[1][v] = gv.y;
@@ -1532,7 +1531,14 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                 }
     
                     __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[sp]);
+                if (lane == 0) {
+                    mbar_arrive(&empty[sp]);
+                    if (HB) mbar_arrive(&emptyb[sb]);
+                }
+                if (HB && ++sb == NB) {
+                    sb = 0;
+                    pb ^= 1;
+                }
                 sp = sc;
                 sc = sn;
                 sn = sn + 1 == NS ? 0 : sn + 1;
@@ -1568,6 +1574,8 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
         atomicOr(L.err, ERRBIT_TIMEOUT);
         for (int j = issued > NS ? issued - NS : 0; j < issued; ++j)
             (void)mbar_wait_bounded(&full[j % NS], (j / NS) & 1, L.wait_limit);
+        for (int j = issuedb > NB ? issuedb - NB : 0; j < issuedb; ++j)
+            (void)mbar_wait_bounded(&fullb[j % NB], (j / NB) & 1, L.wait_limit);
     }
     step_finalize(L, red_scratch);
 }

@@ -1049,10 +1049,13 @@ int encode_targs(const bbx_grid* g, int ty, TissueArgs* t) {
     if (g->aniso) {
         const cuuint64_t fd4[4] = {(cuuint64_t)g->pxf, (cuuint64_t)g->ny, (cuuint64_t)g->nz, 3};
         const cuuint64_t fstr4[3] = {(cuuint64_t)g->pxf * 4, (cuuint64_t)g->fplane * 4, (cuuint64_t)g->fvol * 4};
-        const cuuint32_t fbox[4] = {(cuuint32_t)(kTileX + 8), (cuuint32_t)(ty + 2), 1, 3};
+        const cuuint32_t fbox[4] = {(cuuint32_t)kTileX, (cuuint32_t)ty, 1, 3};  // a tile's own fibres
         if (!encode(&t->tm_f, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->d_fib, fd4, fstr4, fbox)) return BBX_ERR_CUDA;
+        const cuuint64_t dd4[4] = {(cuuint64_t)g->nx, (cuuint64_t)g->ny, (cuuint64_t)g->nz, 3};
+        if (!encode(&t->tm_d, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->d_div, dd4, str4, fbox)) return BBX_ERR_CUDA;
     } else {
         t->tm_f = t->tm_u[0];
+        t->tm_d = t->tm_u[0];
     }
     if (g->d_mask) {
         const cuuint64_t mstr[2] = {(cuuint64_t)g->px, (cuuint64_t)g->plane};
