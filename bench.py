@@ -472,7 +472,10 @@ def run_configs(args, dev, stream, dist=None, n_ranks=1):
         gates = {"_u16": bbx.BBX_GATES_UNORM16, "_f16": bbx.BBX_GATES_FP16}.get(name[-4:], bbx.BBX_GATES_FP32)
         if gates != bbx.BBX_GATES_FP32:
             G.set_gate_storage(gates)
-        G.autotune(w.dt)
+        if args.config_tile:
+            G.set_tiling(*(int(v) for v in args.config_tile.split(",")))
+        else:
+            G.autotune(w.dt)
         G.write_all(st)
         del st
         resident = False
@@ -506,37 +509,66 @@ def run_configs(args, dev, stream, dist=None, n_ranks=1):
 
 
 def run_output(args, dev, stream, G, w, n_tissue):
-    """The headless output kernels on the bench slab: a 3-layer byte frame
-    (15 B per node: three float layers read, three bytes written) and the
-    phase singularities of (u, v) (8 B per node), device-timed, L2 flushed
-    before each call."""
+    """The headless output kernels, device-timed, L2 flushed (write, then read)
+    before each call:
+    on the bench slab the sample script's colour map as a byte frame (red = u,
+    green = v: two float layers read, three bytes written per node), and the
+    phase singularities of (u, v) (8 B per node) on the same slab started from
+    a cross-field condition (u = 1 where x < nx/2, v = 0.5 where y < ny/2,
+    every z) and stepped until the broken front has curled into a scroll wave
+    whose filament crosses every z cross-section."""
+    import numpy as np
     import torch
+    from paper_1605_06015_gb300 import bbx
     peak, _ = load_peaks()
     frame = torch.empty(3 * w.n_cells, dtype=torch.uint8, device=dev)
     xyz = torch.empty(3 * 65536, dtype=torch.float32, device=dev)
+    # L2 flush before each call as in the step timing: a 256 MiB write, then a
+    # 256 MiB read, so that no dirty line of the flush is left for the timed
+    # kernel to write back
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush_rd = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    sink = torch.empty((), dtype=torch.float32, device=dev)
+    # the scroll-wave state
+    S = bbx.Grid(w.nx, w.ny, w.nz, w.h, w.mask, stream=stream)
+    S.set_fibres(w.fibres, w.D_par, w.D_perp)
+    S.set_ionic_model(w.model, w.params)
+    st = np.zeros((2,) + w.shape, np.float32)
+    st[0, :, :, : w.nx // 2] = 1.0
+    st[1, :, : w.ny // 2, :] = 0.5
+    S.write_all(st)
+    S.step(w.dt, args.scroll_steps)
+    layers = (0, 1, -1)
     res = {}
-    for name in ("ppm_frame", "phase_singularities"):
+    for name, grid in (("ppm_frame", G), ("phase_singularities", S)):
         ts, found = [], 0
         for i in range(12):
             flush.fill_(float(i))
+            torch.sum(flush_rd, dim=0, out=sink)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             if name == "ppm_frame":
-                G.ppm_frame((0, 1, -1), (0.0, 0.0, 0.0), (1.0, 0.8, 1.0), frame)
+                grid.ppm_frame(layers, (0.0, 0.0, 0.0), (1.0, 0.8, 1.0), frame)
             else:
-                found = G.phase_singularities(0, 0.5, 1, 0.3, xyz, 65536)
+                found = grid.phase_singularities(0, 0.5, 1, 0.3, xyz, 65536)
             e1.record(stream)
             torch.cuda.synchronize()
             if i >= 2:
                 ts.append(e0.elapsed_time(e1) * 1e-3)
         sec = sum(ts) / len(ts)
-        b = 15 if name == "ppm_frame" else 8
+        if name == "ppm_frame":
+            b = 4 * sum(1 for c in layers if c >= 0) + 3 + (1 if w.mask is not None else 0)
+        else:
+            b = 8 + (1 if w.mask is not None else 0)
         res[name] = {"us_per_call": sec * 1e6, "bytes_per_node": b, "GB_s": b * w.n_cells / sec / 1e9,
                      "roofline_frac": b * w.n_cells / sec / 1e9 / peak}
         if name != "ppm_frame":
             res[name]["points"] = found
+            res[name]["state"] = "scroll wave: cross-field start, %d steps" % args.scroll_steps
+        else:
+            res[name]["layers"] = list(layers)
+    S.close()
     return res
 
 
@@ -707,10 +739,12 @@ def main():
     ap.add_argument("--batch-3d", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=48)
     ap.add_argument("--tile", default=None, help="TY,TZ brick shape instead of autotuning")
+    ap.add_argument("--config-tile", default=None, help="TY,TZ brick shape of the --configs workloads instead of autotuning")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--configs", default="fhn_200,fhn_16384,barkley_512x512x256,br_shell_512,br_256x256x64,br_mrl_256x256x64,"
                             "br_256x256x64_tab,br_shell_512_tab,br_shell_512_u16,br_shell_512_f16,br_256x256x64_u16",
                     help="comma-separated other workloads to time by differencing ('' for none)")
+    ap.add_argument("--scroll-steps", type=int, default=2000)
     ap.add_argument("--surrogate-pairs", type=int, default=10_000_000)
     ap.add_argument("--surrogate-traj-steps", type=int, default=6000)
     ap.add_argument("--surrogate-train-steps", type=int, default=4000)

@@ -526,6 +526,12 @@ int bbx_debug_cover_chunks(const uint8_t* flags, int ncx, int nby, int nbz, int 
                            int cap, int* count);
 int bbx_debug_plan_first_pieces(const int* segs4, int nsegs, int ctas, int* out, int cap, int* used);
 
+/* GPU test hook: out_dev[i] = the e^x - 1 the Beeler-Reuter kernels use
+ * (the Taylor series about 0 for |x| < 0.25, else e^x - 1) and ref_dev[i] =
+ * CUDA's expm1f, for n floats x_dev (device memory).  Synchronises the
+ * stream.  Errors: BBX_ERR_ARG, BBX_ERR_CUDA. */
+int bbx_debug_expm1(const float* x_dev, float* out_dev, float* ref_dev, int n, void* cuda_stream);
+
 /* Static text for a status code. */
 const char* bbx_status_string(int status);
 

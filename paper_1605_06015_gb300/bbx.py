@@ -94,6 +94,7 @@ def _load():
         "bbx_batch_sync": [P],
         "bbx_batch_autotune": [P, ctypes.POINTER(D)],
         "bbx_batch_info": [P, ctypes.POINTER(I), ctypes.POINTER(I), I],
+        "bbx_debug_expm1": [P, P, P, I, P],
         "bbx_set_gate_storage": [P, I],
         "bbx_set_halo_planes": [P, I, I],
         "bbx_halo_exchange": [P, P],
@@ -454,6 +455,12 @@ def bbx_batch_info(b):
 
 def bbx_batch_destroy(b):
     _lib.bbx_batch_destroy(b)
+
+
+def bbx_debug_expm1(x_dev, out_dev, ref_dev, stream=None):
+    """The kernels' e^x - 1 and CUDA's expm1f of device tensors (test hook)."""
+    _check(_lib.bbx_debug_expm1(_devptr(x_dev), _devptr(out_dev), _devptr(ref_dev), int(x_dev.numel()),
+                                _stream_handle(stream)), "bbx_debug_expm1")
 
 
 def bbx_set_gate_storage(g, mode):

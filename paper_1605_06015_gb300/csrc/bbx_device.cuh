@@ -445,6 +445,23 @@ __device__ __forceinline__ void rk4_update(const float* mp, float* y, float L, f
 // Rate constants of the 1977 publication, written out per gate.
 __device__ __forceinline__ float br_ratio(float num, float den) { return __fdividef(num, den); }
 
+// e^x - 1 in FP32: near 0 the Taylor series of e^x - 1 about 0 up to x^7/5040
+// (|x| < 0.25: the first omitted term is below 2e-9 of the value), elsewhere
+// the difference e^x - 1, whose cancellation is bounded there (e^x - 1 >= 0.22
+// for x >= 0.25, <= -0.22 for x <= -0.25).
+__device__ __forceinline__ float expm1_br(float x) {
+    if (fabsf(x) < 0.25f) {
+        float p = fmaf(x, 1.0f / 5040.0f, 1.0f / 720.0f);
+        p = fmaf(x, p, 1.0f / 120.0f);
+        p = fmaf(x, p, 1.0f / 24.0f);
+        p = fmaf(x, p, 1.0f / 6.0f);
+        p = fmaf(x, p, 0.5f);
+        p = fmaf(x, p, 1.0f);
+        return x * p;
+    }
+    return __expf(x) - 1.0f;
+}
+
 // Voltage tables of the Beeler-Reuter models: kTabN entries kTabDv mV apart
 // from kTabVmin (-120 to +80 mV), 16 floats (4 float4) each; V outside the
 // range takes the end entry.  Entry index and interpolation weight of V.
@@ -467,7 +484,7 @@ struct Model<BBX_BR> {
     // The change of every variable over one step (the update is y + d): the
     // Euler increments of V and Ca, and the Rush-Larsen increments of the
     // gates, Eq. (RL) read as y' = A y + B, i.e. d = (1 - A)(y_inf - y) with
-    // 1 - A by expm1f (no cancellation when (alpha+beta) dt is small).
+    // 1 - A by expm1_br (no cancellation when (alpha+beta) dt is small).
     __device__ static __forceinline__ void increment(const float* mp, const float* y, float L, float Is, float dt,
                                                      float* d) {
         increment_m3(mp, y, y[3] * y[3] * y[3], L, Is, dt, d);
@@ -486,7 +503,7 @@ struct Model<BBX_BR> {
         const float Is_ = mp[3] * dd * f * (V - Es);
         const float Ix1 = x1 * 0.8f * (__expf(0.04f * (V + 77.0f)) - 1.0f) * __expf(-0.04f * (V + 35.0f));
         const float w = V + 23.0f;
-        const float lin = (w == 0.0f) ? 5.0f : br_ratio(0.2f * w, -expm1f(-0.04f * w));
+        const float lin = (w == 0.0f) ? 5.0f : br_ratio(0.2f * w, -expm1_br(-0.04f * w));
         const float IK1 = 0.35f * (br_ratio(4.0f * (__expf(0.04f * (V + 85.0f)) - 1.0f),
                                             __expf(0.08f * (V + 53.0f)) + __expf(0.04f * (V + 53.0f))) +
                                    lin);
@@ -497,7 +514,7 @@ struct Model<BBX_BR> {
         const float a_x1 = br_ratio(0.0005f * __expf(0.083f * (V + 50.0f)), __expf(0.057f * (V + 50.0f)) + 1.0f);
         const float b_x1 = br_ratio(0.0013f * __expf(-0.06f * (V + 20.0f)), __expf(-0.04f * (V + 20.0f)) + 1.0f);
         const float xm = V + 47.0f;
-        const float a_m = (xm == 0.0f) ? 10.0f : br_ratio(-xm, expm1f(-0.1f * xm));
+        const float a_m = (xm == 0.0f) ? 10.0f : br_ratio(-xm, expm1_br(-0.1f * xm));
         const float b_m = 40.0f * __expf(-0.056f * (V + 72.0f));
         const float a_h = 0.126f * __expf(-0.25f * (V + 77.0f));
         const float b_h = br_ratio(1.7f, __expf(-0.082f * (V + 22.5f)) + 1.0f);
@@ -520,7 +537,7 @@ struct Model<BBX_BR> {
 
     __device__ static __forceinline__ float rl_inc(float y, float al, float be, float dt) {
         const float s = al + be;
-        const float one_minus_A = -expm1f(-s * dt);
+        const float one_minus_A = -expm1_br(-s * dt);
         return one_minus_A * (__fdividef(al, s) - y);
     }
 

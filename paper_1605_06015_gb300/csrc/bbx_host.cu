@@ -2654,6 +2654,25 @@ extern "C" int bbx_debug_cover_chunks(const uint8_t* flags, int ncx, int nby, in
     return BBX_OK;
 }
 
+namespace {
+// The step kernels' e^x - 1 next to CUDA's expm1f, for the accuracy test.
+__global__ void k_debug_expm1(const float* __restrict__ x, float* __restrict__ y, float* __restrict__ ref, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        y[i] = expm1_br(x[i]);
+        ref[i] = expm1f(x[i]);
+    }
+}
+}  // namespace
+
+extern "C" int bbx_debug_expm1(const float* x_dev, float* out_dev, float* ref_dev, int n, void* cuda_stream) {
+    if (!x_dev || !out_dev || !ref_dev || n <= 0) return BBX_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    k_debug_expm1<<<n_blocks_for(n, 256), 256, 0, s>>>(x_dev, out_dev, ref_dev, n);
+    BBX_CUDA(cudaGetLastError());
+    BBX_CUDA(cudaStreamSynchronize(s));
+    return BBX_OK;
+}
+
 extern "C" int bbx_debug_plan_first_pieces(const int* segs4, int nsegs, int ctas, int* out, int cap, int* used) {
     if (!segs4 || nsegs <= 0 || ctas <= 0 || !out || !used) return BBX_ERR_ARG;
     std::vector<Seg> segs((size_t)nsegs);

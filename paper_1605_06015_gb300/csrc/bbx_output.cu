@@ -15,64 +15,84 @@ constexpr uint8_t kTissue = 1;  // mask bit 0: the node is tissue
 
 // t = (v - lo) / (hi - lo) clamped to [0, 1]; code = floor(255 t + 0.5), each
 // operation rounded once (no contraction), so the host can reproduce it.
-__device__ __forceinline__ uint8_t quantise(float v, float lo, float span) {
-    float t = __fdiv_rn(__fsub_rn(v, lo), span);
-    t = fminf(fmaxf(t, 0.0f), 1.0f);
-    return (uint8_t)floorf(__fadd_rn(__fmul_rn(t, 255.0f), 0.5f));
+// The quotient is first formed as (v - lo) times the rounded reciprocal of the
+// span: it differs from the rounded quotient by at most about 3 units in its
+// last place, i.e. 255 t + 0.5 by less than 1e-4, so the floor is the same
+// unless 255 t + 0.5 lies within 1e-4 of an integer; there the exact division
+// decides.  (The division's own slow path, which denormal inputs such as a
+// decaying resting variable take, is then rarely reached.)
+__device__ __forceinline__ uint8_t quantise(float v, float lo, float span, float rspan) {
+    const float d = __fsub_rn(v, lo);
+    float t = fminf(fmaxf(__fmul_rn(d, rspan), 0.0f), 1.0f);
+    float q = __fadd_rn(__fmul_rn(t, 255.0f), 0.5f);
+    const float fr = q - floorf(q);
+    if (fr < 1e-4f || fr > 1.0f - 1e-4f) {
+        t = fminf(fmaxf(__fdiv_rn(d, span), 0.0f), 1.0f);
+        q = __fadd_rn(__fmul_rn(t, 255.0f), 0.5f);
+    }
+    return (uint8_t)floorf(q);
 }
 
-// One thread per group of 4 consecutive nodes of a row: float4 loads from the
-// padded rows (px is a multiple of 32) and three 32-bit stores of the 12
-// bytes, except in a row's last partial group.  The current buffer is picked
-// on the device from the grid's parity, so the call does not synchronise.
+// Each warp takes whole rows (y, z): its lanes walk the row in groups of 4
+// consecutive nodes, float4 loads from the padded rows (px is a multiple of
+// 32) and three 32-bit stores of the 12 bytes of a group, except in a row's
+// last partial group or where the output row is not 4-byte aligned.  Rows are
+// spread over the warps of the grid, so the only divisions are one per row.
+// The current buffer is picked on the device from the grid's parity, so the
+// call does not synchronise.
 __global__ void k_ppm(const float* __restrict__ s0, const float* __restrict__ s1, const int* __restrict__ cur,
                       const uint8_t* __restrict__ mask, long long vol, int nx, int ny, int nz, int px,
                       long long plane, int3 layer, float3 lo, float3 span, uint8_t* __restrict__ out) {
     const float* state = *cur ? s1 : s0;
     const int gx = (nx + 3) / 4;
-    const long long n = (long long)gx * ny * nz;
+    const long long rows = (long long)ny * nz;
     const int ly[3] = {layer.x, layer.y, layer.z};
     const float l[3] = {lo.x, lo.y, lo.z}, sp[3] = {span.x, span.y, span.z};
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = int(i % gx) * 4;
-        const long long r = i / gx;
-        const int y = int(r % ny), z = int(r / ny);
-        const long long gi = z * plane + (long long)y * px + x;
-        const long long oi = ((long long)z * ny + y) * nx + x;  // first node of the group in the output
-        uint8_t c[4][3] = {};
-        bool tis[4] = {true, true, true, true};
-        if (mask) {
-            const uchar4 m = *reinterpret_cast<const uchar4*>(mask + gi);
-            tis[0] = m.x & kTissue; tis[1] = m.y & kTissue; tis[2] = m.z & kTissue; tis[3] = m.w & kTissue;
-        }
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            if (ly[ch] < 0) continue;
-            const float4 v = *reinterpret_cast<const float4*>(state + ly[ch] * vol + gi);
-            const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) c[k][ch] = tis[k] ? quantise(vv[k], l[ch], sp[ch]) : 0;
-        }
-        if (x + 4 <= nx && (oi & 3) == 0) {
-            uint32_t w[3];
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                w[b] = 0;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int byte = 4 * b + k;  // byte of the 12-byte group
-                    w[b] |= (uint32_t)c[byte / 3][byte % 3] << (8 * k);
-                }
+    const float rs[3] = {__frcp_rn(span.x), __frcp_rn(span.y), __frcp_rn(span.z)};
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+        const int z = (int)(r / ny), y = (int)(r - (long long)z * ny);
+        const float* row = state + z * plane + (long long)y * px;
+        const uint8_t* mrow = mask ? mask + z * plane + (long long)y * px : nullptr;
+        uint8_t* orow = out + 3 * (((long long)z * ny + y) * nx);
+        const bool aligned = ((((long long)z * ny + y) * nx) & 3) == 0;
+        for (int g = lane; g < gx; g += 32) {
+            const int x = 4 * g;
+            uint8_t c[4][3] = {};
+            bool tis[4] = {true, true, true, true};
+            if (mrow) {
+                const uchar4 m = *reinterpret_cast<const uchar4*>(mrow + x);
+                tis[0] = m.x & kTissue; tis[1] = m.y & kTissue; tis[2] = m.z & kTissue; tis[3] = m.w & kTissue;
             }
-            uint32_t* o = reinterpret_cast<uint32_t*>(out + 3 * oi);
-            o[0] = w[0];
-            o[1] = w[1];
-            o[2] = w[2];
-        } else {
-            for (int k = 0; k < 4 && x + k < nx; ++k)
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) out[3 * (oi + k) + ch] = c[k][ch];
+            for (int ch = 0; ch < 3; ++ch) {
+                if (ly[ch] < 0) continue;
+                const float4 v = *reinterpret_cast<const float4*>(row + ly[ch] * vol + x);
+                const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) c[k][ch] = tis[k] ? quantise(vv[k], l[ch], sp[ch], rs[ch]) : 0;
+            }
+            if (x + 4 <= nx && aligned) {
+                uint32_t w[3];
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    w[b] = 0;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int byte = 4 * b + k;  // byte of the 12-byte group
+                        w[b] |= (uint32_t)c[byte / 3][byte % 3] << (8 * k);
+                    }
+                }
+                uint32_t* o = reinterpret_cast<uint32_t*>(orow + 3 * x);
+                o[0] = w[0];
+                o[1] = w[1];
+                o[2] = w[2];
+            } else {
+                for (int k = 0; k < 4 && x + k < nx; ++k)
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) orow[3 * (x + k) + ch] = c[k][ch];
+            }
         }
     }
 }
@@ -87,7 +107,7 @@ __device__ __forceinline__ int cell_crossings(const float g[4], float2 p[2]) {
     for (int i = 0; i < 4; ++i) {
         const int j = (i + 1) & 3;
         if ((g[i] > 0.0f) != (g[j] > 0.0f)) {
-            const float s = __fdiv_rn(g[i], __fsub_rn(g[i], g[j]));
+            const float s = __fdividef(g[i], __fsub_rn(g[i], g[j]));  // |g[i] - g[j]| > 0, far below 2^126
             if (n < 2) p[n] = make_float2(cx[i] + s * (cx[j] - cx[i]), cy[i] + s * (cy[j] - cy[i]));
             ++n;
         }
@@ -102,13 +122,14 @@ __global__ void k_singz(const float* __restrict__ s0, const float* __restrict__ 
     const float* st = *cur ? s1 : s0;  // the current buffer, from the grid's parity
     const float* fa = st + off_a;
     const float* fb = st + off_b;
-    const long long cx = nx - 1, cy = ny - 1;
-    const long long n = cx * cy * nz;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = int(i % cx);
-        const long long r = i / cx;
-        const int y = int(r % cy), z = int(r / cy);
+    // each warp takes whole rows of cells (y, z), its lanes walking x
+    const int cx = nx - 1, cy = ny - 1;
+    const long long rows = (long long)cy * nz;
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long rr = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); rr < rows; rr += warps)
+    for (int x = lane; x < cx; x += 32) {
+        const int z = (int)(rr / cy), y = (int)(rr - (long long)z * cy);
         const long long g0 = z * plane + (long long)y * px + x;
         const long long gi[4] = {g0, g0 + 1, g0 + px + 1, g0 + px};  // corners in cell order
         bool tis = true;
@@ -131,8 +152,9 @@ __global__ void k_singz(const float* __restrict__ s0, const float* __restrict__ 
         const float det = d1y * d2x - d1x * d2y;
         if (det == 0.0f) continue;
         const float rx = pb[0].x - pa[0].x, ry = pb[0].y - pa[0].y;
-        const float al = (ry * d2x - rx * d2y) / det;
-        const float be = (d1x * ry - d1y * rx) / det;
+        const float rdet = __frcp_rn(det);
+        const float al = (ry * d2x - rx * d2y) * rdet;
+        const float be = (d1x * ry - d1y * rx) * rdet;
         if (!(al >= 0.0f && al <= 1.0f && be >= 0.0f && be <= 1.0f)) continue;
         const int k = atomicAdd(count, 1);
         if (k < max_points) {
@@ -143,19 +165,15 @@ __global__ void k_singz(const float* __restrict__ s0, const float* __restrict__ 
     }
 }
 
-int blocks_for(long long n, int num_sms) {
-    long long b = (n + 255) / 256;
-    const long long cap = (long long)num_sms * 8;
-    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
-}
-
 }  // namespace
 
 cudaError_t launch_ppm(const float* s0, const float* s1, const int* cur, const uint8_t* mask, long long vol, int nx,
                        int ny, int nz, int px, long long plane, const int layer[3], const float lo[3],
                        const float hi[3], uint8_t* out, int num_sms, cudaStream_t s) {
-    const long long n = (long long)((nx + 3) / 4) * ny * nz;
-    k_ppm<<<blocks_for(n, num_sms), 256, 0, s>>>(s0, s1, cur, mask, vol, nx, ny, nz, px, plane,
+    const long long rows = (long long)ny * nz;  // one warp per row, 8 rows per block
+    long long nb = (rows + 7) / 8;
+    if (nb > (long long)num_sms * 16) nb = (long long)num_sms * 16;
+    k_ppm<<<(int)(nb < 1 ? 1 : nb), 256, 0, s>>>(s0, s1, cur, mask, vol, nx, ny, nz, px, plane,
                                                  make_int3(layer[0], layer[1], layer[2]),
                                                  make_float3(lo[0], lo[1], lo[2]),
                                                  make_float3(hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]), out);
@@ -169,7 +187,9 @@ cudaError_t launch_singz(const float* s0, const float* s1, const int* cur, long 
     if (e != cudaSuccess) return e;
     const long long n = (long long)(nx - 1) * (ny - 1) * nz;
     if (n <= 0) return cudaSuccess;
-    k_singz<<<blocks_for(n, num_sms), 256, 0, s>>>(s0, s1, cur, off_a, off_b, iso_a, iso_b, mask, nx, ny, nz, px,
+    long long nb = ((long long)(ny - 1) * nz + 7) / 8;  // one warp per row of cells, 8 rows per block
+    if (nb > (long long)num_sms * 16) nb = (long long)num_sms * 16;
+    k_singz<<<(int)(nb < 1 ? 1 : nb), 256, 0, s>>>(s0, s1, cur, off_a, off_b, iso_a, iso_b, mask, nx, ny, nz, px,
                                                    plane, xyz, max_points, d_count);
     return cudaGetLastError();
 }
