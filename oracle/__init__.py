@@ -12,6 +12,9 @@ Parity status per function (see ``bbx_oracle.c`` for the passages):
   tests/test_oracle_output.py.
   Matrix Rush-Larsen (transition matrix of the Markov form of the BR sodium
   activation, the BR_MRL model): pinned by tests/test_oracle_markov.py.
+  Multivariate matrix Rush-Larsen (the two-gate calcium-dependent
+  inactivation channel of BR_FCA, split into its univariate subsystems):
+  pinned by tests/test_oracle_markov_ca.py.
   Beeler-Reuter rates and currents: the paper does not print them
   (transcribed from Beeler & Reuter 1977); pinned by physics and physiology
   in tests/test_oracle_br.py (directions, windows, hierarchy, reversal
@@ -32,8 +35,10 @@ _SRC = os.path.join(_HERE, "bbx_oracle.c")
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
 
-FHN, BARKLEY, BR, ZFK, DIFFUSION, BR_MRL = 1, 2, 3, 4, 5, 6
-NVARS = {FHN: 2, BARKLEY: 2, BR: 8, ZFK: 1, DIFFUSION: 1, BR_MRL: 11}
+FHN, BARKLEY, BR, ZFK, DIFFUSION, BR_MRL, BR_FCA = 1, 2, 3, 4, 5, 6, 7
+NVARS = {FHN: 2, BARKLEY: 2, BR: 8, ZFK: 1, DIFFUSION: 1, BR_MRL: 11, BR_FCA: 11}
+# default parameters of BR_FCA: gNa, gNaC, ENa, gs, Kc (mol/L), tau_c (ms), eps
+FCA_DEFAULTS = (4.0, 0.003, 50.0, 0.09, 5e-6, 2.0, 0.05)
 MAXS = 11
 INT32_MAX = np.iinfo(np.int32).max
 
@@ -88,6 +93,9 @@ def lib():
         L.orc_br_currents.argtypes = [P, P, P]
         L.orc_mrl_generator.argtypes = [D, P]
         L.orc_mrl_transition.argtypes = [D, D, P]
+        L.orc_fca_generator.argtypes = [P, I, D, D, P]
+        L.orc_fca_split_step.argtypes = [P, I, D, D, D, P, P]
+        L.orc_fca_exact_step.argtypes = [P, I, D, D, D, P, P]
         L.orc_run.argtypes = [P, P, P, D, I, P, P, P]
         L.orc_run.restype = I
         L.orc_set_threads.argtypes = [I]
@@ -218,6 +226,40 @@ def mrl_transition(V, dt):
     return T.reshape(4, 4)
 
 
+def _fca_par(par):
+    p = np.array(FCA_DEFAULTS if par is None else par, dtype=np.float64)
+    return p, len(p)
+
+
+def fca_generator(V, Ca, par=None):
+    """Generator A(V, Ca) of the two-gate slow-inward inactivation channel
+    of BR_FCA (4 x 4, state q = f + 2 c, A[i, j] = rate from j into i)."""
+    p, n = _fca_par(par)
+    A = np.zeros(16)
+    lib().orc_fca_generator(p.ctypes.data, n, float(V), float(Ca), A.ctypes.data)
+    return A.reshape(4, 4)
+
+
+def fca_split_step(V, Ca, dt, u, par=None):
+    """The multivariate matrix Rush-Larsen step of the channel: the exact
+    step of the voltage gate, then of the calcium gate, then Euler for the
+    remainder."""
+    p, n = _fca_par(par)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros(4)
+    lib().orc_fca_split_step(p.ctypes.data, n, float(V), float(Ca), float(dt), u.ctypes.data, out.ctypes.data)
+    return out
+
+
+def fca_exact_step(V, Ca, dt, u, par=None):
+    """exp(dt A(V, Ca)) u, the unsplit matrix Rush-Larsen step."""
+    p, n = _fca_par(par)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros(4)
+    lib().orc_fca_exact_step(p.ctypes.data, n, float(V), float(Ca), float(dt), u.ctypes.data, out.ctypes.data)
+    return out
+
+
 def br_currents(y, par=None):
     p = np.array([4.0, 0.003, 50.0, 0.09] if par is None else par, dtype=np.float64)
     y = np.ascontiguousarray(y, dtype=np.float64)
@@ -241,7 +283,8 @@ class Sim:
         self.S = NVARS[model]
         self.par = np.zeros(0) if par is None else np.ascontiguousarray(par, dtype=np.float64)
         if theta is None:
-            theta = {FHN: 0.0, BARKLEY: 0.5, BR: -40.0, ZFK: 0.5, DIFFUSION: 0.5, BR_MRL: -40.0}[model]
+            theta = {FHN: 0.0, BARKLEY: 0.5, BR: -40.0, ZFK: 0.5, DIFFUSION: 0.5, BR_MRL: -40.0,
+                     BR_FCA: -40.0}[model]
         self.theta = float(theta)
         if state is None:
             rs = rest_state(model, self.par if self.par.size else None)

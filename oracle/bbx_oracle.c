@@ -72,7 +72,7 @@
 #define ORC_ERR_FIBRE (-3)
 #define ORC_ERR_NOMEM (-8)
 
-enum { ORC_FHN = 1, ORC_BARKLEY = 2, ORC_BR = 3, ORC_ZFK = 4, ORC_DIFFUSION = 5, ORC_BR_MRL = 6 };
+enum { ORC_FHN = 1, ORC_BARKLEY = 2, ORC_BR = 3, ORC_ZFK = 4, ORC_DIFFUSION = 5, ORC_BR_MRL = 6, ORC_BR_FCA = 7 };
 #define ORC_MAXS 11
 
 typedef struct {
@@ -244,6 +244,7 @@ int orc_nvars(int model) {
         case ORC_BR: return 8;
         case ORC_DIFFUSION: return 1;
         case ORC_BR_MRL: return 11;
+        case ORC_BR_FCA: return 11;
     }
     return 0;
 }
@@ -259,6 +260,9 @@ static void model_params(int model, const double* par, int npar, double* p) {
         case ORC_BR:
         case ORC_BR_MRL: d[0] = 4.0; d[1] = 0.003; d[2] = 50.0; d[3] = 0.09; n = 4; break;
             /* gNa, gNaC, ENa, gs */
+        case ORC_BR_FCA:
+            d[0] = 4.0; d[1] = 0.003; d[2] = 50.0; d[3] = 0.09; d[4] = 5e-6; d[5] = 2.0; d[6] = 0.05; n = 7;
+            break; /* gNa, gNaC, ENa, gs, Kc (mol/L), tau_c (ms), eps */
     }
     for (int i = 0; i < 8; i++) p[i] = (i < npar && i < n && par) ? par[i] : d[i];
 }
@@ -363,12 +367,22 @@ static void mat4_mul(const double* X, const double* Y, double* Z) {
     memcpy(Z, t, sizeof(t));
 }
 
-/* T = exp(dt A(V)) of the scheme u_{n+1} = T(V_n) u_n: the power series
- * sum_k M^k / k! of M = dt A / 2^s (s chosen so that the largest absolute
- * row sum of M is at most 1/2; 30 terms), squared s times. */
+static void mat4_expm(const double* A16, double dt, double* T16);
+
+/* T = exp(dt A(V)) of the scheme u_{n+1} = T(V_n) u_n (mat4_expm below). */
+
 void orc_mrl_transition(double V, double dt, double* T16) {
     double M[16];
     orc_mrl_generator(V, M);
+    mat4_expm(M, dt, T16);
+}
+
+/* exp(dt A) for a 4 x 4 matrix A: the power series sum_k M^k / k! of M = dt A
+ * / 2^s (s chosen so that the largest absolute row sum of M is at most 1/2; 30
+ * terms), squared s times. */
+static void mat4_expm(const double* A16, double dt, double* T16) {
+    double M[16];
+    memcpy(M, A16, sizeof(M));
     double nrm = 0.0;
     for (int i = 0; i < 4; i++) {
         double r = 0.0;
@@ -388,6 +402,96 @@ void orc_mrl_transition(double V, double dt, double* T16) {
     }
     for (int q = 0; q < s; q++) mat4_mul(E, E, E);
     memcpy(T16, E, sizeof(E));
+}
+
+/* ---- a Markov chain with two control variables (multivariate matrix RL) --- */
+
+/* Beeler-Reuter with the inactivation of the slow inward current as a
+ * two-gate channel: the voltage-dependent gate f of the 1977 model (rates
+ * alpha_f, beta_f) and a calcium-dependent gate c, closed -> open at
+ * alpha_c = c_inf / tau_c, open -> closed at beta_c = (1 - c_inf) / tau_c,
+ * c_inf = 1 / (1 + Ca / Kc).  The channel's four states q = f + 2 c (f, c in
+ * {0, 1}: gate open) obey Eq. (markov-generic) with A(V, Ca) = A_f(V) (+)
+ * A_c(Ca) + R(V, Ca): the Kronecker sum of the two gates' univariate
+ * generators plus a small multivariate remainder, a direct transition from
+ * (f open, c closed) to (f closed, c open) at rate eps alpha_f(V) (1 -
+ * c_inf(Ca)).  I_s = g_s d Q3 (V - E_s), Q3 = P(f and c open).  The paper
+ * prints no such model; it exercises the scheme of section "Exponential
+ * solvers" for a matrix depending on V and Ca: Lie splitting into the
+ * univariate subsystems, each advanced by its exact (matrix Rush-Larsen)
+ * step, and forward Euler for the remainder.  State order: V, Ca, x1, m, h,
+ * j, d, Q0, Q1, Q2, Q3. */
+enum { FC_V = 0, FC_CA, FC_X1, FC_M, FC_H, FC_J, FC_D, FC_Q0 };
+
+static double fca_cinf(const double* p, double Ca) { return 1.0 / (1.0 + Ca / p[4]); }
+
+/* The generator A(V, Ca) of the channel (row-major, A[i][j] = rate from
+ * state j into state i; columns sum to zero). */
+void orc_fca_generator(const double* par, int npar, double V, double Ca, double* A16) {
+    double p[8], al[6], be[6];
+    model_params(ORC_BR_FCA, par, npar, p);
+    orc_br_rates(V, al, be);
+    const double af = al[5], bf = be[5], ci = fca_cinf(p, Ca);
+    const double ac = ci / p[5], bc = (1.0 - ci) / p[5], r = p[6] * af * (1.0 - ci);
+    for (int i = 0; i < 16; i++) A16[i] = 0.0;
+    for (int q = 0; q < 4; q++) {
+        const int f = q & 1, c = q >> 1;
+        const int qf = q ^ 1, qc = q ^ 2;  /* the states one gate away */
+        A16[qf * 4 + q] += f ? bf : af;
+        A16[qc * 4 + q] += c ? bc : ac;
+    }
+    A16[2 * 4 + 1] += r; /* (f open, c closed) -> (f closed, c open) */
+    for (int q = 0; q < 4; q++) {
+        double out = 0.0;
+        for (int i = 0; i < 4; i++)
+            if (i != q) out += A16[i * 4 + q];
+        A16[q * 4 + q] = -out;
+    }
+}
+
+/* The exact step of a two-state gate with rates a (closed -> open) and b
+ * (open -> closed) applied to one index of the channel's state: Eq. (RL)
+ * for the open probability, A = exp(-(a+b) dt), B = a/(a+b) (1 - A), as the
+ * 2 x 2 transition matrix [[1-B, 1-A-B], [B, A+B]] (columns: from closed,
+ * from open), on the pairs of states that differ in the gate `bit`. */
+static void gate2_step(double a, double b, double dt, int bit, double* u) {
+    const double A = exp(-(a + b) * dt), B = a / (a + b) * (1.0 - A);
+    for (int q = 0; q < 4; q++) {
+        if (q & bit) continue;
+        const double u0 = u[q], u1 = u[q | bit];
+        u[q] = (1.0 - B) * u0 + (1.0 - A - B) * u1;
+        u[q | bit] = B * u0 + (A + B) * u1;
+    }
+}
+
+/* The multivariate matrix Rush-Larsen step of the channel with V and Ca held
+ * at their values at the start of the step: the voltage gate's exact step,
+ * then the calcium gate's, then forward Euler for the remainder R. */
+void orc_fca_split_step(const double* par, int npar, double V, double Ca, double dt, const double* u, double* un) {
+    double p[8], al[6], be[6], w[4];
+    model_params(ORC_BR_FCA, par, npar, p);
+    orc_br_rates(V, al, be);
+    const double ci = fca_cinf(p, Ca);
+    for (int q = 0; q < 4; q++) w[q] = u[q];
+    gate2_step(al[5], be[5], dt, 1, w);
+    gate2_step(ci / p[5], (1.0 - ci) / p[5], dt, 2, w);
+    const double r = p[6] * al[5] * (1.0 - ci);
+    for (int q = 0; q < 4; q++) un[q] = w[q];
+    un[1] -= dt * r * w[1];
+    un[2] += dt * r * w[1];
+}
+
+/* The same step without splitting: u_{n+1} = exp(dt A(V, Ca)) u_n, the matrix
+ * exponential of the whole generator (the "on the fly" matrix Rush-Larsen). */
+void orc_fca_exact_step(const double* par, int npar, double V, double Ca, double dt, const double* u, double* un) {
+    double A[16], T[16];
+    orc_fca_generator(par, npar, V, Ca, A);
+    mat4_expm(A, dt, T);
+    for (int i = 0; i < 4; i++) {
+        double s = 0.0;
+        for (int j = 0; j < 4; j++) s += T[i * 4 + j] * u[j];
+        un[i] = s;
+    }
 }
 
 /* One unsplit step of one node: Eq. (Euler) for the non-gate variables with
@@ -452,6 +556,24 @@ void orc_cell_update(int model, const double* par, int npar, const double* y, do
                 for (int j = 0; j < 4; j++) s += T[i * 4 + j] * y[MR_P0 + j];
                 yn[MR_P0 + i] = s;
             }
+        } break;
+        case ORC_BR_FCA: {
+            /* Eq. (Euler) for V and Ca with I_s = g_s d Q3 (V - E_s), Eq.
+             * (RL) for x1, m, h, j, d, and the channel by the split matrix
+             * Rush-Larsen step at (V, Ca) of the start of the step */
+            const double Cm = 1.0;
+            double cur[3], al[6], be[6];
+            const double m = y[FC_M];
+            br_currents_m3(p, y[FC_V], y[FC_CA], y[FC_X1], m * m * m, y[FC_H], y[FC_J], y[FC_D], y[FC_Q0 + 3], cur);
+            orc_br_rates(y[FC_V], al, be);
+            yn[FC_V] = y[FC_V] + dt * (-(cur[0] - Istim) / Cm + L);
+            yn[FC_CA] = y[FC_CA] + dt * cur[2];
+            for (int g = 0; g < 5; g++) { /* x1, m, h, j, d: the first five rates */
+                double A = exp(-(al[g] + be[g]) * dt);
+                double B = al[g] / (al[g] + be[g]) * (1.0 - A);
+                yn[FC_X1 + g] = A * y[FC_X1 + g] + B;
+            }
+            orc_fca_split_step(par, npar, y[FC_V], y[FC_CA], dt, y + FC_Q0, yn + FC_Q0);
         } break;
     }
 }
@@ -545,6 +667,23 @@ int orc_rest_state(int model, const double* par, int npar, double* y) {
             y[MR_P0 + 2] = 3 * m * m * (1 - m);
             y[MR_P0 + 3] = m * m * m;
         } return ORC_OK;
+        case ORC_BR_FCA: {
+            /* from the BR rest state with the channel at the product of the
+             * two gates' steady states, the space-clamped cell integrated
+             * for 20 s at dt = 0.01 ms (the calcium gate moves the rest) */
+            double r[8], yn[ORC_MAXS];
+            orc_rest_state(ORC_BR, par, npar, r);
+            for (int v = 0; v < 7; v++) y[v] = r[v]; /* V, Ca, x1, m, h, j, d share the BR order */
+            const double f = r[BR_F], c = fca_cinf(p, r[BR_CA]);
+            y[FC_Q0 + 0] = (1 - f) * (1 - c);
+            y[FC_Q0 + 1] = f * (1 - c);
+            y[FC_Q0 + 2] = (1 - f) * c;
+            y[FC_Q0 + 3] = f * c;
+            for (int n = 0; n < 2000000; n++) {
+                orc_cell_update(model, par, npar, y, 0.0, 0.0, 0.01, yn);
+                memcpy(y, yn, sizeof(double) * 11);
+            }
+        } return ORC_OK;
     }
     return ORC_ERR_ARG;
 }
@@ -614,7 +753,7 @@ int orc_run(const orc_geom* g, const orc_run_cfg* c, double* state, double dt, i
             double* t, long long* n, int32_t* act) {
     const size_t N = (size_t)g->nx * g->ny * g->nz;
     const int S = orc_nvars(c->model);
-    if (S == 0 || (c->rk4 && (c->model == ORC_BR || c->model == ORC_BR_MRL))) return ORC_ERR_ARG;
+    if (S == 0 || (c->rk4 && (c->model == ORC_BR || c->model == ORC_BR_MRL || c->model == ORC_BR_FCA))) return ORC_ERR_ARG;
     int rc = orc_check_fibres(g);
     if (rc) return rc;
     size_t nt = 0;
@@ -670,7 +809,7 @@ int orc_step_cells(const orc_geom* g, const orc_run_cfg* c, const double* state,
                    double t, const long long* cells, int ncells, double* out) {
     const size_t N = (size_t)g->nx * g->ny * g->nz;
     const int S = orc_nvars(c->model);
-    if (S == 0 || (c->rk4 && (c->model == ORC_BR || c->model == ORC_BR_MRL))) return ORC_ERR_ARG;
+    if (S == 0 || (c->rk4 && (c->model == ORC_BR || c->model == ORC_BR_MRL || c->model == ORC_BR_FCA))) return ORC_ERR_ARG;
     int on = c->amp != 0.0 && t >= c->t_on && t < c->t_off;
     double W[27], y[ORC_MAXS], yn[ORC_MAXS];
     for (int i = 0; i < ncells; i++) {
