@@ -442,6 +442,12 @@ def run_configs(args, dev, stream, dist=None, n_ranks=1):
         "br_mrl_256x256x64": (lambda: wl.br_mrl_slab(256, 256, 64), (2, 22),
                               "the same slab with the sodium activation as a 4-state Markov chain, "
                               "matrix Rush-Larsen with T(V) tabulated"),
+        "br_fca_256x256x64": (lambda: wl.br_fca_slab(256, 256, 64), (2, 22),
+                              "the same slab with the slow inward current's inactivation as a voltage gate and "
+                              "a calcium gate (4-state chain, A(V, Ca) split into univariate parts)"),
+        "br_fca_256x256x64_onfly": (lambda: wl.br_fca_slab(256, 256, 64, onfly=True), (2, 22),
+                                    "the calcium-gated slab with the channel by exp(dt A(V, Ca)) of the whole "
+                                    "generator at run time (no table, no splitting)"),
         "br_shell_256": (lambda: wl.br_shell(256), (2, 22),
                          "Beeler-Reuter shell in 256^3 (profiling size, not in the default list)"),
         "br_256x256x64_tab": (lambda: wl.br_slab(256, 256, 64), (2, 22),
@@ -741,7 +747,8 @@ def main():
     ap.add_argument("--tile", default=None, help="TY,TZ brick shape instead of autotuning")
     ap.add_argument("--config-tile", default=None, help="TY,TZ brick shape of the --configs workloads instead of autotuning")
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--configs", default="fhn_200,fhn_16384,barkley_512x512x256,br_shell_512,br_256x256x64,br_mrl_256x256x64,"
+    ap.add_argument("--configs", default="fhn_200,fhn_16384,barkley_512x512x256,br_shell_512,br_256x256x64,"
+                            "br_mrl_256x256x64,br_fca_256x256x64,br_fca_256x256x64_onfly,"
                             "br_256x256x64_tab,br_shell_512_tab,br_shell_512_u16,br_shell_512_f16,br_256x256x64_u16",
                     help="comma-separated other workloads to time by differencing ('' for none)")
     ap.add_argument("--scroll-steps", type=int, default=2000)

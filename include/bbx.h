@@ -80,13 +80,37 @@ extern "C" {
  *                with coefficients from the same V grid (as
  *                bbx_set_tabulation does for BBX_BR).  Unsplit Euler / Rush-Larsen
  *                only: bbx_set_scheme(BBX_SCHEME_LIE), bbx_set_solver(
- *                BBX_SOLVER_RK4) and the surrogate are refused. */
+ *                BBX_SOLVER_RK4) and the surrogate are refused.
+ *  BBX_BR_FCA    11 vars (V, Ca, x1, m, h, j, d, Q0, Q1, Q2, Q3).  gNa=4
+ *                gNaC=0.003 ENa=50 gs=0.09 Kc=5e-6 (mol/L) tau_c=2 (ms)
+ *                eps=0.05 onfly=0.  threshold -40 mV.  Beeler-Reuter with the slow
+ *                inward current's inactivation as a channel of two gates, the
+ *                voltage gate f of the 1977 model and a calcium gate c
+ *                (closed -> open at c_inf/tau_c, open -> closed at
+ *                (1-c_inf)/tau_c, c_inf = 1/(1 + Ca/Kc)); Qq = probability of
+ *                state q = f + 2c (gate open = 1); a direct transition
+ *                (f open, c closed) -> (f closed, c open) at
+ *                eps alpha_f (1 - c_inf); I_s = gs d Q3 (V - E_s).  The
+ *                generator A(V, Ca) of Eq. (markov-generic) is multivariate;
+ *                it is advanced as section "Exponential solvers" describes:
+ *                Lie splitting into the V-univariate f gate (Rush-Larsen
+ *                coefficients tabulated in V as for BBX_BR_MRL), the
+ *                Ca-univariate c gate (closed form: its rates sum to 1/tau_c)
+ *                and the small remainder by forward Euler, V and Ca held at
+ *                their values at the start of the step.  onfly=1 instead
+ *                applies exp(dt A(V_n, Ca_n)) of the whole generator at run
+ *                time (the same section's step for a chain with no such
+ *                decomposition: rates at the node, no table, the
+ *                exponential's action by its Taylor series to nine terms on
+ *                2^s substeps that bring dt/2^s |A| to 1/2, s <= 6).
+ *                Unsplit Euler / Rush-Larsen only, as BBX_BR_MRL. */
 #define BBX_FHN 1
 #define BBX_BARKLEY 2
 #define BBX_BR 3
 #define BBX_ZFK 4
 #define BBX_DIFFUSION 5
 #define BBX_BR_MRL 6
+#define BBX_BR_FCA 7
 
 #define BBX_ACT_NONE 2147483647 /* activation map value of a node never activated */
 

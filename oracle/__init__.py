@@ -37,8 +37,9 @@ _LIB = os.path.join(_LIBDIR, "liboracle.so")
 
 FHN, BARKLEY, BR, ZFK, DIFFUSION, BR_MRL, BR_FCA = 1, 2, 3, 4, 5, 6, 7
 NVARS = {FHN: 2, BARKLEY: 2, BR: 8, ZFK: 1, DIFFUSION: 1, BR_MRL: 11, BR_FCA: 11}
-# default parameters of BR_FCA: gNa, gNaC, ENa, gs, Kc (mol/L), tau_c (ms), eps
-FCA_DEFAULTS = (4.0, 0.003, 50.0, 0.09, 5e-6, 2.0, 0.05)
+# default parameters of BR_FCA: gNa, gNaC, ENa, gs, Kc (mol/L), tau_c (ms), eps,
+# onfly (1: the channel by the unsplit exponential instead of the split step)
+FCA_DEFAULTS = (4.0, 0.003, 50.0, 0.09, 5e-6, 2.0, 0.05, 0.0)
 MAXS = 11
 INT32_MAX = np.iinfo(np.int32).max
 

@@ -261,8 +261,9 @@ static void model_params(int model, const double* par, int npar, double* p) {
         case ORC_BR_MRL: d[0] = 4.0; d[1] = 0.003; d[2] = 50.0; d[3] = 0.09; n = 4; break;
             /* gNa, gNaC, ENa, gs */
         case ORC_BR_FCA:
-            d[0] = 4.0; d[1] = 0.003; d[2] = 50.0; d[3] = 0.09; d[4] = 5e-6; d[5] = 2.0; d[6] = 0.05; n = 7;
-            break; /* gNa, gNaC, ENa, gs, Kc (mol/L), tau_c (ms), eps */
+            d[0] = 4.0; d[1] = 0.003; d[2] = 50.0; d[3] = 0.09; d[4] = 5e-6; d[5] = 2.0; d[6] = 0.05; d[7] = 0.0;
+            n = 8;
+            break; /* gNa, gNaC, ENa, gs, Kc (mol/L), tau_c (ms), eps, onfly */
     }
     for (int i = 0; i < 8; i++) p[i] = (i < npar && i < n && par) ? par[i] : d[i];
 }
@@ -560,7 +561,8 @@ void orc_cell_update(int model, const double* par, int npar, const double* y, do
         case ORC_BR_FCA: {
             /* Eq. (Euler) for V and Ca with I_s = g_s d Q3 (V - E_s), Eq.
              * (RL) for x1, m, h, j, d, and the channel by the split matrix
-             * Rush-Larsen step at (V, Ca) of the start of the step */
+             * Rush-Larsen step at (V, Ca) of the start of the step, or with
+             * the parameter onfly set by the unsplit exponential */
             const double Cm = 1.0;
             double cur[3], al[6], be[6];
             const double m = y[FC_M];
@@ -573,7 +575,10 @@ void orc_cell_update(int model, const double* par, int npar, const double* y, do
                 double B = al[g] / (al[g] + be[g]) * (1.0 - A);
                 yn[FC_X1 + g] = A * y[FC_X1 + g] + B;
             }
-            orc_fca_split_step(par, npar, y[FC_V], y[FC_CA], dt, y + FC_Q0, yn + FC_Q0);
+            if (p[7] != 0.0) /* onfly: the unsplit exponential of the whole generator */
+                orc_fca_exact_step(par, npar, y[FC_V], y[FC_CA], dt, y + FC_Q0, yn + FC_Q0);
+            else
+                orc_fca_split_step(par, npar, y[FC_V], y[FC_CA], dt, y + FC_Q0, yn + FC_Q0);
         } break;
     }
 }

@@ -27,8 +27,8 @@ BBX_ERR_STATE = -7
 BBX_ERR_NOMEM = -8
 BBX_ERR_UNSUPPORTED = -9
 
-BBX_FHN, BBX_BARKLEY, BBX_BR, BBX_ZFK, BBX_DIFFUSION, BBX_BR_MRL = 1, 2, 3, 4, 5, 6
-NVARS = {BBX_FHN: 2, BBX_BARKLEY: 2, BBX_BR: 8, BBX_ZFK: 1, BBX_DIFFUSION: 1, BBX_BR_MRL: 11}
+BBX_FHN, BBX_BARKLEY, BBX_BR, BBX_ZFK, BBX_DIFFUSION, BBX_BR_MRL, BBX_BR_FCA = 1, 2, 3, 4, 5, 6, 7
+NVARS = {BBX_FHN: 2, BBX_BARKLEY: 2, BBX_BR: 8, BBX_ZFK: 1, BBX_DIFFUSION: 1, BBX_BR_MRL: 11, BBX_BR_FCA: 11}
 BBX_ACT_NONE = 2147483647
 BBX_SCHEME_UNSPLIT, BBX_SCHEME_LIE = 0, 1
 BBX_SOLVER_EULER, BBX_SOLVER_RK4 = 0, 1

@@ -522,8 +522,8 @@ struct Model<BBX_BR> {
         const float b_j = br_ratio(0.3f, __expf(-0.1f * (V + 32.0f)) + 1.0f);
         const float a_d = br_ratio(0.095f * __expf(-0.01f * (V - 5.0f)), __expf(-0.072f * (V - 5.0f)) + 1.0f);
         const float b_d = br_ratio(0.07f * __expf(-0.017f * (V + 44.0f)), __expf(0.05f * (V + 44.0f)) + 1.0f);
-        const float a_f = br_ratio(0.012f * __expf(-0.008f * (V + 28.0f)), __expf(0.15f * (V + 28.0f)) + 1.0f);
-        const float b_f = br_ratio(0.0065f * __expf(-0.02f * (V + 30.0f)), __expf(-0.2f * (V + 30.0f)) + 1.0f);
+        float a_f, b_f;
+        f_rates(V, &a_f, &b_f);
 
         d[0] = dt * (-(Iion - Is) + L);  // Cm = 1
         d[1] = dt * dCa;
@@ -533,6 +533,12 @@ struct Model<BBX_BR> {
         d[5] = rl_inc(j, a_j, b_j, dt);
         d[6] = rl_inc(dd, a_d, b_d, dt);
         d[7] = rl_inc(f, a_f, b_f, dt);
+    }
+
+    // alpha_f and beta_f, the rates of the slow inward current's inactivation
+    __device__ static __forceinline__ void f_rates(float V, float* a_f, float* b_f) {
+        *a_f = br_ratio(0.012f * __expf(-0.008f * (V + 28.0f)), __expf(0.15f * (V + 28.0f)) + 1.0f);
+        *b_f = br_ratio(0.0065f * __expf(-0.02f * (V + 30.0f)), __expf(-0.2f * (V + 30.0f)) + 1.0f);
     }
 
     __device__ static __forceinline__ float rl_inc(float y, float al, float be, float dt) {
@@ -635,6 +641,152 @@ struct Model<BBX_BR_MRL> {
         for (int g = 0; g < 4; ++g) y[3 + g] = fmaf(c[4 + 2 * g], y[3 + g], c[5 + 2 * g]);  // h, j, d, f
 #pragma unroll
         for (int r = 0; r < 4; ++r) y[7 + r] = pn[r];
+    }
+};
+
+// Beeler-Reuter with the slow inward current's inactivation as a two-gate
+// channel: the voltage gate f (alpha_f, beta_f of the 1977 model) and a
+// calcium gate c (closed -> open at c_inf / tau_c, open -> closed at
+// (1 - c_inf) / tau_c, c_inf = Kc / (Kc + Ca)), the four states q = f + 2 c
+// with probabilities Q0..Q3, and a small direct transition (f open, c
+// closed) -> (f closed, c open) at eps alpha_f (1 - c_inf).  The generator
+// A(V, Ca) of Eq. (markov-generic) is the sum of a V-univariate matrix (the
+// f gate), a Ca-univariate matrix (the c gate) and that multivariate
+// remainder; section "Exponential solvers" advances such a chain by Lie
+// splitting: each univariate part by its exact step from the values of V
+// and Ca at the start of the step, the remainder by forward Euler.  The f
+// gate's step comes from the Rush-Larsen V-table; the c gate's rates sum to
+// 1/tau_c at every Ca, so its step has the closed form open' = open +
+// (1 - e^{-dt/tau_c}) (c_inf total - open) with one constant.  Both gate steps
+// move probability within pairs of states (total of the pair kept exactly).
+// With the parameter onfly set, the channel takes the step the same section
+// gives for a generator with no such decomposition instead: the exponential
+// of the whole A(V, Ca) applied at run time, with no table and no splitting.
+// I_s = g_s d Q3 (V - E_s); x1, m, h, j, d by Rush-Larsen; V, Ca by Euler.
+// State: V, Ca, x1, m, h, j, d, Q0, Q1, Q2, Q3.
+// Kernel parameters mp: gNa, gNaC, ENa, gs, Kc, eps, 1/tau_c, onfly (0 or 1).
+
+template <>
+struct Model<BBX_BR_FCA> {
+    static constexpr int S = 11;
+
+    // the channel step (u = Q0..Q3): f gate by open' = A_f open + B_f total,
+    // c gate as above with omc = 1 - e^{-dt/tau_c}, then the remainder
+    __device__ static __forceinline__ void channel(const float* mp, float A_f, float B_f, float a_f, float omc,
+                                                   float Ca, float dt, float* u) {
+        const float pc0 = u[0] + u[1], pc1 = u[2] + u[3];  // c closed, c open
+        const float fo0 = fmaf(A_f, u[1], B_f * pc0), fo1 = fmaf(A_f, u[3], B_f * pc1);
+        u[0] = pc0 - fo0;
+        u[1] = fo0;
+        u[2] = pc1 - fo1;
+        u[3] = fo1;
+        const float inv = __fdividef(1.0f, mp[4] + Ca);
+        const float ci = mp[4] * inv, one_minus_ci = Ca * inv;
+        const float pf0 = u[0] + u[2], pf1 = u[1] + u[3];  // f closed, f open
+        const float co0 = fmaf(omc, fmaf(ci, pf0, -u[2]), u[2]), co1 = fmaf(omc, fmaf(ci, pf1, -u[3]), u[3]);
+        u[0] = pf0 - co0;
+        u[2] = co0;
+        u[1] = pf1 - co1;
+        u[3] = co1;
+        const float flow = dt * mp[5] * a_f * one_minus_ci * u[1];
+        u[1] -= flow;
+        u[2] += flow;
+    }
+
+    // u <- exp(dt A(V, Ca)) u with every rate evaluated at the node: the
+    // Taylor series of the exponential's action on u to nine terms, on 2^s
+    // substeps, s the smallest (at most 6) that brings dt / 2^s times the
+    // largest absolute column sum of A (twice the largest outflow) to 1/2.
+    __device__ static __forceinline__ void channel_onfly(const float* mp, float V, float Ca, float dt, float* u) {
+        float a_f, b_f;
+        Model<BBX_BR>::f_rates(V, &a_f, &b_f);
+        const float inv = __fdividef(1.0f, mp[4] + Ca);
+        const float a_c = mp[4] * inv * mp[6], b_c = Ca * inv * mp[6];
+        const float r = mp[5] * a_f * (Ca * inv);
+        // outflow of each state q = f + 2 c
+        const float o0 = a_f + a_c, o1 = b_f + a_c + r, o2 = a_f + b_c, o3 = b_f + b_c;
+        float nrm = 2.0f * dt * fmaxf(fmaxf(o0, o1), fmaxf(o2, o3)), h = dt;
+        int s = 0;
+        while (nrm > 0.5f && s < 6) {
+            nrm *= 0.5f;
+            h *= 0.5f;
+            ++s;
+        }
+        for (int k = 0; k < (1 << s); ++k) {
+            float t0 = u[0], t1 = u[1], t2 = u[2], t3 = u[3];
+            float s0 = t0, s1 = t1, s2 = t2, s3 = t3;
+#pragma unroll
+            for (int n = 1; n <= 9; ++n) {
+                const float c = h * (1.0f / (float)n);
+                const float n0 = fmaf(-o0, t0, fmaf(b_f, t1, b_c * t2));
+                const float n1 = fmaf(a_f, t0, fmaf(-o1, t1, b_c * t3));
+                const float n2 = fmaf(a_c, t0, fmaf(r, t1, fmaf(-o2, t2, b_f * t3)));
+                const float n3 = fmaf(a_c, t1, fmaf(a_f, t2, -o3 * t3));
+                t0 = c * n0;
+                t1 = c * n1;
+                t2 = c * n2;
+                t3 = c * n3;
+                s0 += t0;
+                s1 += t1;
+                s2 += t2;
+                s3 += t3;
+            }
+            u[0] = s0;
+            u[1] = s1;
+            u[2] = s2;
+            u[3] = s3;
+        }
+    }
+
+    // tab: the Rush-Larsen table of Model<BBX_BR>::update_tab (kTabN x 4
+    // float4) with entry 14 = alpha_f(V) and entry 15 = 1 - e^{-dt/tau_c}.
+    __device__ static __forceinline__ void update_tab(const float* mp, const float4* __restrict__ tab, float* y,
+                                                      float L, float Is, float dt) {
+        const float V = y[0], Ca = y[1];
+        float w;
+        const int i = tab_index(V, &w);
+        float c[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 a = __ldg(tab + 4 * i + q), b = __ldg(tab + 4 * i + 4 + q);
+            c[4 * q + 0] = fmaf(w, b.x - a.x, a.x);
+            c[4 * q + 1] = fmaf(w, b.y - a.y, a.y);
+            c[4 * q + 2] = fmaf(w, b.z - a.z, a.z);
+            c[4 * q + 3] = fmaf(w, b.w - a.w, a.w);
+        }
+        const float m = y[3];
+        const float INa = (mp[0] * m * m * m * y[4] * y[5] + mp[1]) * (V - mp[2]);
+        const float Es = -82.3f - 13.0287f * __logf(Ca);
+        const float Is_ = mp[3] * y[6] * y[10] * (V - Es);
+        const float Iion = INa + Is_ + y[2] * c[12] + c[13];
+        const float dCa = -1e-7f * Is_ + 0.07f * (1e-7f - Ca);
+        y[0] = V + dt * (-(Iion - Is) + L);  // Cm = 1
+        y[1] = Ca + dt * dCa;
+#pragma unroll
+        for (int g = 0; g < 5; ++g) y[2 + g] = fmaf(c[2 * g], y[2 + g], c[2 * g + 1]);  // x1, m, h, j, d
+        if (mp[7] != 0.0f)
+            channel_onfly(mp, V, Ca, dt, y + 7);
+        else
+            channel(mp, c[10], c[11], c[14], c[15], Ca, dt, y + 7);
+    }
+
+    // The same step with every rate evaluated at V (no table): the rest-state
+    // integration uses it.
+    __device__ static __forceinline__ void update(const float* mp, float* y, float L, float Is, float dt) {
+        const float V = y[0], Ca = y[1];
+        float y8[8] = {y[0], y[1], y[2], y[3], y[4], y[5], y[6], y[10]};  // Q3 in the place of f
+        float d[8];
+        Model<BBX_BR>::increment_m3(mp, y8, y[3] * y[3] * y[3], L, Is, dt, d);
+        float a_f, b_f;
+        Model<BBX_BR>::f_rates(V, &a_f, &b_f);
+        const float omA = -expm1_br(-(a_f + b_f) * dt);
+        const float omc = -expm1_br(-dt * mp[6]);
+#pragma unroll
+        for (int v = 0; v < 7; ++v) y[v] += d[v];
+        if (mp[7] != 0.0f)
+            channel_onfly(mp, V, Ca, dt, y + 7);
+        else
+            channel(mp, 1.0f - omA, __fdividef(a_f, a_f + b_f) * omA, a_f, omc, Ca, dt, y + 7);
     }
 };
 
@@ -1498,7 +1650,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
 #pragma unroll
                                 for (int e = 0; e < 2; ++e) Model<MODEL>::update(mp, yv[e], Lr[r][e], Isr[e], a.dt);
                             }
-                        } else if constexpr (MODEL == BBX_BR_MRL) {
+                        } else if constexpr (MODEL == BBX_BR_MRL || MODEL == BBX_BR_FCA) {
 #pragma unroll
                             for (int e = 0; e < 2; ++e)
                                 Model<MODEL>::update_tab(mp, a.tab, yv[e], Lr[r][e], Isr[e], a.dt);

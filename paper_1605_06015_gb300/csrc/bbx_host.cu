@@ -21,8 +21,9 @@ StepKernel step_kernel_br(bool masked, bool aniso, int ty, bool planar, bool gen
 StepKernel step_kernel_zfk(bool masked, bool aniso, int ty, bool planar, bool general);
 StepKernel step_kernel_diffusion(bool masked, bool aniso, int ty, bool planar, bool general);
 StepKernel step_kernel_br_mrl(bool masked, bool aniso, int ty, bool planar, bool general);
+StepKernel step_kernel_br_fca(bool masked, bool aniso, int ty, bool planar, bool general);
 cudaError_t mrl_build_table(float4* tab, double dt, cudaStream_t s);
-cudaError_t br_build_rl_table(float4* tab, double dt, cudaStream_t s);
+cudaError_t br_build_rl_table(float4* tab, double dt, double tau_c, cudaStream_t s);
 StepKernel step_kernel_br_surrogate(bool masked, bool aniso, int ty);
 StepKernel step_kernel_br16(bool masked, bool aniso, int ty, bool planar, bool general, int gates);
 cudaError_t launch_ppm(const float* s0, const float* s1, const int* cur, const uint8_t* mask, long long vol, int nx,
@@ -53,6 +54,7 @@ int model_nvars(int model) {
         case BBX_ZFK: return 1;
         case BBX_DIFFUSION: return 1;
         case BBX_BR_MRL: return 11;
+        case BBX_BR_FCA: return 11;
     }
     return 0;
 }
@@ -61,7 +63,8 @@ double model_threshold(int model) {
     switch (model) {
         case BBX_FHN: return 0.0;
         case BBX_BR:
-        case BBX_BR_MRL: return -40.0;
+        case BBX_BR_MRL:
+        case BBX_BR_FCA: return -40.0;
         default: return 0.5;
     }
 }
@@ -73,6 +76,9 @@ int model_defaults(int model, double* p) {
         case BBX_BARKLEY: p[0] = 0.75; p[1] = 0.02; p[2] = 0.02; return 3;
         case BBX_BR:
         case BBX_BR_MRL: p[0] = 4.0; p[1] = 0.003; p[2] = 50.0; p[3] = 0.09; return 4;
+        case BBX_BR_FCA:
+            p[0] = 4.0; p[1] = 0.003; p[2] = 50.0; p[3] = 0.09; p[4] = 5e-6; p[5] = 2.0; p[6] = 0.05; p[7] = 0.0;
+            return 8;  // ..., Kc (mol/L), tau_c (ms), eps, onfly
         case BBX_ZFK: p[0] = 0.13; return 1;
         case BBX_DIFFUSION: return 0;
     }
@@ -87,6 +93,12 @@ void model_kernel_params(int model, const double* p, float* mp) {
         case BBX_BARKLEY: mp[0] = float(1.0 / p[0]); mp[1] = float(p[1]); mp[2] = float(1.0 / p[2]); break;
         case BBX_BR:
         case BBX_BR_MRL: for (int i = 0; i < 4; ++i) mp[i] = float(p[i]); break;
+        case BBX_BR_FCA:
+            for (int i = 0; i < 5; ++i) mp[i] = float(p[i]);
+            mp[5] = float(p[6]);
+            mp[6] = float(1.0 / p[5]);
+            mp[7] = p[7] != 0.0 ? 1.0f : 0.0f;
+            break;
         case BBX_ZFK: mp[0] = float(p[0]); break;
         default: break;
     }
@@ -109,6 +121,7 @@ StepKernel lookup_kernel(int model, bool masked, bool aniso, int ty, bool surrog
         case BBX_ZFK: return step_kernel_zfk(masked, aniso, ty, planar, general);
         case BBX_DIFFUSION: return step_kernel_diffusion(masked, aniso, ty, planar, general);
         case BBX_BR_MRL: return step_kernel_br_mrl(masked, aniso, ty, planar, general);
+        case BBX_BR_FCA: return step_kernel_br_fca(masked, aniso, ty, planar, general);
     }
     return StepKernel{nullptr, 0, 0, 0};
 }
@@ -366,6 +379,21 @@ __global__ void k_rest(int model, const float* mp, double beta_d, double gamma_d
         out[8] = float(3 * m * (1 - m) * (1 - m));
         out[9] = float(3 * m * m * (1 - m));
         out[10] = float(m * m * m);
+    } else if (model == BBX_BR_FCA) {
+        // from the Beeler-Reuter rest state with the channel at the product
+        // of the gates' steady states, the cell integrated for another 10 s
+        // (the calcium gate moves the rest state)
+        float y[11] = {-84.0f, 1e-7f, 0.0f, 0.0f, 1.0f, 1.0f, 0.0f, 1.0f, 0.0f, 0.0f, 0.0f};
+        float p[8];
+        for (int i = 0; i < 8; ++i) p[i] = mp[i];
+        for (int n = 0; n < 200000; ++n) Model<BBX_BR>::update(p, y, 0.0f, 0.0f, 0.05f);
+        const float f = y[7], c = p[4] / (p[4] + y[1]);
+        y[7] = (1.0f - f) * (1.0f - c);
+        y[8] = f * (1.0f - c);
+        y[9] = (1.0f - f) * c;
+        y[10] = f * c;
+        for (int n = 0; n < 200000; ++n) Model<BBX_BR_FCA>::update(p, y, 0.0f, 0.0f, 0.05f);
+        for (int i = 0; i < 11; ++i) out[i] = y[i];
     }
 }
 
@@ -790,6 +818,7 @@ struct bbx_grid {
     cudaStream_t copy_stream = nullptr;          // bbx_exchange_state: device-to-host copies
     cudaEvent_t ev_enter = nullptr, ev_out = nullptr;
     int tab_model = 0;        // the model d_tab was built for
+    double tab_tau_c = 0.0;   // and its tau_c (BBX_BR_FCA; 0 otherwise)
     bool tab_on = false;      // Beeler-Reuter with tabulated Rush-Larsen coefficients (bbx_set_tabulation)
     float* d_mp = nullptr;    // 8 floats
 
@@ -1092,7 +1121,8 @@ int encode_targs(const bbx_grid* g, int ty, TissueArgs* t) {
     t->c_iso = (float)(g->Dpar * ih2);
     model_kernel_params(g->model, g->par, t->mp);
     t->surr = (g->surr_on && g->model == BBX_BR) ? g->d_surr : nullptr;
-    t->tab = (g->model == BBX_BR_MRL || (g->model == BBX_BR && g->tab_on)) ? g->d_tab : nullptr;
+    t->tab = (g->model == BBX_BR_MRL || g->model == BBX_BR_FCA || (g->model == BBX_BR && g->tab_on)) ? g->d_tab
+                                                                                                    : nullptr;
     return BBX_OK;
 }
 
@@ -1103,11 +1133,12 @@ int finish_total(bbx_grid* g);
 bool wants_general(const bbx_grid* g) { return g->split || g->rk4 || (g->tab_on && g->model == BBX_BR); }
 
 // The V-table of a grid that uses one (the Rush-Larsen coefficients of BBX_BR
-// with tabulation on; those and the chain matrices of BBX_BR_MRL), allocated on first
-// use and rebuilt on the grid's stream whenever the model or the time step
-// differs from the ones it was built for.
+// with tabulation on and of BBX_BR_FCA; those and the chain matrices of
+// BBX_BR_MRL), allocated on first use and rebuilt on the grid's stream
+// whenever the model, the time step or tau_c differs from the ones it was
+// built for.
 int tab_refresh(bbx_grid* g) {
-    const bool want = g->model == BBX_BR_MRL || (g->model == BBX_BR && g->tab_on);
+    const bool want = g->model == BBX_BR_MRL || g->model == BBX_BR_FCA || (g->model == BBX_BR && g->tab_on);
     if (!want) return BBX_OK;
     if (!g->d_tab) {  // room for both tables of BBX_BR_MRL
         if (dmalloc(&g->d_tab, sizeof(float4) * 8 * (size_t)kTabN) != cudaSuccess) {
@@ -1116,11 +1147,13 @@ int tab_refresh(bbx_grid* g) {
         }
         g->tab_model = 0;
     }
-    if (!(g->dt > 0.0) || (g->tab_dt == g->dt && g->tab_model == g->model)) return BBX_OK;
-    BBX_CUDA(br_build_rl_table(g->d_tab, g->dt, g->stream));
+    const double tau_c = g->model == BBX_BR_FCA ? g->par[5] : 0.0;
+    if (!(g->dt > 0.0) || (g->tab_dt == g->dt && g->tab_model == g->model && g->tab_tau_c == tau_c)) return BBX_OK;
+    BBX_CUDA(br_build_rl_table(g->d_tab, g->dt, tau_c, g->stream));
     if (g->model == BBX_BR_MRL) BBX_CUDA(mrl_build_table(g->d_tab + 4 * (size_t)kTabN, g->dt, g->stream));
     g->tab_dt = g->dt;
     g->tab_model = g->model;
+    g->tab_tau_c = tau_c;
     return BBX_OK;
 }
 
@@ -1519,8 +1552,8 @@ int bbx_set_ionic_model(bbx_grid* g, int model, const double* params, int n_para
         return BBX_ERR_NOMEM;
     }
     if (model != BBX_BR) g->surr_on = false;
-    if (model == BBX_BR || model == BBX_BR_MRL) g->rk4 = 0;  // Beeler-Reuter keeps Euler / Rush-Larsen
-    if (model == BBX_BR_MRL) g->split = 0;  // unsplit only (no Lie-scheme kernels for this model)
+    if (model == BBX_BR || model == BBX_BR_MRL || model == BBX_BR_FCA) g->rk4 = 0;  // Euler / Rush-Larsen
+    if (model == BBX_BR_MRL || model == BBX_BR_FCA) g->split = 0;  // unsplit only (no Lie-scheme kernels)
     if (model != BBX_BR) g->tab_on = false;
     g->model = model;
     g->S = S;
@@ -1708,14 +1741,15 @@ static int apply_kinetics_setting(bbx_grid* g) {
 
 int bbx_set_scheme(bbx_grid* g, int scheme) {
     if (!g || (scheme != BBX_SCHEME_UNSPLIT && scheme != BBX_SCHEME_LIE)) return BBX_ERR_ARG;
-    if (scheme == BBX_SCHEME_LIE && g->model == BBX_BR_MRL) return BBX_ERR_UNSUPPORTED;
+    if (scheme == BBX_SCHEME_LIE && (g->model == BBX_BR_MRL || g->model == BBX_BR_FCA)) return BBX_ERR_UNSUPPORTED;
     g->split = scheme == BBX_SCHEME_LIE ? 1 : 0;
     return apply_kinetics_setting(g);
 }
 
 int bbx_set_solver(bbx_grid* g, int solver) {
     if (!g || (solver != BBX_SOLVER_EULER && solver != BBX_SOLVER_RK4)) return BBX_ERR_ARG;
-    if (solver == BBX_SOLVER_RK4 && (g->model == BBX_BR || g->model == BBX_BR_MRL)) return BBX_ERR_UNSUPPORTED;
+    if (solver == BBX_SOLVER_RK4 && (g->model == BBX_BR || g->model == BBX_BR_MRL || g->model == BBX_BR_FCA))
+        return BBX_ERR_UNSUPPORTED;
     g->rk4 = solver == BBX_SOLVER_RK4 ? 1 : 0;
     return apply_kinetics_setting(g);
 }

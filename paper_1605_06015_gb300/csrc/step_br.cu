@@ -62,9 +62,10 @@ __device__ void br_rates_d(double V, double* al, double* be) {
 }
 
 // One entry per thread: A = exp(-(alpha+beta) dt) and B = alpha/(alpha+beta)
-// (1 - A) of Eq. (RLcoeff) for the six gates, then K(V) with I_x1 = x1 K(V)
-// and I_K1(V); FP64, stored as float.
-__global__ void k_rl_table(float4* __restrict__ tab, int n, double vmin, double dv, double dt) {
+// (1 - A) of Eq. (RLcoeff) for the six gates, then K(V) with I_x1 = x1 K(V),
+// I_K1(V), alpha_f(V) and 1 - exp(-dt/tau_c) (the calcium gate of BBX_BR_FCA;
+// 0 when tau_c = 0); FP64, stored as float.
+__global__ void k_rl_table(float4* __restrict__ tab, int n, double vmin, double dv, double dt, double tau_c) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     const double V = vmin + dv * e;
@@ -79,7 +80,8 @@ __global__ void k_rl_table(float4* __restrict__ tab, int n, double vmin, double 
     const double w = V + 23.0;
     const double lin = w == 0.0 ? 5.0 : 0.2 * w / (-expm1(-0.04 * w));
     c[13] = 0.35 * (4.0 * (exp(0.04 * (V + 85.0)) - 1.0) / (exp(0.08 * (V + 53.0)) + exp(0.04 * (V + 53.0))) + lin);
-    c[14] = c[15] = 0.0;
+    c[14] = al[5];
+    c[15] = tau_c > 0.0 ? -expm1(-dt / tau_c) : 0.0;
     for (int q = 0; q < 4; ++q)
         tab[e * 4 + q] = make_float4((float)c[4 * q], (float)c[4 * q + 1], (float)c[4 * q + 2], (float)c[4 * q + 3]);
 }
@@ -87,9 +89,9 @@ __global__ void k_rl_table(float4* __restrict__ tab, int n, double vmin, double 
 }  // namespace
 
 // Tabulate the Rush-Larsen coefficients of Beeler-Reuter for the time step
-// dt into tab (kTabN x 4 float4).
-cudaError_t br_build_rl_table(float4* tab, double dt, cudaStream_t s) {
-    k_rl_table<<<(kTabN + 127) / 128, 128, 0, s>>>(tab, kTabN, (double)kTabVmin, (double)kTabDv, dt);
+// dt into tab (kTabN x 4 float4); tau_c > 0 adds the calcium gate's constant.
+cudaError_t br_build_rl_table(float4* tab, double dt, double tau_c, cudaStream_t s) {
+    k_rl_table<<<(kTabN + 127) / 128, 128, 0, s>>>(tab, kTabN, (double)kTabVmin, (double)kTabDv, dt, tau_c);
     return cudaGetLastError();
 }
 

@@ -17,7 +17,7 @@ import numpy as np
 
 SEED0 = 16050601
 
-FHN, BARKLEY, BR, ZFK, BR_MRL = 1, 2, 3, 4, 6
+FHN, BARKLEY, BR, ZFK, BR_MRL, BR_FCA = 1, 2, 3, 4, 6, 7
 
 
 @dataclass
@@ -198,6 +198,20 @@ def br_mrl_slab(nx=256, ny=256, nz=64, **kw):
     w = br_slab(nx, ny, nz, **kw)
     w.name = "br_mrl_slab_%dx%dx%d" % (nx, ny, nz)
     w.model = BR_MRL
+    return w
+
+
+def br_fca_slab(nx=256, ny=256, nz=64, onfly=False, **kw):
+    """br_slab with the slow inward current's inactivation as a two-gate
+    channel (voltage gate f, calcium gate c; BR_FCA, the multivariate chain
+    split into univariate parts, or with onfly its whole generator's
+    exponential at run time); same geometry, fibres and initial condition,
+    default channel parameters."""
+    w = br_slab(nx, ny, nz, **kw)
+    w.name = "br_fca_slab_%dx%dx%d%s" % (nx, ny, nz, "_onfly" if onfly else "")
+    w.model = BR_FCA
+    if onfly:
+        w.params = [4.0, 0.003, 50.0, 0.09, 5e-6, 2.0, 0.05, 1.0]
     return w
 
 

@@ -204,3 +204,25 @@ def test_rk4_is_refused_and_lie_splitting_runs():
     s = oracle.Sim(g, oracle.BR_FCA, split=True)
     s.step(0.02, 3)
     assert np.all(np.isfinite(s.state))
+
+
+def test_onfly_cell_update_takes_the_exponential_of_the_whole_generator():
+    # parameter onfly = 1: the channel's step in the cell update is
+    # exp(dt A(V_n, Ca_n)) u_n (scipy's expm); the other variables are those
+    # of the split cell update
+    par_s = list(oracle.FCA_DEFAULTS)
+    par_x = list(oracle.FCA_DEFAULTS)
+    par_x[7] = 1.0
+    rng = np.random.default_rng(7)
+    r = oracle.rest_state(oracle.BR_FCA)
+    for V, Ca in [(-84.0, 1.6e-7), (-20.0, 2e-6), (10.0, 8e-6)]:
+        y = r.copy()
+        y[0], y[1] = V, Ca
+        y[7:] = rng.dirichlet(np.ones(4))
+        for dt in (0.02, 0.5):
+            ys = oracle.cell_update(oracle.BR_FCA, y, dt=dt, par=par_s)
+            yx = oracle.cell_update(oracle.BR_FCA, y, dt=dt, par=par_x)
+            ref = expm(dt * oracle.fca_generator(V, Ca)) @ y[7:]
+            assert np.allclose(yx[7:], ref, rtol=0, atol=1e-13)
+            assert np.array_equal(yx[:7], ys[:7])
+            assert 0.0 < np.abs(yx[7:] - ys[7:]).max() < 0.05 * dt * dt
