@@ -115,6 +115,20 @@ __device__ __forceinline__ int cell_crossings(const float g[4], float2 p[2]) {
     return n;
 }
 
+// Number of the four cell edges whose ends lie on different sides of the
+// isoline (g > 0 at one end only): the same test cell_crossings applies.
+__device__ __forceinline__ int edge_changes(const float g[4]) {
+    const unsigned s = (g[0] > 0.0f ? 1u : 0u) | (g[1] > 0.0f ? 2u : 0u) | (g[2] > 0.0f ? 4u : 0u) |
+                       (g[3] > 0.0f ? 8u : 0u);
+    return __popc(s ^ (((s >> 1) | (s << 3)) & 15u));
+}
+
+// Each warp takes whole rows of cells (y, z); each lane four consecutive
+// cells x .. x+3, from float4 loads of rows y and y+1 of both fields (px is a
+// multiple of 32, so x + 3 stays inside the padded row) and the corner column
+// x + 4 from the next lane, or loaded where no next lane holds it.  A cell is
+// examined further only where both isolines change sides exactly twice
+// around it; that examination is cell_crossings and the intersection below.
 __global__ void k_singz(const float* __restrict__ s0, const float* __restrict__ s1, const int* __restrict__ cur,
                         long long off_a, long long off_b, float iso_a, float iso_b, const uint8_t* __restrict__ mask,
                         int nx, int ny, int nz, int px, long long plane, float* __restrict__ xyz, int max_points,
@@ -122,45 +136,81 @@ __global__ void k_singz(const float* __restrict__ s0, const float* __restrict__ 
     const float* st = *cur ? s1 : s0;  // the current buffer, from the grid's parity
     const float* fa = st + off_a;
     const float* fb = st + off_b;
-    // each warp takes whole rows of cells (y, z), its lanes walking x
     const int cx = nx - 1, cy = ny - 1;
+    const int gx = (cx + 3) / 4;  // groups of four cells in a row
     const long long rows = (long long)cy * nz;
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long rr = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); rr < rows; rr += warps)
-    for (int x = lane; x < cx; x += 32) {
+    for (long long rr = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); rr < rows; rr += warps) {
         const int z = (int)(rr / cy), y = (int)(rr - (long long)z * cy);
-        const long long g0 = z * plane + (long long)y * px + x;
-        const long long gi[4] = {g0, g0 + 1, g0 + px + 1, g0 + px};  // corners in cell order
-        bool tis = true;
-        if (mask) {
+        const long long r0 = z * plane + (long long)y * px, r1 = r0 + px;
+        for (int gb = 0; gb < gx; gb += 32) {
+            const int g = gb + lane;
+            const bool act = g < gx;
+            const int x = 4 * g;
+            float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+            uint32_t m0 = 0xffffffffu, m1 = 0xffffffffu;  // four mask bytes of each row (all tissue without a mask)
+            if (act) {
+                a0 = *reinterpret_cast<const float4*>(fa + r0 + x);
+                a1 = *reinterpret_cast<const float4*>(fa + r1 + x);
+                b0 = *reinterpret_cast<const float4*>(fb + r0 + x);
+                b1 = *reinterpret_cast<const float4*>(fb + r1 + x);
+                if (mask) {
+                    m0 = *reinterpret_cast<const uint32_t*>(mask + r0 + x);
+                    m1 = *reinterpret_cast<const uint32_t*>(mask + r1 + x);
+                }
+            }
+            float a0e = __shfl_down_sync(0xffffffffu, a0.x, 1), a1e = __shfl_down_sync(0xffffffffu, a1.x, 1);
+            float b0e = __shfl_down_sync(0xffffffffu, b0.x, 1), b1e = __shfl_down_sync(0xffffffffu, b1.x, 1);
+            uint32_t m0e = __shfl_down_sync(0xffffffffu, m0, 1), m1e = __shfl_down_sync(0xffffffffu, m1, 1);
+            if (!act) continue;
+            if ((lane == 31 || g + 1 >= gx) && x + 4 < nx) {  // column x + 4 of the last cell
+                a0e = fa[r0 + x + 4];
+                a1e = fa[r1 + x + 4];
+                b0e = fb[r0 + x + 4];
+                b1e = fb[r1 + x + 4];
+                if (mask) {
+                    m0e = mask[r0 + x + 4];
+                    m1e = mask[r1 + x + 4];
+                }
+            }
+            const float A0[5] = {a0.x, a0.y, a0.z, a0.w, a0e}, A1[5] = {a1.x, a1.y, a1.z, a1.w, a1e};
+            const float B0[5] = {b0.x, b0.y, b0.z, b0.w, b0e}, B1[5] = {b1.x, b1.y, b1.z, b1.w, b1e};
+            const uint32_t t0 = (m0 & 0x01010101u) | ((m0e & 1u) << 31);  // tissue bits, column k at bit 8k
+            const uint32_t t1 = (m1 & 0x01010101u) | ((m1e & 1u) << 31);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) tis = tis && (mask[gi[k]] & kTissue);
-        }
-        if (!tis) continue;
-        float ga[4], gb[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            ga[k] = __fsub_rn(fa[gi[k]], iso_a);
-            gb[k] = __fsub_rn(fb[gi[k]], iso_b);
-        }
-        float2 pa[2], pb[2];
-        if (cell_crossings(ga, pa) != 2 || cell_crossings(gb, pb) != 2) continue;
-        // pa0 + al (pa1 - pa0) = pb0 + be (pb1 - pb0)
-        const float d1x = pa[1].x - pa[0].x, d1y = pa[1].y - pa[0].y;
-        const float d2x = pb[1].x - pb[0].x, d2y = pb[1].y - pb[0].y;
-        const float det = d1y * d2x - d1x * d2y;
-        if (det == 0.0f) continue;
-        const float rx = pb[0].x - pa[0].x, ry = pb[0].y - pa[0].y;
-        const float rdet = __frcp_rn(det);
-        const float al = (ry * d2x - rx * d2y) * rdet;
-        const float be = (d1x * ry - d1y * rx) * rdet;
-        if (!(al >= 0.0f && al <= 1.0f && be >= 0.0f && be <= 1.0f)) continue;
-        const int k = atomicAdd(count, 1);
-        if (k < max_points) {
-            xyz[3 * k] = (float)x + pa[0].x + al * d1x;
-            xyz[3 * k + 1] = (float)y + pa[0].y + al * d1y;
-            xyz[3 * k + 2] = (float)z;
+            for (int k = 0; k < 4; ++k) {
+                if (x + k >= cx) break;
+                if (mask) {
+                    const uint32_t n0 = k < 3 ? (t0 >> (8 * (k + 1))) & 1u : t0 >> 31;
+                    const uint32_t n1 = k < 3 ? (t1 >> (8 * (k + 1))) & 1u : t1 >> 31;
+                    if (!(((t0 >> (8 * k)) & 1u) && n0 && n1 && ((t1 >> (8 * k)) & 1u))) continue;
+                }
+                // corners in cell order: (x, y), (x+1, y), (x+1, y+1), (x, y+1)
+                const float ga[4] = {__fsub_rn(A0[k], iso_a), __fsub_rn(A0[k + 1], iso_a), __fsub_rn(A1[k + 1], iso_a),
+                                     __fsub_rn(A1[k], iso_a)};
+                const float gbv[4] = {__fsub_rn(B0[k], iso_b), __fsub_rn(B0[k + 1], iso_b),
+                                      __fsub_rn(B1[k + 1], iso_b), __fsub_rn(B1[k], iso_b)};
+                if (edge_changes(ga) != 2 || edge_changes(gbv) != 2) continue;
+                float2 pa[2], pb[2];
+                if (cell_crossings(ga, pa) != 2 || cell_crossings(gbv, pb) != 2) continue;
+                // pa0 + al (pa1 - pa0) = pb0 + be (pb1 - pb0)
+                const float d1x = pa[1].x - pa[0].x, d1y = pa[1].y - pa[0].y;
+                const float d2x = pb[1].x - pb[0].x, d2y = pb[1].y - pb[0].y;
+                const float det = d1y * d2x - d1x * d2y;
+                if (det == 0.0f) continue;
+                const float rx = pb[0].x - pa[0].x, ry = pb[0].y - pa[0].y;
+                const float rdet = __frcp_rn(det);
+                const float al = (ry * d2x - rx * d2y) * rdet;
+                const float be = (d1x * ry - d1y * rx) * rdet;
+                if (!(al >= 0.0f && al <= 1.0f && be >= 0.0f && be <= 1.0f)) continue;
+                const int slot = atomicAdd(count, 1);
+                if (slot < max_points) {
+                    xyz[3 * slot] = (float)(x + k) + pa[0].x + al * d1x;
+                    xyz[3 * slot + 1] = (float)y + pa[0].y + al * d1y;
+                    xyz[3 * slot + 2] = (float)z;
+                }
+            }
         }
     }
 }
