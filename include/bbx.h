@@ -294,6 +294,24 @@ int bbx_read_all(bbx_grid* g, float* host_out, size_t n);
  * Synchronises.  Errors as bbx_read_all / bbx_write_all, BBX_ERR_CUDA. */
 int bbx_exchange_state(bbx_grid* g, const float* host_in, float* host_out, size_t n);
 
+/* The same exchange, enqueued without waiting (a pipeline of steps fed from and
+ * drained to the host: each step's copies overlap the neighbouring steps).
+ * The current state (as the grid's stream will hold it when the call's work
+ * runs, i.e. after every step enqueued before) goes to host_out and host_in
+ * becomes the new state, through two device stages in each direction and
+ * their own host-to-device and device-to-host streams; steps enqueued after
+ * the call see the new state.  The host buffers must be pinned, stay valid and
+ * unchanged (host_in) and unread (host_out) until bbx_exchange_wait returns;
+ * the library keeps 4 x nvars x nx*ny*nz floats of stages per grid from the
+ * first call on.  Grids with padded rows (nx not a multiple of 32) or 16-bit
+ * gates: BBX_ERR_UNSUPPORTED (use bbx_exchange_state).  BBX_ERR_ARG, BBX_ERR_STATE,
+ * BBX_ERR_NOMEM, BBX_ERR_CUDA. */
+int bbx_exchange_state_async(bbx_grid* g, const float* host_in, float* host_out, size_t n);
+
+/* Wait until every bbx_exchange_state_async of the grid has finished with its
+ * host buffers.  BBX_ERR_ARG, BBX_ERR_CUDA. */
+int bbx_exchange_wait(bbx_grid* g);
+
 /* Activation steps (BBX_ACT_NONE where not activated), n int32.  Synchronises. */
 int bbx_read_activation(bbx_grid* g, int32_t* host_out, size_t n);
 

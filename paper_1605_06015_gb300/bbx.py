@@ -62,6 +62,8 @@ def _load():
         "bbx_write_all": [P, P, Z],
         "bbx_read_all": [P, P, Z],
         "bbx_exchange_state": [P, P, P, Z],
+        "bbx_exchange_state_async": [P, P, P, Z],
+        "bbx_exchange_wait": [P],
         "bbx_debug_cover_chunks": [P, I, I, I, I, I, I, P, I, P],
         "bbx_debug_plan_first_pieces": [P, I, I, P, I, P],
         "bbx_bind_state": [P, P, P, Z],
@@ -256,6 +258,37 @@ def bbx_exchange_state(g, state_in, out):
         raise ValueError("out must be a contiguous float32 array")
     _check(_lib.bbx_exchange_state(g, ip, op, S * n), "bbx_exchange_state")
     return out
+
+
+def _pinned_ptr(a):
+    """(host pointer, elements) of a contiguous float32 buffer that the caller
+    keeps alive (a pinned CPU tensor or a NumPy array); no copies."""
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        if a.is_cuda or not a.is_contiguous() or a.element_size() != 4 or a.is_floating_point() is False:
+            raise ValueError("expected a contiguous float32 CPU tensor")
+        return a.data_ptr(), a.numel()
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags.c_contiguous):
+        raise ValueError("expected a contiguous float32 array")
+    return a.ctypes.data, a.size
+
+
+def bbx_exchange_state_async(g, state_in, out):
+    """Enqueue out <- the current state and state_in -> the new state without
+    waiting; both must be contiguous float32 buffers of nvars x nz x ny x nx
+    elements (pinned CPU tensors for the copies to overlap) that stay alive
+    and untouched until bbx_exchange_wait.  Makes no synchronising call (the
+    library checks the element count against the grid)."""
+    ip, ni = _pinned_ptr(state_in)
+    op, no = _pinned_ptr(out)
+    if ni != no:
+        raise ValueError("state_in and out differ in size")
+    _check(_lib.bbx_exchange_state_async(g, ip, op, ni), "bbx_exchange_state_async")
+    return out
+
+
+def bbx_exchange_wait(g):
+    """Wait for the grid's asynchronous exchanges to finish with their host buffers."""
+    _check(_lib.bbx_exchange_wait(g), "bbx_exchange_wait")
 
 
 def bbx_debug_cover_chunks(flags, ty, zb, nz):

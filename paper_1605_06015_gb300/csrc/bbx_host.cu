@@ -397,6 +397,18 @@ __global__ void k_rest(int model, const float* mp, double beta_d, double gamma_d
     }
 }
 
+// Device-to-device copy of n4 float4 by the SMs (the asynchronous exchange's
+// stage copies, which would otherwise take a copy engine from the host copies
+// they are meant to overlap); up to two destinations.
+__global__ void k_copy4(float4* __restrict__ d0, float4* __restrict__ d1, const float4* __restrict__ src,
+                        long long n4) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+        const float4 v = __ldcs(src + i);
+        d0[i] = v;
+        if (d1) d1[i] = v;
+    }
+}
+
 __global__ void k_fill_state(float* __restrict__ st, int S, long long vol, const float* __restrict__ rest) {
     const long long n = (long long)S * vol;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -817,6 +829,15 @@ struct bbx_grid {
     int h_cur = 0;            // buffer parity as the enqueued work leaves it (mirror of d_dyn->cur)
     cudaStream_t copy_stream = nullptr;          // bbx_exchange_state: device-to-host copies
     cudaEvent_t ev_enter = nullptr, ev_out = nullptr;
+    // bbx_exchange_state_async: two input and two output stages on the device,
+    // a host-to-device and a device-to-host stream, and per stage the events
+    // that order them against the grid's stream
+    float* d_xin[2] = {nullptr, nullptr};
+    float* d_xout[2] = {nullptr, nullptr};
+    size_t x_bytes = 0;
+    cudaStream_t xs_in = nullptr, xs_out = nullptr;
+    cudaEvent_t xev_in_ready[2] = {}, xev_in_used[2] = {}, xev_out_ready[2] = {}, xev_out_done[2] = {};
+    long long x_issued = 0;  // asynchronous exchanges issued since the stages were allocated
     int tab_model = 0;        // the model d_tab was built for
     double tab_tau_c = 0.0;   // and its tau_c (BBX_BR_FCA; 0 otherwise)
     bool tab_on = false;      // Beeler-Reuter with tabulated Rush-Larsen coefficients (bbx_set_tabulation)
@@ -1137,6 +1158,26 @@ bool wants_general(const bbx_grid* g) { return g->split || g->rk4 || (g->tab_on 
 // BBX_BR_MRL), allocated on first use and rebuilt on the grid's stream
 // whenever the model, the time step or tau_c differs from the ones it was
 // built for.
+// The asynchronous exchange's stages, streams and events, after its copies end.
+void exchange_release(bbx_grid* g) {
+    if (g->xs_out) cudaStreamSynchronize(g->xs_out);
+    if (g->xs_in) cudaStreamSynchronize(g->xs_in);
+    for (int j = 0; j < 2; ++j) {
+        cudaFree(g->d_xin[j]);
+        cudaFree(g->d_xout[j]);
+        g->d_xin[j] = g->d_xout[j] = nullptr;
+        for (cudaEvent_t* e : {&g->xev_in_ready[j], &g->xev_in_used[j], &g->xev_out_ready[j], &g->xev_out_done[j]}) {
+            if (*e) cudaEventDestroy(*e);
+            *e = nullptr;
+        }
+    }
+    if (g->xs_in) cudaStreamDestroy(g->xs_in);
+    if (g->xs_out) cudaStreamDestroy(g->xs_out);
+    g->xs_in = g->xs_out = nullptr;
+    g->x_bytes = 0;
+    g->x_issued = 0;
+}
+
 int tab_refresh(bbx_grid* g) {
     const bool want = g->model == BBX_BR_MRL || g->model == BBX_BR_FCA || (g->model == BBX_BR && g->tab_on);
     if (!want) return BBX_OK;
@@ -1305,6 +1346,7 @@ const char* bbx_status_string(int s) {
 void bbx_destroy_grid(bbx_grid* g) {
     if (!g) return;
     cudaStreamSynchronize(g->stream);
+    exchange_release(g);
     if (g->copy_stream) {
         cudaStreamSynchronize(g->copy_stream);
         cudaStreamDestroy(g->copy_stream);
@@ -1879,6 +1921,10 @@ int bbx_read_all(bbx_grid* g, float* host, size_t n) {
 int bbx_exchange_state(bbx_grid* g, const float* host_in, float* host_out, size_t n) {
     if (!g) return BBX_ERR_ARG;
     if (!g->model) return BBX_ERR_STATE;
+    if (g->x_issued) {  // asynchronous exchanges still writing the caller's buffers
+        const int rc = bbx_exchange_wait(g);
+        if (rc) return rc;
+    }
     if (!host_in || !host_out || n != (size_t)g->S * (size_t)g->ncell) return BBX_ERR_ARG;
     if (g->px != g->nx || g->gates != GATES_F32) {  // padded rows or 16-bit gates: one direction after the other
         int rc = bbx_read_all(g, host_out, n);
@@ -1909,6 +1955,77 @@ int bbx_exchange_state(bbx_grid* g, const float* host_in, float* host_out, size_
     g->h_cur = oth;
     BBX_CUDA(cudaStreamSynchronize(g->stream));
     return check_sticky(g);
+}
+
+int bbx_exchange_state_async(bbx_grid* g, const float* host_in, float* host_out, size_t n) {
+    if (!g) return BBX_ERR_ARG;
+    if (!g->model) return BBX_ERR_STATE;
+    if (!host_in || !host_out || n != (size_t)g->S * (size_t)g->ncell) return BBX_ERR_ARG;
+    if (g->px != g->nx || g->gates != GATES_F32) return BBX_ERR_UNSUPPORTED;
+    const size_t bytes = sizeof(float) * n;
+    if (g->x_bytes != bytes) {  // first use, or a model with another number of variables
+        exchange_release(g);
+        bool ok = cudaStreamCreateWithFlags(&g->xs_in, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&g->xs_out, cudaStreamNonBlocking) == cudaSuccess;
+        for (int j = 0; j < 2 && ok; ++j)
+            ok = cudaEventCreateWithFlags(&g->xev_in_ready[j], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&g->xev_in_used[j], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&g->xev_out_ready[j], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&g->xev_out_done[j], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            exchange_release(g);
+            return BBX_ERR_CUDA;
+        }
+        for (int j = 0; j < 2 && ok; ++j)
+            ok = dmalloc(&g->d_xin[j], bytes) == cudaSuccess && dmalloc(&g->d_xout[j], bytes) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            exchange_release(g);
+            return BBX_ERR_NOMEM;
+        }
+        g->x_bytes = bytes;
+        g->x_issued = 0;
+    }
+    const int j = (int)(g->x_issued & 1);
+    const bool reuse = g->x_issued >= 2;  // stage j was used two exchanges ago
+    const int cur = g->h_cur;
+    // the current state into output stage j (once that stage's previous copy to
+    // the host is done), then to the host on the output stream
+    const long long n4 = (long long)(bytes / 16);  // vol is a multiple of 32 floats (rows padded to 32)
+    const int cb = g->num_sms * 4;
+    if (reuse) BBX_CUDA(cudaStreamWaitEvent(g->stream, g->xev_out_done[j], 0));
+    k_copy4<<<cb, 256, 0, g->stream>>>(reinterpret_cast<float4*>(g->d_xout[j]), nullptr,
+                                       reinterpret_cast<const float4*>(g->d_state[cur]), n4);
+    BBX_CUDA(cudaGetLastError());
+    BBX_CUDA(cudaEventRecord(g->xev_out_ready[j], g->stream));
+    BBX_CUDA(cudaStreamWaitEvent(g->xs_out, g->xev_out_ready[j], 0));
+    BBX_CUDA(cudaMemcpyAsync(host_out, g->d_xout[j], bytes, cudaMemcpyDeviceToHost, g->xs_out));
+    BBX_CUDA(cudaEventRecord(g->xev_out_done[j], g->xs_out));
+    // the new state into input stage j on the input stream (once the grid's
+    // stream has taken what the stage held before), then into the state
+    if (reuse) BBX_CUDA(cudaStreamWaitEvent(g->xs_in, g->xev_in_used[j], 0));
+    BBX_CUDA(cudaMemcpyAsync(g->d_xin[j], host_in, bytes, cudaMemcpyHostToDevice, g->xs_in));
+    BBX_CUDA(cudaEventRecord(g->xev_in_ready[j], g->xs_in));
+    BBX_CUDA(cudaStreamWaitEvent(g->stream, g->xev_in_ready[j], 0));
+    // (void nodes hold the same values in both buffers of a masked grid)
+    k_copy4<<<cb, 256, 0, g->stream>>>(reinterpret_cast<float4*>(g->d_state[cur]),
+                                       g->d_mask ? reinterpret_cast<float4*>(g->d_state[cur ^ 1]) : nullptr,
+                                       reinterpret_cast<const float4*>(g->d_xin[j]), n4);
+    BBX_CUDA(cudaGetLastError());
+    BBX_CUDA(cudaEventRecord(g->xev_in_used[j], g->stream));
+    ++g->x_issued;
+    return BBX_OK;
+}
+
+int bbx_exchange_wait(bbx_grid* g) {
+    if (!g) return BBX_ERR_ARG;
+    if (!g->xs_in) return BBX_OK;
+    const cudaError_t a = cudaStreamSynchronize(g->xs_out);
+    const cudaError_t b = cudaStreamSynchronize(g->xs_in);
+    if (a != cudaSuccess) return fail_cuda(a);
+    if (b != cudaSuccess) return fail_cuda(b);
+    return BBX_OK;
 }
 
 int bbx_read_activation(bbx_grid* g, int32_t* host, size_t n) {

@@ -559,3 +559,67 @@ def test_exchange_state_is_read_all_then_write_all(bbx, nx, masked):
     H.write_all(s0)
     H.step(w.dt, 2)
     assert np.array_equal(G.read_all(), H.read_all())
+
+
+@pytest.mark.parametrize("masked", [False, True])
+def test_asynchronous_exchange_pipeline_matches_the_synchronous_one(bbx, masked):
+    # a pipeline of exchange-then-step with new inputs every step: the
+    # asynchronous exchange (stages on the device, copies on their own
+    # streams, no wait until the end) gives every step's output bitwise as the
+    # synchronous exchange does; then the state is read back as usual
+    import torch
+    w = wl.barkley_slab(64, 24, 8)
+    if masked:
+        w.mask, w.fibres = wl.random_geometry(64, 24, 8, seed=9, tissue_frac=0.8)
+    rest = oracle.rest_state(w.model, w.params)
+    s0 = w.initial_state(rest).astype(np.float32)
+    rng = np.random.default_rng(5)
+    ins = [(s0 + np.float32(0.01) * rng.random(s0.shape, dtype=np.float32)).astype(np.float32) for _ in range(5)]
+    A = _gpu_grid(bbx, w, 14, 4)
+    B = _gpu_grid(bbx, w, 14, 4)
+    A.write_all(s0)
+    B.write_all(s0)
+    pin_in = [torch.from_numpy(x).pin_memory() for x in ins]
+    pin_out = [torch.empty(s0.shape, dtype=torch.float32).pin_memory() for _ in ins]
+    ref_out = [np.empty_like(s0) for _ in ins]
+    for k in range(len(ins)):
+        A.exchange_state_async(pin_in[k], pin_out[k])
+        A.step(w.dt, 2)
+        B.exchange_state(ins[k], ref_out[k])
+        B.step(w.dt, 2)
+    A.exchange_wait()
+    for k in range(len(ins)):
+        assert np.array_equal(pin_out[k].numpy(), ref_out[k]), k
+    assert np.array_equal(A.read_all(), B.read_all())
+    # the same host buffers reused every step (the pattern of a streaming loop)
+    for k in range(3):
+        A.exchange_state_async(pin_in[k], pin_out[0])
+        A.step(w.dt, 1)
+        B.exchange_state(ins[k], ref_out[0])
+        B.step(w.dt, 1)
+    A.exchange_wait()
+    assert np.array_equal(pin_out[0].numpy(), ref_out[0])
+    assert np.array_equal(A.read_all(), B.read_all())
+    # a synchronous exchange after an asynchronous one waits for it first
+    prev = A.read_all()
+    out = np.empty_like(s0)
+    A.exchange_state_async(pin_in[0], pin_out[1])
+    A.exchange_state(ins[1], out)
+    assert np.array_equal(pin_out[1].numpy(), prev)
+    assert np.array_equal(out, ins[0])
+    assert np.array_equal(A.read_all(), ins[1])
+
+
+def test_asynchronous_exchange_refusals(bbx):
+    import torch
+    w = wl.barkley_slab(70, 24, 8)  # padded rows
+    G = _gpu_grid(bbx, w, 14, 4)
+    S = 2
+    a = torch.zeros((S,) + w.shape, dtype=torch.float32).pin_memory()
+    b = torch.zeros((S,) + w.shape, dtype=torch.float32).pin_memory()
+    with pytest.raises(bbx.BbxError) as e:
+        G.exchange_state_async(a, b)
+    assert e.value.code == bbx.BBX_ERR_UNSUPPORTED
+    with pytest.raises(ValueError):
+        G.exchange_state_async(a.double(), b)
+    G.exchange_wait()  # nothing pending: returns at once
