@@ -104,6 +104,9 @@ struct LaunchArgs {
     int n_slots;               // ctas x cta_stride; unused slots keep a zero partial
     double* partials;          // one per slot
     unsigned int* ticket;      // zero between launches
+    unsigned int* tissue_done; // per grid: pieces finished in this launch (zero between launches)
+    const int* empty_tissues;  // the grids with no piece (their time still advances)
+    int n_empty;
     int* err;                  // sticky error bits
     long long wait_limit;      // clock64 cycles a wait may spin before giving up
     int poison_first_load;     // fault injection: CTA 0's first plane never completes
@@ -281,15 +284,72 @@ __device__ __forceinline__ void start_ticket(const LaunchArgs& L, const TissueDy
     }
 }
 
-// End of a launch over several grids, in the last CTA to finish: per-grid
-// totals from the per-piece partials (fixed order), then t += dt, n += 1 and
-// the buffer parity flip of every grid of the launch.  A single-grid launch
-// has no end step: its producers advance t, n and the parity as soon as
-// every CTA has read them (start_ticket), and the grid's total is summed
-// from the partials when it is asked for.
+// The fixed-order sum of a grid's per-piece partials tissue_pieces[k0 .. k1):
+// each of `stride` threads takes every stride-th piece from `first`, four
+// loads at a time so their L2 latencies overlap; then a shuffle tree over
+// the warp (the caller adds the warps' results in order).
+__device__ __forceinline__ double grid_partials_sum(const LaunchArgs& L, int k0, int k1, int first, int stride) {
+    double s = 0.0;
+    for (int k = k0 + first; k < k1; k += 4 * stride) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int kk = k + u * stride;
+            v[u] = kk < k1 ? __ldcg(&L.partials[__ldcg(&L.tissue_pieces[kk])]) : 0.0;
+        }
+        s += (v[0] + v[1]) + (v[2] + v[3]);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// The end of a grid's step in a launch over several grids: its total, then
+// t += dt, n += 1 and the buffer parity flip.
+__device__ __forceinline__ void finish_grid(const LaunchArgs& L, int ti, double s) {
+    const TissueArgs* T = L.tissues + ti;
+    TissueDyn* d = T->dyn;
+    if (!isfinite(s)) atomicOr(L.err, ERRBIT_NAN);
+    d->total = s;
+    d->t = d->t + T->dt_d;
+    d->n = d->n + 1;
+    d->cur = d->cur ^ 1;
+    d->total_pending = 0;
+}
+
+// Launch over several grids, one warp of the CTA that has just written the
+// partial of piece pi (lane 0 wrote it): the piece counts towards its grid,
+// and the CTA that completes a grid finishes it at once (per-grid sums spread
+// over the CTAs while the others still compute, instead of one CTA summing
+// every grid at the end).  A grid's pieces all precede its finish, so no
+// producer reads the grid's parity after it flips.
+__device__ __forceinline__ void grid_piece_done(const LaunchArgs& L, int pi, int lane) {
+    int fin = -1;
+    if (lane == 0) {
+        __threadfence();  // the piece's partial before its count
+        const int ti = L.piece_tissue[pi];
+        const unsigned int npc = (unsigned int)(L.tissue_off[ti + 1] - L.tissue_off[ti]);
+        if (atomicAdd(&L.tissue_done[ti], 1u) == npc - 1u) fin = ti;
+    }
+    fin = __shfl_sync(0xffffffffu, fin, 0);
+    if (fin < 0) return;
+    __threadfence();
+    const double s = grid_partials_sum(L, __ldcg(&L.tissue_off[fin]), __ldcg(&L.tissue_off[fin + 1]), lane, 32);
+    if (lane == 0) {
+        finish_grid(L, fin, s);
+        L.tissue_done[fin] = 0u;
+    }
+}
+
+// End of a launch over several grids: the grids without pieces (no tissue)
+// advance t, n and the parity in the last CTA to finish; the others were
+// finished by grid_piece_done.  A single-grid launch has no end step: its
+// producers advance t, n and the parity as soon as every CTA has read them
+// (start_ticket), and the grid's total is summed from the partials when it
+// is asked for.
 __device__ __forceinline__ void step_finalize(const LaunchArgs& L, double* scratch32) {
     __shared__ bool last;
-    if (L.single) return;
+    (void)scratch32;
+    if (L.single || L.n_empty == 0) return;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -298,53 +358,7 @@ __device__ __forceinline__ void step_finalize(const LaunchArgs& L, double* scrat
     }
     __syncthreads();
     if (!last) return;
-    __threadfence();
-    // Fixed-order sums (deterministic).  One grid in the launch: every
-    // thread of the CTA strides over its pieces, then a shuffle tree per warp
-    // and the warps in order.  Several grids: one warp per grid, lanes
-    // striding its pieces.  The partials are loaded several at a time so
-    // their L2 latencies overlap.
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
-    auto finish = [&](int ti, double s) {
-        const TissueArgs* T = L.tissues + ti;
-        TissueDyn* d = T->dyn;
-        if (!isfinite(s)) atomicOr(L.err, ERRBIT_NAN);
-        d->total = s;
-        d->t = d->t + T->dt_d;
-        d->n = d->n + 1;
-        d->cur = d->cur ^ 1;
-        d->total_pending = 0;
-    };
-    // the partials of the grid's pieces tissue_pieces[k0 .. k1)
-    auto strided_sum = [&](int k0, int k1, int first, int stride) {
-        double s = 0.0;
-        for (int k = k0 + first; k < k1; k += 4 * stride) {
-            double v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int kk = k + u * stride;
-                v[u] = kk < k1 ? __ldcg(&L.partials[__ldcg(&L.tissue_pieces[kk])]) : 0.0;
-            }
-            s += (v[0] + v[1]) + (v[2] + v[3]);
-        }
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        return s;
-    };
-    if (L.n_tissues == 1) {
-        const double s = strided_sum(__ldcg(&L.tissue_off[0]), __ldcg(&L.tissue_off[1]), threadIdx.x, blockDim.x);
-        if (lane == 0) scratch32[warp] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < nwarps; ++w) t += scratch32[w];
-            finish(0, t);
-        }
-    } else {
-        for (int ti = warp; ti < L.n_tissues; ti += nwarps) {
-            const double s = strided_sum(__ldcg(&L.tissue_off[ti]), __ldcg(&L.tissue_off[ti + 1]), lane, 32);
-            if (lane == 0) finish(ti, s);
-        }
-    }
+    for (int e = threadIdx.x; e < L.n_empty; e += blockDim.x) finish_grid(L, __ldcg(&L.empty_tissues[e]), 0.0);
     __syncthreads();
     if (threadIdx.x == 0) *L.ticket = 0u;
 }
@@ -1731,6 +1745,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                 if (!isfinite(s)) atomicOr(L.err, ERRBIT_NAN);
             }
             consumers_sync(NCT);
+            if (!L.single && warp == 0 && !any_to) grid_piece_done(L, pi, lane);
             vsum.hi = vsum.lo = 0.0f;
             if (any_to) break;
         }

@@ -599,7 +599,10 @@ struct LaunchPlan {
     int* d_tissue_pieces = nullptr;
     double* d_partials = nullptr;
     unsigned int* d_ticket = nullptr;
-    size_t cap_pieces = 0, cap_cta = 0, cap_tis = 0, cap_tlist = 0;
+    unsigned int* d_tissue_done = nullptr;  // per grid, zero between launches
+    int* d_empty = nullptr;                 // grids without pieces
+    int n_empty = 0;
+    size_t cap_pieces = 0, cap_cta = 0, cap_tis = 0, cap_tlist = 0, cap_done = 0, cap_empty = 0;
     int cta_stride = 1, n_slots = 0;
 
     void release() {
@@ -610,6 +613,8 @@ struct LaunchPlan {
         cudaFree(d_tissue_pieces);
         cudaFree(d_partials);
         cudaFree(d_ticket);
+        cudaFree(d_tissue_done);
+        cudaFree(d_empty);
         *this = LaunchPlan();
     }
 };
@@ -716,6 +721,13 @@ int build_plan(LaunchPlan* lp, const std::vector<Seg>& segs, int n_tissues, int 
     if ((rc = upload(&lp->d_tissue_off, &lp->cap_tis, toff))) return rc;
     std::vector<double> zeros(nslot, 0.0);
     if ((rc = upload(&lp->d_partials, &cap_part, zeros))) return rc;
+    std::vector<unsigned int> done((size_t)n_tissues, 0u);
+    if ((rc = upload(&lp->d_tissue_done, &lp->cap_done, done))) return rc;
+    std::vector<int> empty;
+    for (int t = 0; t < n_tissues; ++t)
+        if (toff[(size_t)t + 1] == toff[(size_t)t]) empty.push_back(t);
+    if ((rc = upload(&lp->d_empty, &lp->cap_empty, empty))) return rc;
+    lp->n_empty = (int)empty.size();
     lp->cta_stride = stride;
     lp->n_slots = (int)nslot;
     if (!lp->d_ticket) {
@@ -753,6 +765,9 @@ LaunchArgs launch_args(const LaunchPlan& lp, const TissueArgs* d_tissues, int* d
     L.n_tissues = lp.n_tissues;
     L.partials = lp.d_partials;
     L.ticket = lp.d_ticket;
+    L.tissue_done = lp.d_tissue_done;
+    L.empty_tissues = lp.d_empty;
+    L.n_empty = lp.n_empty;
     L.err = d_err;
     L.poison_first_load = poison;
     L.cur_hint = -1;
@@ -2691,7 +2706,11 @@ int bbx_batch_step(bbx_batch* b, int n_steps) {
 int bbx_batch_sync(bbx_batch* b) {
     if (!b) return BBX_ERR_ARG;
     BBX_CUDA(cudaStreamSynchronize(b->ps));
-    return check_sticky_ptr(b->stream, b->d_err);
+    const int rc = check_sticky_ptr(b->stream, b->d_err);
+    if (rc)  // a launch cut short (a timeout) may have left per-grid piece counts behind
+        for (auto& gr : b->groups)
+            if (gr.lp.d_tissue_done) cudaMemset(gr.lp.d_tissue_done, 0, sizeof(unsigned int) * gr.lp.n_tissues);
+    return rc;
 }
 
 int bbx_batch_autotune(bbx_batch* b, double* best_ms) {
