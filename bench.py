@@ -563,9 +563,11 @@ def run_output(args, dev, stream, G, w, n_tissue):
     for name, grid in (("ppm_frame", G), ("phase_singularities", S)):
         ts, found = [], 0
         for i in range(12):
+            # the flush is still running when the call is enqueued, so the
+            # events see the device time of the call, not the host's latency
+            # (the singularity call still waits for its 4-byte count)
             flush.fill_(float(i))
             torch.sum(flush_rd, dim=0, out=sink)
-            torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             if name == "ppm_frame":
