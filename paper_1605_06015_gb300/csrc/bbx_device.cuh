@@ -817,9 +817,10 @@ __host__ __device__ constexpr int rows_of_threads(int ty) { return ty == 28 ? 14
 
 // Resident CTAs per SM a kernel variant is built for (the register budget:
 // two CTAs of 256 threads allow 128 registers a thread; the masked
-// anisotropic stencil with 2 rows a thread and the surrogate need more).
+// anisotropic stencil with 2 rows a thread and the surrogate need more; the
+// unmasked isotropic variants fit in 64, so four CTAs hide more latency).
 __host__ __device__ constexpr int ctas_per_sm(bool masked, bool aniso, int ty, bool surr) {
-    return (masked && aniso && ty != 7) || ty == 28 || (surr && ty != 7) ? 1 : 2;
+    return (masked && aniso && ty != 7) || ty == 28 || (surr && ty != 7) ? 1 : (!masked && !aniso && !surr ? 4 : 2);
 }
 constexpr int align128(int b) { return (b + 127) & ~127; }
 
