@@ -2585,10 +2585,31 @@ int batch_build(bbx_batch* b, const std::vector<int>* tys) {
     return BBX_OK;
 }
 
+// One batch step of grids that hold no tissue (a group without pieces):
+// nothing moves, time, step count and parity advance as for the others.
+__global__ void k_advance_empty(const TissueArgs* __restrict__ T, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        TissueDyn* d = T[i].dyn;
+        d->total = 0.0;
+        d->t = d->t + T[i].dt_d;
+        d->n = d->n + 1;
+        d->cur = d->cur ^ 1;
+        d->total_pending = 0;
+    }
+}
+
 int batch_launch_step(bbx_batch* b) {
     BBX_CUDA(cudaEventRecord(b->fork, b->ps));
     for (auto& gr : b->groups) {
-        if (gr.lp.n_planes == 0) continue;
+        if (gr.lp.n_planes == 0) {
+            if (gr.members.empty()) continue;
+            BBX_CUDA(cudaStreamWaitEvent(gr.s, b->fork, 0));
+            k_advance_empty<<<1, 32, 0, gr.s>>>(gr.d_t, (int)gr.members.size());
+            BBX_CUDA(cudaGetLastError());
+            BBX_CUDA(cudaEventRecord(gr.done, gr.s));
+            BBX_CUDA(cudaStreamWaitEvent(b->ps, gr.done, 0));
+            continue;
+        }
         BBX_CUDA(cudaStreamWaitEvent(gr.s, b->fork, 0));
         const LaunchArgs L = launch_args(gr.lp, gr.d_t, b->d_err, 0);
         BBX_CUDA(launch(gr.lp, L, gr.s));

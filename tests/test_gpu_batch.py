@@ -126,3 +126,34 @@ def test_batch_argument_errors(bbx):
     B.step(3)
     B.sync()
     assert G.get_time()[1] == 3
+
+
+def test_grid_without_tissue_in_a_batch_advances_time_and_totals(bbx):
+    # a member whose mask holds no tissue has no pieces: its time and step
+    # count still advance every batch step (the last CTA finishes it), and
+    # the grids with pieces are finished by the CTA that completes them, with
+    # totals equal to the grid stepped alone
+    ws = _members()[:3]
+    st0 = [w.initial_state(oracle.rest_state(w.model, w.params)).astype(np.float32) for w in ws]
+    empty = wl.Workload("void", 40, 20, 6, 0.3, 0.005, wl.BARKLEY, [0.75, 0.02, 0.02], 1.0, 1.0,
+                        mask=np.zeros((6, 20, 40), np.uint8), theta=0.5)
+    e0 = empty.initial_state(oracle.rest_state(empty.model, empty.params)).astype(np.float32)
+    n = 20
+    solo_tot = []
+    for w, s0 in zip(ws, st0):
+        G = _grid(bbx, w, s0)
+        G.step(w.dt, n)
+        solo_tot.append(G.step_total())
+    grids = [_grid(bbx, w, s0) for w, s0 in zip(ws, st0)] + [_grid(bbx, empty, e0)]
+    B = bbx.Batch(grids)
+    B.step(n)
+    B.sync()
+    t, steps = grids[-1].get_time()
+    assert steps == n and abs(t - n * empty.dt) < 1e-12
+    for G, ref in zip(grids[:-1], solo_tot):
+        assert G.get_time()[1] == n
+        assert abs(G.step_total() - ref) <= 1e-12 * max(1.0, abs(ref))
+    B.step(n)  # again: the per-grid piece counts were left at zero
+    B.sync()
+    assert grids[-1].get_time()[1] == 2 * n
+    assert all(G.get_time()[1] == 2 * n for G in grids)
