@@ -217,13 +217,14 @@ int bbx_phase_singularities(bbx_grid* g, int var_a, double iso_a, int var_b, dou
                             int max_points, int* n_found);
 
 /* Resident multi-step mode for small sheets.  With on = 1, bbx_step calls of
- * two or more steps on this grid run as one launch of a cluster of 8 CTAs
- * that keeps the whole sheet in their shared memory (each CTA a band of
+ * two or more steps on this grid run as one launch of a cluster of 16 CTAs
+ * (8 where the GPU offers no 16-CTA clusters) that keeps the whole sheet in
+ * their shared memory (each CTA a band of
  * rows, the rows next to its band read from the neighbours' shared memory),
  * so a step costs neither a kernel launch nor a trip through DRAM.  Serves
  * unmasked isotropic sheets (nz = 1) of FHN, Barkley, ZFK or pure diffusion
  * with the unsplit scheme and Euler solver, up to about 200 KB of state per
- * CTA (for two variables, nx * ny up to ~130 000).  Results agree with the
+ * CTA (for two variables, nx * ny up to ~260 000 with 16 CTAs).  Results agree with the
  * tiled kernel to rounding, not bitwise.  The fused total, time, step count
  * and activation map are kept as by the tiled kernel.  When the grid stops
  * qualifying (fibres, a mask, another scheme), steps go back to the tiled

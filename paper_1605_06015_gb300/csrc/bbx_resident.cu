@@ -18,7 +18,9 @@ namespace bbx {
 
 namespace {
 
-constexpr int kResCtas = 8;        // CTAs in the cluster (portable size)
+// CTAs in the cluster: 16 (a non-portable cluster size the launch asks for),
+// else the portable 8
+constexpr int kResCtasLarge = 16, kResCtasPortable = 8;
 constexpr int kResThreads = 1024;
 constexpr int kResMaxSmem = 200 * 1024;
 
@@ -28,30 +30,30 @@ __device__ __forceinline__ void res_two_sum(double& hi, double& lo, double b) {
     hi = s;
 }
 
-// Launched with kResCtas CTAs forming one cluster.  Shared memory per CTA:
+// Launched with NC CTAs forming one cluster.  Shared memory per CTA:
 // two buffers of the band's V (maxr rows of nx) and S-1 buffers of the other
 // variables, updated in place (only V is read by neighbours).
-template <int MODEL>
-__global__ void __cluster_dims__(kResCtas, 1, 1) __launch_bounds__(kResThreads, 1)
+template <int MODEL, int NC>
+__global__ void __cluster_dims__(NC, 1, 1) __launch_bounds__(kResThreads, 1)
     k_resident_sheet(const TissueArgs* __restrict__ T, int n_steps, int* __restrict__ err) {
     constexpr int S = Model<MODEL>::S;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     extern __shared__ float sm[];
     __shared__ double red_hi[kResThreads / 32], red_lo[kResThreads / 32];
-    __shared__ double cl_part[kResCtas];
+    __shared__ double cl_part[NC];
 
     const int nx = T->nx, ny = T->ny, px = T->px;
     const long long vol = T->vol;
-    const int maxr = (ny + kResCtas - 1) / kResCtas;
-    const int rb0 = (int)((long long)ny * rank / kResCtas), rb1 = (int)((long long)ny * (rank + 1) / kResCtas);
+    const int maxr = (ny + NC - 1) / NC;
+    const int rb0 = (int)((long long)ny * rank / NC), rb1 = (int)((long long)ny * (rank + 1) / NC);
     const int nr = rb1 - rb0;
     const int nb = nr * nx;
     float* V[2] = {sm, sm + maxr * nx};
     float* Wv = sm + 2 * maxr * nx;  // the other variables, (S-1) x maxr x nx
     // the neighbouring bands' V buffers (rows rb0-1 and rb1 live there)
-    const int up = rank > 0 ? rank - 1 : rank, dn = rank + 1 < kResCtas ? rank + 1 : rank;
-    const int nr_up = rb0 - (int)((long long)ny * up / kResCtas);
+    const int up = rank > 0 ? rank - 1 : rank, dn = rank + 1 < NC ? rank + 1 : rank;
+    const int nr_up = rb0 - (int)((long long)ny * up / NC);
     float* Vu[2] = {cl.map_shared_rank(V[0], up), cl.map_shared_rank(V[1], up)};
     float* Vd[2] = {cl.map_shared_rank(V[0], dn), cl.map_shared_rank(V[1], dn)};
 
@@ -142,7 +144,7 @@ __global__ void __cluster_dims__(kResCtas, 1, 1) __launch_bounds__(kResThreads, 
     cl.sync();
     if (rank == 0 && threadIdx.x == 0) {
         double tot = 0.0;
-        for (int k = 0; k < kResCtas; ++k) tot += cl_part[k];
+        for (int k = 0; k < NC; ++k) tot += cl_part[k];
         if (!isfinite(tot)) atomicOr(err, ERRBIT_NAN);
         D->total = tot;
         D->total_pending = 0;
@@ -153,33 +155,51 @@ __global__ void __cluster_dims__(kResCtas, 1, 1) __launch_bounds__(kResThreads, 
     cl.sync();  // no CTA leaves while its shared memory may still be read
 }
 
-template <int MODEL>
+template <int MODEL, int NC>
 int resident_smem(int nx, int ny) {
-    const int maxr = (ny + kResCtas - 1) / kResCtas;
+    const int maxr = (ny + NC - 1) / NC;
     return (int)(sizeof(float) * (size_t)(Model<MODEL>::S + 1) * maxr * nx);
+}
+
+// One cluster of NC CTAs, if the grid fits and the GPU can hold such a
+// cluster (*ok); returns launch errors.
+template <int MODEL, int NC>
+cudaError_t resident_try(const TissueArgs* d_t, int nx, int ny, int n_steps, int* d_err, cudaStream_t s,
+                         bool check_only, bool* ok) {
+    const int smem = resident_smem<MODEL, NC>(nx, ny);
+    *ok = false;
+    if (smem > kResMaxSmem || ny < NC) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_resident_sheet<MODEL, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    if (NC > kResCtasPortable &&
+        cudaFuncSetAttribute(k_resident_sheet<MODEL, NC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess) {
+        cudaGetLastError();  // not offered here: the caller tries the portable size
+        return cudaSuccess;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(NC);
+    cfg.blockDim = dim3(kResThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, k_resident_sheet<MODEL, NC>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return cudaSuccess;
+    }
+    if (clusters < 1) return cudaSuccess;
+    *ok = true;
+    if (check_only) return cudaSuccess;
+    k_resident_sheet<MODEL, NC><<<NC, kResThreads, smem, s>>>(d_t, n_steps, d_err);
+    return cudaGetLastError();
 }
 
 template <int MODEL>
 cudaError_t resident_launch(const TissueArgs* d_t, int nx, int ny, int n_steps, int* d_err, cudaStream_t s,
                             bool check_only, bool* ok) {
-    const int smem = resident_smem<MODEL>(nx, ny);
-    *ok = false;
-    if (smem > kResMaxSmem || ny < kResCtas) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_resident_sheet<MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(kResCtas);
-    cfg.blockDim = dim3(kResThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    int clusters = 0;
-    e = cudaOccupancyMaxActiveClusters(&clusters, k_resident_sheet<MODEL>, &cfg);
-    if (e != cudaSuccess) return e;
-    if (clusters < 1) return cudaSuccess;
-    *ok = true;
-    if (check_only) return cudaSuccess;
-    k_resident_sheet<MODEL><<<kResCtas, kResThreads, smem, s>>>(d_t, n_steps, d_err);
-    return cudaGetLastError();
+    cudaError_t e = resident_try<MODEL, kResCtasLarge>(d_t, nx, ny, n_steps, d_err, s, check_only, ok);
+    if (e != cudaSuccess || *ok) return e;
+    return resident_try<MODEL, kResCtasPortable>(d_t, nx, ny, n_steps, d_err, s, check_only, ok);
 }
 
 }  // namespace
