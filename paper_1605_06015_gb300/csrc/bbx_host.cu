@@ -899,6 +899,7 @@ struct bbx_grid {
     double* d_total2 = nullptr;
     int* d_err = nullptr;
     int* d_count = nullptr;  // phase-singularity counter (allocated on first use)
+    int* h_small = nullptr;  // pinned host words: a small result and the error bits, read in one wait
     int poison = 0;
 };
 
@@ -1294,6 +1295,27 @@ int check_sticky_ptr(cudaStream_t s, int* d_err) {
 
 int check_sticky(bbx_grid* g) { return check_sticky_ptr(g->stream, g->d_err); }
 
+// A 4-byte device result and the grid's error bits copied to pinned host
+// memory together, with one wait for the stream (one round trip instead of
+// two); then the sticky-error check as check_sticky.
+int read_word_and_sticky(bbx_grid* g, const int* d_word, int* out) {
+    if (!g->h_small && cudaMallocHost(&g->h_small, 2 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        g->h_small = nullptr;
+        BBX_CUDA(cudaMemcpyAsync(out, d_word, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+        return check_sticky(g);
+    }
+    BBX_CUDA(cudaMemcpyAsync(g->h_small, d_word, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    BBX_CUDA(cudaMemcpyAsync(g->h_small + 1, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    BBX_CUDA(cudaStreamSynchronize(g->stream));
+    *out = g->h_small[0];
+    const int err = g->h_small[1];
+    if (err & ERRBIT_TIMEOUT) return BBX_ERR_TIMEOUT;
+    if (err & ERRBIT_NAN) return BBX_ERR_NAN;
+    if (err & ERRBIT_HINT) return BBX_ERR_STATE;
+    return BBX_OK;
+}
+
 // Dense host field <-> pitched device field; one linear copy when the rows
 // are not padded (nx a multiple of 32).
 int copy_in(bbx_grid* g, void* dst, const void* src, size_t elem) {
@@ -1392,6 +1414,7 @@ void bbx_destroy_grid(bbx_grid* g) {
     cudaFree(g->d_total2);
     cudaFree(g->d_err);
     cudaFree(g->d_count);
+    if (g->h_small) cudaFreeHost(g->h_small);
     cudaGetLastError();
     delete g;
 }
@@ -2114,9 +2137,7 @@ int bbx_phase_singularities(bbx_grid* g, int var_a, double iso_a, int var_b, dou
     BBX_CUDA(launch_singz(g->d_state[0], g->d_state[1], &g->d_dyn->cur, (long long)var_a * g->vol,
                           (long long)var_b * g->vol, (float)iso_a, (float)iso_b, g->d_mask, g->nx, g->ny, g->nz, g->px,
                           g->plane, xyz_dev, max_points, g->d_count, g->num_sms, g->stream));
-    BBX_CUDA(cudaMemcpyAsync(n_found, g->d_count, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
-    BBX_CUDA(cudaStreamSynchronize(g->stream));
-    return check_sticky(g);
+    return read_word_and_sticky(g, g->d_count, n_found);
 }
 
 int bbx_step_total(bbx_grid* g, double* out) {
