@@ -206,3 +206,56 @@ def test_surrogate_activation_against_the_oracle_at_the_benchmark_thresholds(env
             assert frac > 0.1
     finally:
         bbx.bbx_mlp_destroy(m)
+
+
+def test_state_of_more_than_two_to_the_31_elements_one_step_sampled(env):
+    # A Beeler-Reuter slab of 1024 x 512 x 520 nodes (8 variables: 2.18e9
+    # state elements, beyond 32-bit element offsets) with random fibre
+    # directions and a random voltage field: one step, checked at sampled
+    # nodes, among them nodes of the last planes and of the boundaries, for V
+    # and for the last variable (the highest offsets).  After one step a node
+    # depends only on the state and fibres within one node, so the oracle
+    # steps the 3 x 3 x 3 box around each sampled node (clipped at the grid's
+    # faces, which are the box's faces there too).
+    torch, bbx = env
+    nx, ny, nz, h, dt = 1024, 512, 520, 0.2, 0.02
+    assert 8 * nx * ny * nz > 2 ** 31
+    rng = np.random.default_rng(2031)
+    fib = rng.standard_normal((nz, ny, nx, 3), dtype=np.float32)
+    fib /= np.linalg.norm(fib, axis=-1, keepdims=True) + np.float32(1e-6)
+    par = [4.0, 0.003, 50.0, 0.09]
+    rest = oracle.rest_state(oracle.BR, par)
+    st0 = np.empty((8, nz, ny, nx), np.float32)
+    for v in range(1, 8):
+        st0[v] = rest[v]
+    st0[0] = rest[0] + 20.0 * rng.standard_normal((nz, ny, nx), dtype=np.float32)
+    G = bbx.Grid(nx, ny, nz, h, None)
+    G.set_fibres(fib, 0.1, 0.025)
+    G.set_ionic_model(bbx.BBX_BR, par)
+    G.set_timestep(dt)
+    G.write_all(st0)
+    G.step(dt, 1)
+    V1 = G.read_state(0)
+    F1 = G.read_state(7)
+    pick = [(nz - 1, ny - 1, nx - 1), (nz - 1, 0, 0), (0, 0, 0), (nz - 2, ny // 2, nx - 1), (nz - 1, 17, 513)]
+    for _ in range(120):
+        pick.append((int(rng.integers(nz)), int(rng.integers(ny)), int(rng.integers(nx))))
+    for _ in range(60):  # the last planes
+        pick.append((nz - 1 - int(rng.integers(3)), int(rng.integers(ny)), int(rng.integers(nx))))
+    ev = ef = 0.0
+    for z, y, x in pick:
+        z0, z1 = max(z - 1, 0), min(z + 2, nz)
+        y0, y1 = max(y - 1, 0), min(y + 2, ny)
+        x0, x1 = max(x - 1, 0), min(x + 2, nx)
+        box = np.ascontiguousarray(st0[:, z0:z1, y0:y1, x0:x1]).astype(np.float64)
+        fb = np.ascontiguousarray(fib[z0:z1, y0:y1, x0:x1])
+        og = oracle.Grid(x1 - x0, y1 - y0, z1 - z0, h, None, fb, 0.1, 0.025)
+        osim = oracle.Sim(og, oracle.BR, par=par, state=box)
+        osim.step(dt, 1)
+        ref_v = osim.state[0, z - z0, y - y0, x - x0]
+        ref_f = osim.state[7, z - z0, y - y0, x - x0]
+        ev = max(ev, abs(float(V1[z, y, x]) - ref_v) / max(abs(ref_v), 1.0))
+        ef = max(ef, abs(float(F1[z, y, x]) - ref_f))
+    G.close()
+    assert ev <= 1e-5, ev
+    assert ef <= 1e-6, ef
