@@ -1251,6 +1251,13 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
         mbar_init_fence();
     }
     __syncthreads();
+    // Programmatic dependent launch: the next step's grid may be scheduled from
+    // here on (its CTAs take the SMs this grid's CTAs leave), and every thread
+    // waits until the previous grid on the stream has completed and its writes
+    // are visible before it touches memory that grid wrote (state, t, n,
+    // parity, activation map); with no such grid the wait returns at once.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     const int piece_begin = blockIdx.x * L.cta_stride, piece_end = piece_begin + L.cta_count[blockIdx.x];
     int issued = 0;   // producer lane 0: plane loads issued (ring A)

@@ -775,10 +775,25 @@ LaunchArgs launch_args(const LaunchPlan& lp, const TissueArgs* d_tissues, int* d
     return L;
 }
 
+// A step launch, allowed to start while the previous kernel on the stream
+// finishes (programmatic stream serialization: the step kernel waits for it
+// with griddepcontrol.wait before it reads or writes anything that kernel may
+// touch; each grid is at most one wave of resident CTAs, so the early CTAs
+// never hold back the previous grid's).
 cudaError_t launch(const LaunchPlan& lp, const LaunchArgs& L, cudaStream_t s) {
     if (lp.n_planes == 0) return cudaSuccess;
     void* args[] = {(void*)&L};
-    return cudaLaunchKernel(lp.k.fn, dim3(lp.ctas), dim3(lp.k.threads), args, (size_t)lp.k.smem, s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(lp.ctas);
+    cfg.blockDim = dim3(lp.k.threads);
+    cfg.dynamicSmemBytes = (size_t)lp.k.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, lp.k.fn, args);
 }
 
 // Select the kernel for a configuration, check it fits, and return the CTA
