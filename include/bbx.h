@@ -53,7 +53,10 @@ extern "C" {
 #define BBX_ERR_UNSUPPORTED (-9) /* no compiled kernel for this configuration */
 
 /* ---- cell models (section "Cell models") ------------------------------- */
-/* Parameters in order; a shorter params array keeps the remaining defaults.
+/* Parameters in order; a shorter params array keeps the remaining defaults,
+ * entries past the model's list are ignored.  bbx_set_ionic_model returns
+ * BBX_ERR_ARG for a non-finite parameter, FHN eps = 0, Barkley a or eps = 0,
+ * and BBX_BR_FCA Kc or tau_c not positive or eps negative.
  *  BBX_FHN       2 vars (u, v).  eps=0.3 beta=0.71 gamma=0.5.  Eq. (FHN), read
  *                with the cubic u - u^3/3 (fhncub).  threshold 0.
  *  BBX_BARKLEY   2 vars (u, v).  a=0.75 b=0.02 eps=0.02.  Barkley (1991):

@@ -1625,6 +1625,10 @@ int bbx_set_ionic_model(bbx_grid* g, int model, const double* params, int n_para
     for (int i = 0; i < n_params && i < nd; ++i) p[i] = params[i];
     for (int i = 0; i < nd; ++i)
         if (!std::isfinite(p[i])) return BBX_ERR_ARG;
+    // parameters the kernels divide by, and the calcium gate's constants
+    if ((model == BBX_FHN && p[0] == 0.0) || (model == BBX_BARKLEY && (p[0] == 0.0 || p[2] == 0.0)) ||
+        (model == BBX_BR_FCA && (!(p[4] > 0.0) || !(p[5] > 0.0) || p[6] < 0.0)))
+        return BBX_ERR_ARG;
     cudaStreamSynchronize(g->stream);
     const size_t old_words = g->d_state[0] ? state_words(g) : 0;
     g->gates = GATES_F32;  // a new model starts with 32-bit storage

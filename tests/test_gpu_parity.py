@@ -393,6 +393,14 @@ def test_errors_are_reported(bbx):
     with pytest.raises(bbx.BbxError) as e:
         G.step(1.0, 1)
     assert e.value.code == bbx.BBX_ERR_UNSTABLE
+    # parameters the kernels divide by are refused, and the grid keeps its model
+    for model, par in ((bbx.BBX_FHN, [0.0]), (bbx.BBX_BARKLEY, [0.75, 0.02, 0.0]),
+                       (bbx.BBX_BR_FCA, [4.0, 0.003, 50.0, 0.09, 5e-6, 0.0]),
+                       (bbx.BBX_BR_FCA, [4.0, 0.003, 50.0, 0.09, -1.0])):
+        with pytest.raises(bbx.BbxError) as e:
+            G.set_ionic_model(model, par)
+        assert e.value.code == bbx.BBX_ERR_ARG
+    assert G.get_info()["model"] == bbx.BBX_FHN
     fib = np.ones((4, 8, 16, 3), np.float32)
     fib[1, 2, 3] = 0
     with pytest.raises(bbx.BbxError) as e:
