@@ -685,6 +685,29 @@ def run_bbx(args):
     ms_step = dev_ms / args.steps
     value = whole_job_rate(n_tissue, args.steps, ws, dev_ms * 1e-3)
 
+    # A/B on the same grid: the flushed step with the W-tilde sums loaded
+    # although they all vanish (the library skips them by default)
+    wsum_loaded = None
+    if ws == 1 and info["wsum_skipped"]:
+        G.set_wsum_elision(False)
+        for _ in range(args.warmup):
+            flush_l2(1.0)
+            one_step()
+        ab = []
+        for i in range(args.steps):
+            flush_l2(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one_step()
+            e1.record(stream)
+            ab.append((e0, e1))
+        torch.cuda.synchronize()
+        ab_ms = sum(a.elapsed_time(b) for a, b in ab) / args.steps
+        G.set_wsum_elision(True)
+        G.step_total()  # synchronising call: reports any device error of the runs
+        wsum_loaded = {"ms_per_step": ab_ms, "value": n_tissue / (ab_ms * 1e-3), "unit": "cell-updates/s",
+                       "note": "same grid and timing with the vanishing W-tilde sums (12 B per node) loaded"}
+
     e2e = None if args.no_e2e else run_e2e(G, w, st0, S, args, dist, dev, ws, n_tissue, one_step)
 
 
@@ -722,7 +745,8 @@ def run_bbx(args):
                                   else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": load_traffic("barkley_slab_256x256x64"), "peak_kind": peak_kind,
-                     "bytes_per_cell": B_alg},
+                     "bytes_per_cell": B_alg, "wsum_skipped": bool(info["wsum_skipped"]),
+                     "wsum_loaded": wsum_loaded},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "batched": batched,

@@ -139,6 +139,7 @@ typedef struct {
     long long n_tissue;      /* tissue nodes (active cells per step) */
     long long step;          /* steps taken since the model was set */
     double t;                /* model time */
+    int wsum_skipped;        /* 1: the W-tilde sums all vanish and a step does not load them */
 } bbx_info;
 
 /* Create a grid of nx*ny*nz nodes with spacing h (the paper's hx).
@@ -248,6 +249,18 @@ int bbx_set_resident(bbx_grid* g, int on);
  * Errors: BBX_ERR_ARG, BBX_ERR_STATE (no model), BBX_ERR_UNSUPPORTED (model
  * is not BBX_BR), BBX_ERR_NOMEM, BBX_ERR_CUDA. */
 int bbx_set_tabulation(bbx_grid* g, int on);
+
+/* Skip loading W-tilde sums that vanish.  The W-tilde part of the weights
+ * (Eq. (W), section "Monodomain diffusion and boundary conditions") differences
+ * the diffusion tensor across each node; the library stores those sums once
+ * per grid.  Where all of them are exactly 0 (fibres in the x-y plane whose
+ * direction depends on z only, the paper's rotational anisotropy; uniform
+ * fibres), a step of the grid on its own (not in a batch) does not read them
+ * from memory and uses zeros instead: the result is bitwise the same, with
+ * 12 bytes per node less to read.  on != 0: skip them where they all vanish
+ * (default); on = 0: always read them.  bbx_get_info's wsum_skipped tells
+ * whether the current fibres qualify.  Errors: BBX_ERR_ARG (null grid). */
+int bbx_set_wsum_elision(bbx_grid* g, int on);
 
 /* Time-stepping scheme.  BBX_SCHEME_UNSPLIT (default; section "Computation of
  * intermediate expressions"): V^{n+1} = V^n + dt (f(V^n, g^n) + L V^n +

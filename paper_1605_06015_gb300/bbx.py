@@ -46,7 +46,7 @@ class Info(ctypes.Structure):
                 ("nvars", ctypes.c_int), ("model", ctypes.c_int), ("masked", ctypes.c_int),
                 ("anisotropic", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
                 ("tile_z", ctypes.c_int), ("n_bricks", ctypes.c_longlong), ("n_tissue", ctypes.c_longlong),
-                ("step", ctypes.c_longlong), ("t", ctypes.c_double)]
+                ("step", ctypes.c_longlong), ("t", ctypes.c_double), ("wsum_skipped", ctypes.c_int)]
 
 
 def _load():
@@ -89,6 +89,7 @@ def _load():
         "bbx_set_solver": [P, I],
         "bbx_set_resident": [P, I],
         "bbx_set_tabulation": [P, I],
+        "bbx_set_wsum_elision": [P, I],
         "bbx_ppm_frame": [P, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D), P],
         "bbx_phase_singularities": [P, I, D, I, D, P, I, ctypes.POINTER(I)],
         "bbx_batch_create": [ctypes.POINTER(P), ctypes.POINTER(P), I],
@@ -446,6 +447,10 @@ def bbx_set_solver(g, solver):
 
 def bbx_set_tabulation(g, on=True):
     _check(_lib.bbx_set_tabulation(g, int(bool(on))), "bbx_set_tabulation")
+
+
+def bbx_set_wsum_elision(g, on=True):
+    _check(_lib.bbx_set_wsum_elision(g, int(bool(on))), "bbx_set_wsum_elision")
 
 
 def bbx_set_resident(g, on=True):

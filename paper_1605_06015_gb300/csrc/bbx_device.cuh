@@ -71,6 +71,7 @@ struct TissueArgs {  // (CUtensorMap members impose its alignment)
     float dt, theta, stim_amp;
     int split;  // 1: Lie operator splitting (diffusion substep, then kinetics); 0: unsplit
     int rk4;    // kinetics solver: 1 classical RK4 (right-hand-side models), 0 forward Euler / Rush-Larsen
+    int wsum_zero;  // 1: every W-tilde sum of the grid is exactly 0 (a single-grid launch then skips their copies)
     // diffusion constants over h^2: anisotropic D = Dperp I + (Dpar-Dperp) f f^T
     // gives c_perp = Dperp/h^2, c_d = (Dpar-Dperp)/h^2, c_dh = c_d/2 (edge
     // weights), c_s = c_d/4 (Wtilde); isotropic D gives c_iso = D/h^2.
@@ -1238,6 +1239,21 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
     const int tid = threadIdx.x;
     const int warp = tid / 32, lane = tid % 32;
 
+    // W-tilde sums that vanish at every node of the grid (a fibre field whose
+    // tensor does not change along the directions the sums difference, e.g.
+    // fibres in the x-y plane turning with z only, or uniform fibres): a
+    // single-grid launch does not copy them, and their part of every ring-B
+    // stage holds zeros for the whole launch, so the arithmetic is unchanged
+    // and the result is bitwise the one with the sums loaded.  (Batch launches
+    // share stages between grids and always copy them.)
+    const bool skip_d = ANISO && L.single && L.t0.wsum_zero;
+    if (skip_d) {
+        for (int s = 0; s < NB; ++s) {
+            float4* zd = reinterpret_cast<float4*>(bstages + s * P::B_STAGE + P::D_OFF);
+            for (int i = tid; i < P::D_RAW / 16; i += P::THREADS) zd[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    const uint32_t b_bytes = skip_d ? P::B_BYTES - P::D_RAW : P::B_BYTES;
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
@@ -1289,7 +1305,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                 unsigned char* sb = bstages + bslot * P::B_STAGE;
                 if (ANISO) {
                     tma_load_4d(sb + P::F_OFF, &T->tm_f, x0 + 4, y0, z, 0, bar);  // fibres stored from x = -4
-                    tma_load_4d(sb + P::D_OFF, &T->tm_d, x0, y0, z, 0, bar);
+                    if (!skip_d) tma_load_4d(sb + P::D_OFF, &T->tm_d, x0, y0, z, 0, bar);
                 }
                 if (S > 1 && S32 > 1) tma_load_4d(sb + P::S_OFF, &T->tm_s[src], x0, y0, z, 1, bar);
                 if (NG) tma_load_4d(sb + P::G_OFF, &T->tm_g[src], x0, y0, z, 0, bar);
@@ -1323,7 +1339,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                         if (MASKED) tma_load_3d(st + P::M_OFF, &T->tm_m, pc_early.x - 16, y0 - 1, z, bar);
                         if (HB && !halo) {  // computed plane b = off - 1 (3D) or off (sheet): slot b
                             const int b = PLANAR ? off : off - 1;
-                            mbar_expect_tx(&fullb[b], P::B_BYTES);
+                            mbar_expect_tx(&fullb[b], b_bytes);
                             load_b(T, src, pc_early.x, y0, z, b, &fullb[b]);
                         }
                     }
@@ -1404,7 +1420,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                         tma_load_3d(st + P::U_OFF, &T->tm_u[src], pc.x - 4, y0 - 1, z, bar);
                         if (MASKED) tma_load_3d(st + P::M_OFF, &T->tm_m, pc.x - 16, y0 - 1, z, bar);
                         if (HB && comp) {
-                            mbar_arrive_expect_tx(&fullb[bslot], P::B_BYTES);
+                            mbar_arrive_expect_tx(&fullb[bslot], b_bytes);
                             load_b(T, src, pc.x, y0, z, bslot, &fullb[bslot]);
                         }
                     }

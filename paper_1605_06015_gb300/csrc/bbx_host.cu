@@ -198,11 +198,13 @@ __global__ void k_fibres(const float* __restrict__ in, int nx, int ny, int nz, i
 // fibre replaced by f at p (D^p in place of its tensor; the D_perp parts of
 // D cancel in the difference).  The fibre field is fixed, so the three sums
 // are computed once, in double precision, and read by every step.  Layout
-// [3][nz][ny][px]; 0 at void nodes.
+// [3][nz][ny][px]; 0 at void nodes.  *nonzero is set to 1 if any stored sum
+// differs from 0 (the step kernel skips loading sums that all vanish).
 __global__ void k_divergence(const float* __restrict__ fib, int nx, int ny, int nz, int pxf, long long fplane,
                              long long fvol, const uint8_t* __restrict__ mask, int px, long long plane,
-                             long long vol, float* __restrict__ div) {
+                             long long vol, float* __restrict__ div, int* __restrict__ nonzero) {
     const long long n = (long long)nx * ny * nz;
+    bool any = false;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const int x = int(i % nx);
@@ -234,10 +236,13 @@ __global__ void k_divergence(const float* __restrict__ fib, int nx, int ny, int 
                 }
             }
         }
-        div[o] = (float)acc[0];
-        div[vol + o] = (float)acc[1];
-        div[2 * vol + o] = (float)acc[2];
+        const float s0 = (float)acc[0], s1 = (float)acc[1], s2 = (float)acc[2];
+        div[o] = s0;
+        div[vol + o] = s1;
+        div[2 * vol + o] = s2;
+        any = any || s0 != 0.0f || s1 != 0.0f || s2 != 0.0f;
     }
+    if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(nonzero, 1);
 }
 
 // Device mask byte: bit 0 tissue, bit 1 set when all 18 neighbours of the
@@ -840,6 +845,8 @@ struct bbx_grid {
     long long n_tissue = 0;
     float* d_fib = nullptr;  // [3][nz][ny][pxf], x stored from -4 (clamped padding)
     float* d_div = nullptr;  // [3][nz][ny][px]: the fixed W-tilde sums of every node (k_divergence)
+    bool wsum_zero = false;  // every W-tilde sum is exactly 0 (the step need not load them)
+    bool wsum_elide = true;  // skip loading vanishing sums (bbx_set_wsum_elision)
     int pxf = 0;
     long long fplane = 0, fvol = 0;
     bool aniso = false;
@@ -1163,6 +1170,7 @@ int encode_targs(const bbx_grid* g, int ty, TissueArgs* t) {
     t->theta = (float)g->theta;
     t->split = g->split;
     t->rk4 = g->rk4;
+    t->wsum_zero = (g->aniso && g->wsum_zero && g->wsum_elide) ? 1 : 0;
     t->stim_amp = g->d_stim ? (float)g->stim_amp : 0.0f;
     const double ih2 = 1.0 / (g->h * g->h);
     const double cd = (g->Dpar - g->Dperp) * ih2;
@@ -1586,12 +1594,20 @@ int bbx_set_fibres(bbx_grid* g, const float* f, double D_par, double D_perp) {
             } else {
                 e = cudaMemsetAsync(div, 0, sizeof(float) * 3 * (size_t)g->vol, g->stream);
                 if (e == cudaSuccess) {
+                    // g->d_err is clear here (reset after the fibre check); it
+                    // carries the "some sum is nonzero" word for this one call
                     k_divergence<<<n_blocks_for(g->ncell, 256), 256, 0, g->stream>>>(
-                        fib, g->nx, g->ny, g->nz, pxf, fplane, fvol, g->d_mask, g->px, g->plane, g->vol, div);
+                        fib, g->nx, g->ny, g->nz, pxf, fplane, fvol, g->d_mask, g->px, g->plane, g->vol, div,
+                        g->d_err);
                     e = cudaGetLastError();
                 }
+                int nonzero = 1;
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(&nonzero, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream);
+                if (e == cudaSuccess) e = cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream);
                 if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
                 if (e != cudaSuccess) rc = fail_cuda(e);
+                else g->wsum_zero = (nonzero == 0);
             }
         }
         if (rc != BBX_OK) {
@@ -1810,6 +1826,12 @@ int bbx_set_tabulation(bbx_grid* g, int on) {
     if (g->model != BBX_BR) return BBX_ERR_UNSUPPORTED;
     g->tab_on = on != 0;
     return apply_kinetics_setting(g);
+}
+
+int bbx_set_wsum_elision(bbx_grid* g, int on) {
+    if (!g) return BBX_ERR_ARG;
+    g->wsum_elide = on != 0;
+    return g->model ? prepare(g) : BBX_OK;
 }
 
 int bbx_set_resident(bbx_grid* g, int on) {
@@ -2213,6 +2235,7 @@ int bbx_get_info(bbx_grid* g, bbx_info* o) {
     o->n_tissue = owned;
     o->step = d.n;
     o->t = d.t;
+    o->wsum_skipped = (g->aniso && g->wsum_zero && g->wsum_elide) ? 1 : 0;
     return BBX_OK;
 }
 

@@ -40,6 +40,7 @@ def test_argument_errors_without_gpu():
     assert L.bbx_step(None, 0.1, 1) == bbx.BBX_ERR_ARG
     assert L.bbx_read_state(None, 0, None, 0) == bbx.BBX_ERR_ARG
     assert L.bbx_set_fibres(None, None, 1.0, 1.0) == bbx.BBX_ERR_ARG
+    assert L.bbx_set_wsum_elision(None, 1) == bbx.BBX_ERR_ARG
     L.bbx_destroy_grid(None)
 
 

@@ -222,3 +222,26 @@ def test_zero_fibre_at_tissue_is_an_error_and_void_fibres_ignored():
     assert oracle.Grid(3, 3, 2, 0.3, mask, fib, 1, 0.2).check_fibres() == -3
     mask[1, 1, 1] = 0
     assert oracle.Grid(3, 3, 2, 0.3, mask, fib, 1, 0.2).check_fibres() == 0
+
+
+def test_rotational_fibres_have_no_first_order_term():
+    # Fibres in the x-y plane whose angle depends on z only: D_xz = D_yz = 0,
+    # D_zz = D_perp and D_xx, D_yy, D_xy vary with z alone, so every
+    # divergence sum_j d_j D_jk vanishes and the W-tilde part of the weights
+    # (the only part of the face weights that is odd in q) is zero: opposite
+    # face weights are equal, and L of the linear field u = z is exactly 0 on
+    # every plane with two z neighbours.  A field with out-of-plane, varying
+    # fibres breaks both.
+    nx, ny, nz, h = 9, 7, 8, 0.3
+    u = np.broadcast_to(np.arange(nz, dtype=np.float64)[:, None, None], (nz, ny, nx)).copy()
+    g = oracle.Grid(nx, ny, nz, h, None, wl.rotational_fibres(nx, ny, nz), 1.0, 0.25)
+    assert np.all(g.apply_L(u)[1:-1] == 0.0)
+    for (z, y, x) in [(1, 1, 1), (3, 0, 4), (nz - 2, ny - 1, nx - 1), (4, 3, 0)]:
+        W = g.weights(x, y, z)
+        assert W[1, 1, 0] == W[1, 1, 2] or x in (0, nx - 1)
+        assert W[1, 0, 1] == W[1, 2, 1] or y in (0, ny - 1)
+        assert W[0, 1, 1] == W[2, 1, 1]
+    gs = oracle.Grid(nx, ny, nz, h, None, wl.smooth_fibres(nx, ny, nz, h), 1.0, 0.25)
+    assert np.abs(gs.apply_L(u)[1:-1]).max() > 1e-3
+    W = gs.weights(4, 3, 4)
+    assert max(abs(W[1, 1, 0] - W[1, 1, 2]), abs(W[1, 0, 1] - W[1, 2, 1]), abs(W[0, 1, 1] - W[2, 1, 1])) > 1e-6
