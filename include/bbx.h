@@ -256,7 +256,8 @@ int bbx_set_tabulation(bbx_grid* g, int on);
  * per grid.  Where all of them are exactly 0 (fibres in the x-y plane whose
  * direction depends on z only, the paper's rotational anisotropy; uniform
  * fibres), a step of the grid on its own (not in a batch) does not read them
- * from memory and uses zeros instead: the result is bitwise the same, with
+ * from memory: unmasked grids run a kernel variant without the W-tilde term,
+ * the others use zeros in its place.  The result is bitwise the same, with
  * 12 bytes per node less to read.  on != 0: skip them where they all vanish
  * (default); on = 0: always read them.  bbx_get_info's wsum_skipped tells
  * whether the current fibres qualify.  Errors: BBX_ERR_ARG (null grid). */

@@ -820,6 +820,11 @@ __host__ __device__ constexpr int rows_of_threads(int ty) { return ty == 28 ? 14
 // two CTAs of 256 threads allow 128 registers a thread; the masked
 // anisotropic stencil with 2 rows a thread and the surrogate need more; the
 // unmasked isotropic variants fit in 64, so four CTAs hide more latency).
+// Anisotropy of a step kernel variant: isotropic (c_iso only), anisotropic
+// with the W-tilde sums read from memory, or anisotropic for grids whose
+// W-tilde sums all vanish (no sums in the stage ring, no W-tilde arithmetic).
+enum : int { AN_ISO = 0, AN_SUMS = 1, AN_NO_SUMS = 2 };
+
 __host__ __device__ constexpr int ctas_per_sm(bool masked, bool aniso, int ty, bool surr) {
     return (masked && aniso && ty != 7) || ty == 28 || (surr && ty != 7) ? 1 : (!masked && !aniso && !surr ? 4 : 2);
 }
@@ -863,13 +868,13 @@ __device__ __forceinline__ void st_global_u16(uint16_t* p, uint16_t v) {
     asm volatile("st.global.u16 [%0], %1;" ::"l"(p), "h"(v));
 }
 
-template <int MODEL, bool MASKED, bool ANISO, int TY, bool SURR = false, int GATES = GATES_F32>
+template <int MODEL, bool MASKED, int ANISO, int TY, bool SURR = false, int GATES = GATES_F32>
 struct Plan {
     static constexpr int S = Model<MODEL>::S;
     static constexpr int NG = GATES ? 6 : 0;  // variables stored in 16 bits (the gates, last in the state)
     static constexpr int TX = kTileX;
     static constexpr int RY = rows_of_threads(TY);
-    static constexpr int CTAS = ctas_per_sm(MASKED, ANISO, TY, SURR);
+    static constexpr int CTAS = ctas_per_sm(MASKED, ANISO != AN_ISO, TY, SURR);
     static constexpr int CY = TY / RY;  // nodes per thread along y (each a pair in x)
     static constexpr int THREADS = 32 * RY + 32;  // consumer warps + producer warp
     static constexpr int UW = TX + 8;   // x from x0-4 to x0+TX+3 (16-byte aligned start)
@@ -886,7 +891,7 @@ struct Plan {
     // ring B, one stage per computed plane: the node's own unit fibre and
     // W-tilde sums (3 x TX x TY floats each), the other variables
     static constexpr int F_RAW = ANISO ? 3 * TX * TY * 4 : 0;
-    static constexpr int D_RAW = ANISO ? 3 * TX * TY * 4 : 0;
+    static constexpr int D_RAW = ANISO == AN_SUMS ? 3 * TX * TY * 4 : 0;
     static constexpr int S32_RAW = (S > 1) ? (S - 1 - NG) * TX * TY * 4 : 0;  // 32-bit non-diffusing variables
     static constexpr int G_RAW = NG * TX * TY * 2;                              // 16-bit gates
     static constexpr int S_RAW = S32_RAW + G_RAW;
@@ -930,7 +935,7 @@ struct Nb {
 // (L u)_p for a node whose 18 neighbours are all tissue: the weights of
 // Eq. (Lu) with psi = 1 everywhere, in difference form.  c_perp = Dperp/h^2,
 // c_d = (Dpar-Dperp)/h^2, c_dh = c_d/2, c_s = c_d/4.
-template <bool ANISO>
+template <int ANISO>
 __device__ __forceinline__ float lap_interior(const Coef& a, const Nb& n, F3 f, F3 sd) {
     if (!ANISO) {
         return a.c_iso * (((n.xp + n.xm) + (n.yp + n.ym)) + (n.zp + n.zm) - 6.0f * n.u0);
@@ -944,10 +949,12 @@ __device__ __forceinline__ float lap_interior(const Coef& a, const Nb& n, F3 f, 
     float L = Dxx * ((n.xp + n.xm) - two_u);
     L = fmaf(Dyy, (n.yp + n.ym) - two_u, L);
     L = fmaf(Dzz, (n.zp + n.zm) - two_u, L);
-    float dv = sd.x * (n.xp - n.xm);
-    dv = fmaf(sd.y, n.yp - n.ym, dv);
-    dv = fmaf(sd.z, n.zp - n.zm, dv);
-    L = fmaf(a.c_s, dv, L);
+    if (ANISO == AN_SUMS) {
+        float dv = sd.x * (n.xp - n.xm);
+        dv = fmaf(sd.y, n.yp - n.ym, dv);
+        dv = fmaf(sd.z, n.zp - n.zm, dv);
+        L = fmaf(a.c_s, dv, L);
+    }
     L = fmaf(Dxy, (n.pp + n.mm) - (n.pm + n.mp), L);
     L = fmaf(Dxz, (n.xpzp + n.xmzm) - (n.xpzm + n.xmzp), L);
     L = fmaf(Dyz, (n.ypzp + n.ymzm) - (n.ypzm + n.ymzp), L);
@@ -957,7 +964,7 @@ __device__ __forceinline__ float lap_interior(const Coef& a, const Nb& n, F3 f, 
 // (L u)_p for a node of an unmasked grid whose y and z neighbours are inside
 // the array; px, mx in {0, 1} are psi of the x+1 and x-1 neighbours (0 only
 // at the array's x faces).
-template <bool ANISO>
+template <int ANISO>
 __device__ __forceinline__ float lap_xbound(const Coef& a, const Nb& n, float px, float mx, F3 f, F3 sd) {
     const float ex = px * (n.xp - n.u0) + mx * (n.xm - n.u0);
     if (!ANISO) {
@@ -972,10 +979,12 @@ __device__ __forceinline__ float lap_xbound(const Coef& a, const Nb& n, float px
     float L = Dxx * ex;
     L = fmaf(Dyy, (n.yp + n.ym) - two_u, L);
     L = fmaf(Dzz, (n.zp + n.zm) - two_u, L);
-    float dv = (px * mx) * sd.x * (n.xp - n.xm);
-    dv = fmaf(sd.y, n.yp - n.ym, dv);
-    dv = fmaf(sd.z, n.zp - n.zm, dv);
-    L = fmaf(a.c_s, dv, L);
+    if (ANISO == AN_SUMS) {
+        float dv = (px * mx) * sd.x * (n.xp - n.xm);
+        dv = fmaf(sd.y, n.yp - n.ym, dv);
+        dv = fmaf(sd.z, n.zp - n.zm, dv);
+        L = fmaf(a.c_s, dv, L);
+    }
     L = fmaf(Dxy, px * (n.pp - n.pm) + mx * (n.mm - n.mp), L);
     L = fmaf(Dxz, px * (n.xpzp - n.xpzm) + mx * (n.xmzm - n.xmzp), L);
     L = fmaf(Dyz, (n.ypzp + n.ymzm) - (n.ypzm + n.ymzp), L);
@@ -994,7 +1003,7 @@ struct Psi {
 // (L u)_p for any tissue node: every weight carries its psi (a void or
 // out-of-array neighbour contributes nothing); the W-tilde sums already hold
 // a void neighbour's tensor replaced by D^p.
-template <bool ANISO>
+template <int ANISO>
 __device__ __forceinline__ float lap_general(const Coef& a, const Nb& n, const Psi& q, F3 f, F3 sd) {
     auto d = [&](bool ps, float uq) { return ps ? (uq - n.u0) : 0.0f; };
     const float exp_ = d(q.xp, n.xp), exm = d(q.xm, n.xm), eyp = d(q.yp, n.yp), eym = d(q.ym, n.ym);
@@ -1010,10 +1019,12 @@ __device__ __forceinline__ float lap_general(const Coef& a, const Nb& n, const P
     float L = Dxx * (exp_ + exm);
     L = fmaf(Dyy, eyp + eym, L);
     L = fmaf(Dzz, ezp + ezm, L);
-    float dv = (q.xp && q.xm) ? sd.x * (n.xp - n.xm) : 0.0f;
-    if (q.yp && q.ym) dv = fmaf(sd.y, n.yp - n.ym, dv);
-    if (q.zp && q.zm) dv = fmaf(sd.z, n.zp - n.zm, dv);
-    L = fmaf(a.c_s, dv, L);
+    if (ANISO == AN_SUMS) {
+        float dv = (q.xp && q.xm) ? sd.x * (n.xp - n.xm) : 0.0f;
+        if (q.yp && q.ym) dv = fmaf(sd.y, n.yp - n.ym, dv);
+        if (q.zp && q.zm) dv = fmaf(sd.z, n.zp - n.zm, dv);
+        L = fmaf(a.c_s, dv, L);
+    }
     L = fmaf(Dxy, (d(q.pp, n.pp) + d(q.mm, n.mm)) - (d(q.pm, n.pm) + d(q.mp, n.mp)), L);
     L = fmaf(Dxz, (d(q.xpzp, n.xpzp) + d(q.xmzm, n.xmzm)) - (d(q.xpzm, n.xpzm) + d(q.xmzp, n.xmzp)), L);
     L = fmaf(Dyz, (d(q.ypzp, n.ypzp) + d(q.ymzm, n.ymzm)) - (d(q.ypzm, n.ypzm) + d(q.ymzp, n.ymzp)), L);
@@ -1208,9 +1219,9 @@ __device__ __forceinline__ int tile_row_of(int4 pc, int off) {
 // rings: full[s] completes when the plane's bulk copies have landed, empty[s]
 // when all RY consumer warps are done with the plane.  No CTA-wide barrier is
 // taken per plane.
-template <int MODEL, bool MASKED, bool ANISO, int TY, bool SURR = false, bool PLANAR = false, bool GEN = false,
+template <int MODEL, bool MASKED, int ANISO, int TY, bool SURR = false, bool PLANAR = false, bool GEN = false,
           int GATES = GATES_F32>
-__global__ void __launch_bounds__(32 * rows_of_threads(TY) + 32, ctas_per_sm(MASKED, ANISO, TY, SURR))
+__global__ void __launch_bounds__(32 * rows_of_threads(TY) + 32, ctas_per_sm(MASKED, ANISO != AN_ISO, TY, SURR))
 step_kernel(const __grid_constant__ LaunchArgs L) {
     using P = Plan<MODEL, MASKED, ANISO, TY, SURR, GATES>;
     static_assert(GATES == GATES_F32 || (MODEL == BBX_BR && !SURR), "16-bit gates: Beeler-Reuter without surrogate");
@@ -1246,7 +1257,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
     // stage holds zeros for the whole launch, so the arithmetic is unchanged
     // and the result is bitwise the one with the sums loaded.  (Batch launches
     // share stages between grids and always copy them.)
-    const bool skip_d = ANISO && L.single && L.t0.wsum_zero;
+    const bool skip_d = ANISO == AN_SUMS && L.single && L.t0.wsum_zero;
     if (skip_d) {
         for (int s = 0; s < NB; ++s) {
             float4* zd = reinterpret_cast<float4*>(bstages + s * P::B_STAGE + P::D_OFF);
@@ -1305,7 +1316,7 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                 unsigned char* sb = bstages + bslot * P::B_STAGE;
                 if (ANISO) {
                     tma_load_4d(sb + P::F_OFF, &T->tm_f, x0 + 4, y0, z, 0, bar);  // fibres stored from x = -4
-                    if (!skip_d) tma_load_4d(sb + P::D_OFF, &T->tm_d, x0, y0, z, 0, bar);
+                    if (ANISO == AN_SUMS && !skip_d) tma_load_4d(sb + P::D_OFF, &T->tm_d, x0, y0, z, 0, bar);
                 }
                 if (S > 1 && S32 > 1) tma_load_4d(sb + P::S_OFF, &T->tm_s[src], x0, y0, z, 1, bar);
                 if (NG) tma_load_4d(sb + P::G_OFF, &T->tm_g[src], x0, y0, z, 0, bar);
@@ -1555,11 +1566,15 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
                             // the pair's own fibres and W-tilde sums ([comp][row][x] in ring B)
                             const int bo = (row0 + r) * TX + 2 * tx;
                             const float2 fx = ld2(Fb, bo), fy = ld2(Fb + CB, bo), fz = ld2(Fb + 2 * CB, bo);
-                            const float2 dx = ld2(Db, bo), dy = ld2(Db + CB, bo), dz = ld2(Db + 2 * CB, bo);
                             f[0] = F3{fx.x, fy.x, fz.x};
                             f[1] = F3{fx.y, fy.y, fz.y};
-                            sd[0] = F3{dx.x, dy.x, dz.x};
-                            sd[1] = F3{dx.y, dy.y, dz.y};
+                            if (ANISO == AN_SUMS) {
+                                const float2 dx = ld2(Db, bo), dy = ld2(Db + CB, bo), dz = ld2(Db + 2 * CB, bo);
+                                sd[0] = F3{dx.x, dy.x, dz.x};
+                                sd[1] = F3{dx.y, dy.y, dz.y};
+                            } else {
+                                sd[0] = sd[1] = F3{0.f, 0.f, 0.f};
+                            }
                         } else {
     #pragma unroll
                             for (int e = 0; e < 2; ++e) f[e] = sd[e] = F3{0.f, 0.f, 0.f};

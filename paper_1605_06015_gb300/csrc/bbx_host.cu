@@ -15,13 +15,13 @@
 #include "bbx_mlp.cuh"
 
 namespace bbx {
-StepKernel step_kernel_fhn(bool masked, bool aniso, int ty, bool planar, bool general);
-StepKernel step_kernel_barkley(bool masked, bool aniso, int ty, bool planar, bool general);
-StepKernel step_kernel_br(bool masked, bool aniso, int ty, bool planar, bool general);
-StepKernel step_kernel_zfk(bool masked, bool aniso, int ty, bool planar, bool general);
-StepKernel step_kernel_diffusion(bool masked, bool aniso, int ty, bool planar, bool general);
-StepKernel step_kernel_br_mrl(bool masked, bool aniso, int ty, bool planar, bool general);
-StepKernel step_kernel_br_fca(bool masked, bool aniso, int ty, bool planar, bool general);
+StepKernel step_kernel_fhn(bool masked, int aniso, int ty, bool planar, bool general);
+StepKernel step_kernel_barkley(bool masked, int aniso, int ty, bool planar, bool general);
+StepKernel step_kernel_br(bool masked, int aniso, int ty, bool planar, bool general);
+StepKernel step_kernel_zfk(bool masked, int aniso, int ty, bool planar, bool general);
+StepKernel step_kernel_diffusion(bool masked, int aniso, int ty, bool planar, bool general);
+StepKernel step_kernel_br_mrl(bool masked, int aniso, int ty, bool planar, bool general);
+StepKernel step_kernel_br_fca(bool masked, int aniso, int ty, bool planar, bool general);
 cudaError_t mrl_build_table(float4* tab, double dt, cudaStream_t s);
 cudaError_t br_build_rl_table(float4* tab, double dt, double tau_c, cudaStream_t s);
 StepKernel step_kernel_br_surrogate(bool masked, bool aniso, int ty);
@@ -107,13 +107,18 @@ void model_kernel_params(int model, const double* p, float* mp) {
 // planar: a grid with nz = 1 (sheet kernels, tiles marched along y).  The
 // surrogate kernels exist for 3D grids only.  general: the grid uses the Lie
 // scheme or the RK4 solver (kernels for 7- and 14-row tiles).
-StepKernel lookup_kernel(int model, bool masked, bool aniso, int ty, bool surrogate, bool planar, bool general,
+// aniso: AN_ISO, AN_SUMS or AN_NO_SUMS (the last only for the plain kernels of
+// unmasked grids; the 16-bit-gate and surrogate variants read the sums)
+StepKernel lookup_kernel(int model, bool masked, int aniso, int ty, bool surrogate, bool planar, bool general,
                          int gates = GATES_F32) {
     if (gates != GATES_F32)  // 16-bit gates: Beeler-Reuter without surrogate
-        return model == BBX_BR && !surrogate ? step_kernel_br16(masked, aniso, ty, planar, general, gates)
-                                             : StepKernel{nullptr, 0, 0, 0};
+        return model == BBX_BR && !surrogate && aniso != AN_NO_SUMS
+                   ? step_kernel_br16(masked, aniso != AN_ISO, ty, planar, general, gates)
+                   : StepKernel{nullptr, 0, 0, 0};
     if (surrogate)
-        return model == BBX_BR && !planar ? step_kernel_br_surrogate(masked, aniso, ty) : StepKernel{nullptr, 0, 0, 0};
+        return model == BBX_BR && !planar && aniso != AN_NO_SUMS
+                   ? step_kernel_br_surrogate(masked, aniso != AN_ISO, ty)
+                   : StepKernel{nullptr, 0, 0, 0};
     switch (model) {
         case BBX_FHN: return step_kernel_fhn(masked, aniso, ty, planar, general);
         case BBX_BARKLEY: return step_kernel_barkley(masked, aniso, ty, planar, general);
@@ -803,7 +808,7 @@ cudaError_t launch(const LaunchPlan& lp, const LaunchArgs& L, cudaStream_t s) {
 
 // Select the kernel for a configuration, check it fits, and return the CTA
 // budget (resident CTAs on the whole GPU).
-int select_kernel(int model, bool masked, bool aniso, int ty, int device, int num_sms, StepKernel* out,
+int select_kernel(int model, bool masked, int aniso, int ty, int device, int num_sms, StepKernel* out,
                   int* ctas, bool surrogate, bool planar, bool general, int gates = GATES_F32) {
     StepKernel k = lookup_kernel(model, masked, aniso, ty, surrogate, planar, general, gates);
     if (!k.fn) return BBX_ERR_UNSUPPORTED;
@@ -1247,8 +1252,14 @@ int prepare(bbx_grid* g) {
     BBX_CUDA(cudaStreamSynchronize(g->stream));
     StepKernel k;
     int ctas = 0;
-    int rc = select_kernel(g->model, g->d_mask != nullptr, g->aniso, g->ty, g->device, g->num_sms, &k, &ctas,
-                           g->surr_on && g->model == BBX_BR, g->nz == 1, wants_general(g), g->gates);
+    const bool surr = g->surr_on && g->model == BBX_BR;
+    int rc = BBX_ERR_UNSUPPORTED;
+    if (g->aniso && g->wsum_zero && g->wsum_elide && !g->d_mask)  // the variant without W-tilde sums, if built
+        rc = select_kernel(g->model, false, AN_NO_SUMS, g->ty, g->device, g->num_sms, &k, &ctas, surr, g->nz == 1,
+                           wants_general(g), g->gates);
+    if (rc == BBX_ERR_UNSUPPORTED)
+        rc = select_kernel(g->model, g->d_mask != nullptr, g->aniso ? AN_SUMS : AN_ISO, g->ty, g->device,
+                           g->num_sms, &k, &ctas, surr, g->nz == 1, wants_general(g), g->gates);
     if (rc) return rc;
     if ((rc = encode_targs(g, g->ty, &g->h_t))) return rc;
     BBX_CUDA(cudaMemcpyAsync(g->d_t, &g->h_t, sizeof(TissueArgs), cudaMemcpyHostToDevice, g->stream));
@@ -2635,7 +2646,7 @@ int batch_build(bbx_batch* b, const std::vector<int>* tys) {
     for (size_t gi = 0; gi < b->groups.size(); ++gi) {
         auto& gr = b->groups[gi];
         int ctas = 0;
-        int rc = select_kernel(gr.model, gr.masked, gr.aniso, gr.ty, b->device, b->num_sms, &gr.lp.k, &ctas, gr.surr,
+        int rc = select_kernel(gr.model, gr.masked, gr.aniso ? AN_SUMS : AN_ISO, gr.ty, b->device, b->num_sms, &gr.lp.k, &ctas, gr.surr,
                                gr.planar, gr.general);
         if (rc) return rc;
         long long share = total_work > 0 ? (long long)((double)ctas * gr.work / total_work + 0.5) : 1;

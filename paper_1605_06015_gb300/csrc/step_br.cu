@@ -3,7 +3,7 @@
 
 namespace bbx {
 
-template <bool MA, bool AN, int TY, bool SU = false, bool PL = false, bool GE = false>
+template <bool MA, int AN, int TY, bool SU = false, bool PL = false, bool GE = false>
 static StepKernel make_br() {
     using P = Plan<BBX_BR, MA, AN, TY, SU>;
     return StepKernel{reinterpret_cast<const void*>(&step_kernel<BBX_BR, MA, AN, TY, SU, PL, GE>), P::SMEM,
@@ -12,7 +12,15 @@ static StepKernel make_br() {
 
 // planar: grids with nz = 1 (tiles marched along y); general: the variant
 // for the Lie scheme (7- and 14-row tiles)
-StepKernel step_kernel_br(bool masked, bool aniso, int ty, bool planar, bool general) {
+StepKernel step_kernel_br(bool masked, int aniso, int ty, bool planar, bool general) {
+    // unmasked grids whose W-tilde sums all vanish: no sums in the stage ring
+    // (plain variants; the general ones read the sums, or skip their copies)
+#define BBX_CASE_NS(T) \
+    if (!masked && aniso == AN_NO_SUMS && ty == T) \
+        return general ? StepKernel{nullptr, 0, 0, 0} \
+                       : (planar ? make_br<false, AN_NO_SUMS, T, false, true>() : make_br<false, AN_NO_SUMS, T>());
+    BBX_CASE_NS(7) BBX_CASE_NS(14) BBX_CASE_NS(28)
+#undef BBX_CASE_NS
 #define BBX_CASE(MA, AN, T) \
     if (masked == MA && aniso == AN && ty == T) { \
         if (general && T == 28) return StepKernel{nullptr, 0, 0, 0}; \

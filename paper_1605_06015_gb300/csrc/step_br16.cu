@@ -6,14 +6,14 @@
 
 namespace bbx {
 
-template <bool MA, bool AN, int TY, bool PL, bool GE, int GA>
+template <bool MA, int AN, int TY, bool PL, bool GE, int GA>
 static StepKernel make_br16() {
     using P = Plan<BBX_BR, MA, AN, TY, false, GA>;
     return StepKernel{reinterpret_cast<const void*>(&step_kernel<BBX_BR, MA, AN, TY, false, PL, GE, GA>), P::SMEM,
                       P::THREADS, TY};
 }
 
-template <bool MA, bool AN, int TY, int GA>
+template <bool MA, int AN, int TY, int GA>
 static StepKernel pick_br16(bool planar, bool general) {
     if (general) return planar ? make_br16<MA, AN, TY, true, true, GA>() : make_br16<MA, AN, TY, false, true, GA>();
     return planar ? make_br16<MA, AN, TY, true, false, GA>() : make_br16<MA, AN, TY, false, false, GA>();

@@ -5,7 +5,7 @@
 
 namespace bbx {
 
-template <bool MA, bool AN, int TY, bool PL = false>
+template <bool MA, int AN, int TY, bool PL = false>
 static StepKernel make_br_mrl() {
     using P = Plan<BBX_BR_MRL, MA, AN, TY, false>;
     return StepKernel{reinterpret_cast<const void*>(&step_kernel<BBX_BR_MRL, MA, AN, TY, false, PL, false>),
@@ -14,8 +14,12 @@ static StepKernel make_br_mrl() {
 
 // Tile rows 7 and 14 (the eleven variables make a 28-row stage too large for
 // shared memory); unsplit Euler / Rush-Larsen only.
-StepKernel step_kernel_br_mrl(bool masked, bool aniso, int ty, bool planar, bool general) {
+StepKernel step_kernel_br_mrl(bool masked, int aniso, int ty, bool planar, bool general) {
     if (general) return StepKernel{nullptr, 0, 0, 0};
+    // unmasked grids whose W-tilde sums all vanish: no sums in the stage ring
+    if (!masked && aniso == AN_NO_SUMS && (ty == 7 || ty == 14))
+        return ty == 7 ? (planar ? make_br_mrl<false, AN_NO_SUMS, 7, true>() : make_br_mrl<false, AN_NO_SUMS, 7>())
+                       : (planar ? make_br_mrl<false, AN_NO_SUMS, 14, true>() : make_br_mrl<false, AN_NO_SUMS, 14>());
 #define BBX_CASE(MA, AN, T) \
     if (masked == MA && aniso == AN && ty == T) \
         return planar ? make_br_mrl<MA, AN, T, true>() : make_br_mrl<MA, AN, T>();

@@ -3,7 +3,7 @@
 
 namespace bbx {
 
-template <bool MA, bool AN, int TY, bool PL, bool GE>
+template <bool MA, int AN, int TY, bool PL, bool GE>
 static StepKernel make_diffusion() {
     using P = Plan<BBX_DIFFUSION, MA, AN, TY>;
     return StepKernel{reinterpret_cast<const void*>(&step_kernel<BBX_DIFFUSION, MA, AN, TY, false, PL, GE>), P::SMEM,
@@ -12,7 +12,15 @@ static StepKernel make_diffusion() {
 
 // planar: grids with nz = 1 (tiles marched along y); general: the variant
 // for the Lie scheme or the RK4 solver (7- and 14-row tiles)
-StepKernel step_kernel_diffusion(bool masked, bool aniso, int ty, bool planar, bool general) {
+StepKernel step_kernel_diffusion(bool masked, int aniso, int ty, bool planar, bool general) {
+    // unmasked grids whose W-tilde sums all vanish: no sums in the stage ring
+    // (plain variants; the general ones read the sums, or skip their copies)
+#define BBX_CASE_NS(T) \
+    if (!masked && aniso == AN_NO_SUMS && ty == T) \
+        return general ? StepKernel{nullptr, 0, 0, 0} \
+                       : (planar ? make_diffusion<false, AN_NO_SUMS, T, true, false>() : make_diffusion<false, AN_NO_SUMS, T, false, false>());
+    BBX_CASE_NS(7) BBX_CASE_NS(14) BBX_CASE_NS(28)
+#undef BBX_CASE_NS
 #define BBX_CASE(MA, AN, T) \
     if (masked == MA && aniso == AN && ty == T) { \
         if (general && T == 28) return StepKernel{nullptr, 0, 0, 0}; \

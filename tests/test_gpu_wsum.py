@@ -3,9 +3,10 @@
 The W-tilde part of the weights of Eq. (W) differences the diffusion tensor
 across a node.  For fibres in the x-y plane turning with z only (the
 rotational anisotropy of the slab workloads) and for uniform fibres, every
-such sum is exactly zero, and a single-grid step skips their copies and uses
-zeros.  The result must be bitwise the one with the sums loaded, and stay
-within the oracle bars."""
+such sum is exactly zero.  A single-grid step then runs a kernel variant
+without the sums (plain kernels of unmasked grids) or skips their copies and
+uses zeros (masked grids, the general variants).  The result must be bitwise
+the one with the sums loaded, and stay within the oracle bars."""
 import numpy as np
 import pytest
 
@@ -32,7 +33,7 @@ def _uniform_fibres(nx, ny, nz, f=(1.0, 0.5, 0.25)):
     return fib
 
 
-def _grid(bbx, w, fibres, elide, ty=None):
+def _grid(bbx, w, fibres, elide, ty=None, setup=None):
     G = bbx.Grid(w.nx, w.ny, w.nz, w.h, w.mask)
     G.set_wsum_elision(elide)
     G.set_fibres(fibres, w.D_par, w.D_perp)
@@ -40,11 +41,13 @@ def _grid(bbx, w, fibres, elide, ty=None):
         G.set_tiling(ty, 16)
     G.set_ionic_model(w.model, w.params)
     G.set_threshold(w.theta)
+    if setup is not None:
+        setup(G)
     return G
 
 
-def _run(bbx, w, fibres, elide, n_steps, ty=None):
-    G = _grid(bbx, w, fibres, elide, ty)
+def _run(bbx, w, fibres, elide, n_steps, ty=None, setup=None):
+    G = _grid(bbx, w, fibres, elide, ty, setup)
     rest = [float(G.read_state(v).reshape(-1)[0]) for v in range(G.get_info()["nvars"])]
     G.write_all(w.initial_state(rest).astype(np.float32))
     G.step(w.dt, n_steps)
@@ -57,15 +60,29 @@ def _barkley(nx, ny, nz, mask=None):
     return w
 
 
+def _tabulated(G):
+    G.set_tabulation(True)
+
+
+def _lie(G):
+    G.set_scheme(1)
+
+
+# The plain kernels of unmasked grids have a variant without the sums; masked
+# grids and the general variants (Lie scheme, RK4, tabulation) keep the sums
+# in the stage ring and skip only their copies.
 CASES = [
-    # name, workload, fibres, steps, tile rows
-    ("rotational slab, 7-row tiles", lambda: _barkley(100, 37, 19), "rot", 60, 7),
-    ("rotational slab, 14-row tiles", lambda: _barkley(100, 37, 19), "rot", 60, 14),
-    ("rotational slab, 28-row tiles", lambda: _barkley(130, 61, 11), "rot", 60, 28),
+    # name, workload, fibres, steps, tile rows, extra set-up
+    ("rotational slab, 7-row tiles", lambda: _barkley(100, 37, 19), "rot", 60, 7, None),
+    ("rotational slab, 14-row tiles", lambda: _barkley(100, 37, 19), "rot", 60, 14, None),
+    ("rotational slab, 28-row tiles", lambda: _barkley(130, 61, 11), "rot", 60, 28, None),
+    ("rotational slab, Lie scheme", lambda: _barkley(100, 37, 19), "rot", 60, 14, _lie),
     ("masked block, uniform fibres", lambda: _barkley(
-        70, 45, 20, wl.random_geometry(70, 45, 20, seed=7, tissue_frac=0.8, aniso=False)[0]), "uni", 40, None),
-    ("sheet, uniform oblique fibres", lambda: wl.fhn_sheet(150, 70), "uni2d", 80, None),
-    ("Beeler-Reuter slab, rotational", lambda: wl.br_slab(96, 40, 12), "rot", 40, None),
+        70, 45, 20, wl.random_geometry(70, 45, 20, seed=7, tissue_frac=0.8, aniso=False)[0]), "uni", 40, None,
+     None),
+    ("sheet, uniform oblique fibres", lambda: wl.fhn_sheet(150, 70), "uni2d", 80, None, None),
+    ("Beeler-Reuter slab, rotational", lambda: wl.br_slab(96, 40, 12), "rot", 40, None, None),
+    ("Beeler-Reuter slab, tabulated", lambda: wl.br_slab(96, 40, 12), "rot", 40, 7, _tabulated),
 ]
 
 
@@ -77,14 +94,14 @@ def _fibres(w, kind):
     return _uniform_fibres(w.nx, w.ny, w.nz)
 
 
-@pytest.mark.parametrize("name,make,kind,n_steps,ty", CASES, ids=[c[0] for c in CASES])
-def test_skipped_sums_give_the_loaded_result_bitwise(bbx, name, make, kind, n_steps, ty):
+@pytest.mark.parametrize("name,make,kind,n_steps,ty,setup", CASES, ids=[c[0] for c in CASES])
+def test_skipped_sums_give_the_loaded_result_bitwise(bbx, name, make, kind, n_steps, ty, setup):
     w = make()
     if kind == "uni2d":
         w.D_par, w.D_perp = 1.0, 0.3
     fib = _fibres(w, kind)
-    on = _run(bbx, w, fib, True, n_steps, ty)
-    off = _run(bbx, w, fib, False, n_steps, ty)
+    on = _run(bbx, w, fib, True, n_steps, ty, setup)
+    off = _run(bbx, w, fib, False, n_steps, ty, setup)
     assert on[4] == 1 and off[4] == 0
     assert np.array_equal(on[1].view(np.uint32), off[1].view(np.uint32))
     assert np.array_equal(on[2], off[2])
