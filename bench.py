@@ -474,6 +474,12 @@ def run_configs(args, dev, stream, dist=None, n_ranks=1):
                              "Beeler-Reuter shell in 512^3, the six gates stored as binary16"),
         "br_256x256x64_u16": (lambda: wl.br_slab(256, 256, 64), (2, 22),
                               "Beeler-Reuter slab 256x256x64, the six gates stored as 16-bit fixed point"),
+        "br_shell_512_tab_u16": (lambda: wl.br_shell(512), (2, 22),
+                                 "Beeler-Reuter shell in 512^3, Rush-Larsen coefficients tabulated, the six gates "
+                                 "stored as 16-bit fixed point (not in the default list)"),
+        "br_256x256x64_tab_u16": (lambda: wl.br_slab(256, 256, 64), (2, 22),
+                                  "Beeler-Reuter slab 256x256x64, Rush-Larsen coefficients tabulated, the six gates "
+                                  "stored as 16-bit fixed point (not in the default list)"),
     }
     out = {}
     for name in args.configs.split(","):
@@ -486,7 +492,7 @@ def run_configs(args, dev, stream, dist=None, n_ranks=1):
         G.set_ionic_model(w.model, w.params)
         G.set_threshold(w.theta)
         G.set_timestep(w.dt)
-        if name.endswith("_tab"):
+        if name.endswith("_tab") or "_tab_" in name:
             G.set_tabulation(True)
         st = initial_state(G, w)
         gates = {"_u16": bbx.BBX_GATES_UNORM16, "_f16": bbx.BBX_GATES_FP16}.get(name[-4:], bbx.BBX_GATES_FP32)
