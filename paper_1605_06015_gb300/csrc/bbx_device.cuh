@@ -816,15 +816,15 @@ constexpr int kTileX = 64;  // nodes per brick along x: 32 threads x 2 nodes
 // ring of planes and so finish together).
 __host__ __device__ constexpr int rows_of_threads(int ty) { return ty == 28 ? 14 : 7; }
 
-// Resident CTAs per SM a kernel variant is built for (the register budget:
-// two CTAs of 256 threads allow 128 registers a thread; the masked
-// anisotropic stencil with 2 rows a thread and the surrogate need more; the
-// unmasked isotropic variants fit in 64, so four CTAs hide more latency).
 // Anisotropy of a step kernel variant: isotropic (c_iso only), anisotropic
 // with the W-tilde sums read from memory, or anisotropic for grids whose
 // W-tilde sums all vanish (no sums in the stage ring, no W-tilde arithmetic).
 enum : int { AN_ISO = 0, AN_SUMS = 1, AN_NO_SUMS = 2 };
 
+// Resident CTAs per SM a kernel variant is built for (the register budget:
+// two CTAs of 256 threads allow 128 registers a thread; the masked
+// anisotropic stencil with 2 rows a thread and the surrogate need more; the
+// unmasked isotropic variants fit in 64, so four CTAs hide more latency).
 __host__ __device__ constexpr int ctas_per_sm(bool masked, bool aniso, int ty, bool surr) {
     return (masked && aniso && ty != 7) || ty == 28 || (surr && ty != 7) ? 1 : (!masked && !aniso && !surr ? 4 : 2);
 }
@@ -1252,7 +1252,9 @@ step_kernel(const __grid_constant__ LaunchArgs L) {
 
     // W-tilde sums that vanish at every node of the grid (a fibre field whose
     // tensor does not change along the directions the sums difference, e.g.
-    // fibres in the x-y plane turning with z only, or uniform fibres): a
+    // fibres in the x-y plane turning with z only, or uniform fibres), in a
+    // variant that keeps them (masked grids, the general, surrogate and
+    // 16-bit-gate kernels; unmasked plain kernels run AN_NO_SUMS instead): a
     // single-grid launch does not copy them, and their part of every ring-B
     // stage holds zeros for the whole launch, so the arithmetic is unchanged
     // and the result is bitwise the one with the sums loaded.  (Batch launches
