@@ -245,3 +245,29 @@ def test_rotational_fibres_have_no_first_order_term():
     assert np.abs(gs.apply_L(u)[1:-1]).max() > 1e-3
     W = gs.weights(4, 3, 4)
     assert max(abs(W[1, 1, 0] - W[1, 1, 2]), abs(W[1, 0, 1] - W[1, 2, 1]), abs(W[0, 1, 1] - W[2, 1, 1])) > 1e-6
+
+
+def test_uniform_fibres_on_a_masked_grid_have_no_first_order_term():
+    # With a void neighbour's tensor replaced by the node's own (the reading of
+    # the W-tilde sums at void and out-of-array neighbours), uniform fibres
+    # give vanishing sums everywhere, also beside the mask's holes: each face
+    # weight is exactly psi of that neighbour times D_kk / h^2, with no odd part.
+    nx, ny, nz, h = 7, 6, 5, 0.3
+    mask = wl.random_geometry(nx, ny, nz, seed=11, tissue_frac=0.7, aniso=False)[0]
+    g = oracle.Grid(nx, ny, nz, h, mask, _oblique((nz, ny, nx)), 1.0, 0.25)
+    faces = {0: ((1, 1, 2), (1, 1, 0)), 1: ((1, 2, 1), (1, 0, 1)), 2: ((2, 1, 1), (0, 1, 1))}
+    checked = 0
+    for (z, y, x) in zip(*np.nonzero(mask)):
+        x, y, z = int(x), int(y), int(z)
+        W = g.weights(x, y, z)
+        rc, D = g.tensor(x, y, z)
+        assert rc == 0
+        for k, (ip, im) in faces.items():
+            for idx, d in ((ip, 1), (im, -1)):
+                c = [x, y, z]
+                c[k] += d
+                inside = 0 <= c[0] < nx and 0 <= c[1] < ny and 0 <= c[2] < nz
+                psi = 1.0 if inside and mask[c[2], c[1], c[0]] else 0.0
+                assert abs(W[idx] - psi * D[k, k] / h ** 2) <= 1e-12 * D[k, k] / h ** 2
+                checked += 1
+    assert checked > 100
